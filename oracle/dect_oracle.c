@@ -1,0 +1,527 @@
+/*
+ * FP64 CPU oracle for the dual-energy CT hot path (TEST INFRASTRUCTURE ONLY).
+ *
+ * Plain, slow, obviously correct restatement of what the paper computes:
+ *   - Siddon system matrix A of Eq. (1) (Sec. 2.1; Siddon's method, ref. [42]),
+ *   - forward projection A x and its transpose A^T y,
+ *   - the backward-difference gradient and isotropic TV of Eq. (2),
+ *   - the isotropic shrinkage that solves the z-subproblem, Eq. (8),
+ *   - the ADM iteration of Eq. (7)/(9)/(10) with the gradient G_f of Eq. (9),
+ *   - the 2x2 material decomposition of Eq. (11)-(12),
+ *   - the Prewitt edge map and weights e_ik of Eq. (14) (Sec. 2.3),
+ *   - the PLS normal equation of Eq. (13)-(15) solved by Jacobi-preconditioned CG.
+ *
+ * Only the tests, the package smoke check and the benchmark's CPU-baseline leg
+ * load this library.  It shares no code, header or table with the CUDA path.
+ * Compile with -ffp-contract=off so that a*b+c is never fused: the same
+ * source then gives the same bits on x86-64 and on AArch64.
+ *
+ * Readings of places where the paper is silent or garbled (each one is also
+ * listed with the design notes):
+ *   R1 Eq. (8): z = max(|w| - 1/rho, 0) * w/|w| with w = grad f - lambda/rho,
+ *      z = 0 where |w| = 0 (the exact minimiser of the z-line of Eq. (7)).
+ *   R2 lambda and z have the shape of grad f: two components per pixel.
+ *   R3 the TV of Eq. (4) acts on each energy channel separately, so the
+ *      stacked problem of Eq. (3) splits into one ADM per channel.
+ *   R5 xi (multiplier step) is a parameter; the default elsewhere is xi = rho.
+ *   R6 "BB-like" step: with c(G) = |G|^2 / (mu |A G|^2 + rho |grad G|^2)
+ *      (the exact line-search step of the quadratic f-subproblem along -G),
+ *      rule BB1 uses alpha^k = c(G^{k-1}) (alpha^0 = c(G^0)), which is the
+ *      Barzilai-Borwein step s's/s'y of the previous step; rule CAUCHY uses
+ *      alpha^k = c(G^k).  Without the line search of the full method the
+ *      lagged step is strongly non-monotone on sparse-view data, so CAUCHY is
+ *      the default of the callers; both rules are kept.
+ *   R7 Eq. (2) differences with an index outside the image are 0.
+ *      i = row (y), j = column (x).
+ *   R8 no projection onto x >= 0 (Eq. (10) has none).
+ *   R10 Siddon segments between consecutive sorted crossing parameters go to
+ *      the pixel that holds the segment midpoint; zero-length ones are dropped.
+ *   R13 Eq. (15) with Hessian(R) = 2 L_e reads (I + gamma L_e) u = D^{-1} x.
+ *   R14 edges: 3x3 Prewitt magnitude of x_h and x_l (replicate padding), each
+ *      divided by its maximum; a pixel is an edge if either exceeds tau;
+ *      e_ik = eps if pixel i or k is an edge, else 1.
+ *   R16 PCG: Jacobi preconditioner, initial guess D^{-1} x.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+/* Fan-beam slice geometry (Sec. 2.1, Fig. 1; Sec. 3). Units mm and rad. */
+typedef struct {
+    int n;            /* image n x n */
+    double px;        /* pixel side */
+    int nv;           /* views */
+    int nb;           /* detector bins */
+    double pitch;     /* bin pitch */
+    double sod;       /* source to isocentre */
+    double sdd;       /* source to detector */
+    double start;     /* angle of view 0 */
+    double arc;       /* angular range covered by the nv views */
+    double det_offset;
+} orc_geom;
+
+/* ------------------------------------------------------------------------ */
+/* Geometry: one ray per bin, from the source point to the bin centre.       */
+/* ------------------------------------------------------------------------ */
+void orc_ray(const orc_geom *g, int v, int b, double S[2], double D[2])
+{
+    double th = g->start + (double)v * (g->arc / (double)g->nv);
+    double c = cos(th), s = sin(th);
+    S[0] = g->sod * c;
+    S[1] = g->sod * s;
+    double cx = (g->sod - g->sdd) * c, cy = (g->sod - g->sdd) * s;
+    double u = ((double)b - 0.5 * (double)(g->nb - 1)) * g->pitch + g->det_offset;
+    D[0] = cx - u * s;
+    D[1] = cy + u * c;
+}
+
+static int cmp_double(const void *a, const void *b)
+{
+    double x = *(const double *)a, y = *(const double *)b;
+    return (x > y) - (x < y);
+}
+
+/*
+ * Siddon's method (ref. [42]) for ray (v, b): the ray is P(a) = S + a (D - S),
+ * a in [0, 1].  All crossing parameters of the pixel-grid lines inside the
+ * image box are collected, sorted, de-duplicated, and each piece between
+ * consecutive parameters is given to the pixel holding its midpoint (R10).
+ * Writes up to `cap` (pixel index, length in mm) pairs; returns the count.
+ * Pixel index = row * n + col, row = y, col = x.
+ */
+int orc_siddon_ray(const orc_geom *g, int v, int b, int32_t *idx, double *len, int cap)
+{
+    double S[2], D[2];
+    orc_ray(g, v, b, S, D);
+    const int n = g->n;
+    const double dx = D[0] - S[0], dy = D[1] - S[1];
+    const double L = sqrt(dx * dx + dy * dy);
+    const double lo = -0.5 * (double)n * g->px;
+    const double hi = lo + (double)n * g->px;
+
+    double amin = 0.0, amax = 1.0;
+    if (dx != 0.0) {
+        double t0 = (lo - S[0]) / dx, t1 = (hi - S[0]) / dx;
+        amin = fmax(amin, fmin(t0, t1));
+        amax = fmin(amax, fmax(t0, t1));
+    } else if (!(S[0] >= lo && S[0] < hi)) {
+        return 0;
+    }
+    if (dy != 0.0) {
+        double t0 = (lo - S[1]) / dy, t1 = (hi - S[1]) / dy;
+        amin = fmax(amin, fmin(t0, t1));
+        amax = fmin(amax, fmax(t0, t1));
+    } else if (!(S[1] >= lo && S[1] < hi)) {
+        return 0;
+    }
+    if (!(amin < amax)) return 0;
+
+    double *a = (double *)malloc(sizeof(double) * (size_t)(2 * n + 6));
+    int na = 0;
+    a[na++] = amin;
+    a[na++] = amax;
+    for (int k = 0; k <= n; ++k) {
+        double plane = lo + (double)k * g->px;
+        if (dx != 0.0) {
+            double t = (plane - S[0]) / dx;
+            if (t > amin && t < amax) a[na++] = t;
+        }
+        if (dy != 0.0) {
+            double t = (plane - S[1]) / dy;
+            if (t > amin && t < amax) a[na++] = t;
+        }
+    }
+    qsort(a, (size_t)na, sizeof(double), cmp_double);
+
+    int cnt = 0;
+    for (int k = 0; k + 1 < na; ++k) {
+        double a0 = a[k], a1 = a[k + 1];
+        if (!(a1 > a0)) continue;                 /* duplicate (corner) */
+        double mid = 0.5 * (a0 + a1);
+        double xm = S[0] + mid * dx, ym = S[1] + mid * dy;
+        int col = (int)floor((xm - lo) / g->px);
+        int row = (int)floor((ym - lo) / g->px);
+        if (col < 0 || col >= n || row < 0 || row >= n) continue;
+        if (cnt < cap) {
+            idx[cnt] = row * n + col;
+            len[cnt] = (a1 - a0) * L;
+        }
+        ++cnt;
+    }
+    free(a);
+    return cnt;
+}
+
+/* Number of (ray, pixel) intersections of the whole geometry. */
+int64_t orc_table_nnz(const orc_geom *g)
+{
+    int cap = 4 * g->n + 8;
+    int32_t *ti = (int32_t *)malloc(sizeof(int32_t) * (size_t)cap);
+    double *tl = (double *)malloc(sizeof(double) * (size_t)cap);
+    int64_t total = 0;
+    for (int v = 0; v < g->nv; ++v)
+        for (int b = 0; b < g->nb; ++b)
+            total += orc_siddon_ray(g, v, b, ti, tl, cap);
+    free(ti);
+    free(tl);
+    return total;
+}
+
+/* Ray-major table of A (row r = v * nb + b): rowptr[M + 1], idx[nnz], len[nnz]. */
+void orc_table_build(const orc_geom *g, int64_t *rowptr, int32_t *idx, double *len)
+{
+    int cap = 4 * g->n + 8;
+    int64_t pos = 0;
+    rowptr[0] = 0;
+    for (int v = 0; v < g->nv; ++v)
+        for (int b = 0; b < g->nb; ++b) {
+            int c = orc_siddon_ray(g, v, b, idx + pos, len + pos, cap);
+            pos += c;
+            rowptr[(int64_t)v * g->nb + b + 1] = pos;
+        }
+}
+
+/* y = A x  (Eq. (1)). */
+void orc_project(int64_t m, const int64_t *rowptr, const int32_t *idx, const double *len,
+                 const double *x, double *y)
+{
+    for (int64_t r = 0; r < m; ++r) {
+        double s = 0.0;
+        for (int64_t k = rowptr[r]; k < rowptr[r + 1]; ++k) s += len[k] * x[idx[k]];
+        y[r] = s;
+    }
+}
+
+/* x = A^T y: the transpose, written as the scatter of each row. */
+void orc_backproject(int64_t m, int64_t npix, const int64_t *rowptr, const int32_t *idx,
+                     const double *len, const double *y, double *x)
+{
+    for (int64_t j = 0; j < npix; ++j) x[j] = 0.0;
+    for (int64_t r = 0; r < m; ++r)
+        for (int64_t k = rowptr[r]; k < rowptr[r + 1]; ++k) x[idx[k]] += len[k] * y[r];
+}
+
+/* ------------------------------------------------------------------------ */
+/* Eq. (2): backward differences, gradient layout d[2][n][n]:                */
+/*   d[0][i][j] = x[i][j] - x[i-1][j]   (along rows, i = y)                  */
+/*   d[1][i][j] = x[i][j] - x[i][j-1]   (along columns, j = x)               */
+/* with 0 where i-1 or j-1 is outside the image (R7).                         */
+/* ------------------------------------------------------------------------ */
+void orc_grad(int n, const double *x, double *d)
+{
+    int64_t N = (int64_t)n * n;
+    for (int i = 0; i < n; ++i)
+        for (int j = 0; j < n; ++j) {
+            int64_t p = (int64_t)i * n + j;
+            d[p] = (i > 0) ? x[p] - x[p - n] : 0.0;
+            d[N + p] = (j > 0) ? x[p] - x[p - 1] : 0.0;
+        }
+}
+
+/* out = grad^T d, the exact transpose of orc_grad. */
+void orc_grad_t(int n, const double *d, double *out)
+{
+    int64_t N = (int64_t)n * n;
+    for (int64_t p = 0; p < N; ++p) out[p] = 0.0;
+    for (int i = 0; i < n; ++i)
+        for (int j = 0; j < n; ++j) {
+            int64_t p = (int64_t)i * n + j;
+            if (i > 0) { out[p] += d[p]; out[p - n] -= d[p]; }
+            if (j > 0) { out[p] += d[N + p]; out[p - 1] -= d[N + p]; }
+        }
+}
+
+/* Isotropic TV, Eq. (2): sum over pixels of |grad x|. */
+double orc_tv(int n, const double *x)
+{
+    int64_t N = (int64_t)n * n;
+    double *d = (double *)malloc(sizeof(double) * (size_t)(2 * N));
+    orc_grad(n, x, d);
+    double s = 0.0;
+    for (int64_t p = 0; p < N; ++p) s += sqrt(d[p] * d[p] + d[N + p] * d[N + p]);
+    free(d);
+    return s;
+}
+
+/* Eq. (8) under reading R1: per pixel, z = max(|w| - t, 0) w / |w|. */
+void orc_shrink(int64_t npix, const double *w, double t, double *z)
+{
+    for (int64_t p = 0; p < npix; ++p) {
+        double a = w[p], b = w[npix + p];
+        double nrm = sqrt(a * a + b * b);
+        double s = nrm - t;
+        if (s > 0.0 && nrm > 0.0) {
+            z[p] = s * a / nrm;
+            z[npix + p] = s * b / nrm;
+        } else {
+            z[p] = 0.0;
+            z[npix + p] = 0.0;
+        }
+    }
+}
+
+static double dot(int64_t n, const double *a, const double *b)
+{
+    double s = 0.0;
+    for (int64_t i = 0; i < n; ++i) s += a[i] * b[i];
+    return s;
+}
+
+/* ADM parameters for one channel (Eq. (6)-(10)). */
+typedef struct {
+    double mu, rho, xi;
+    int step_rule;     /* 0 = BB1 (lagged exact step), 1 = CAUCHY (R6) */
+    int max_iter;
+    double tol;        /* stop when |Phi_{k+1} - Phi_k| / Phi_k < tol; 0 = run max_iter */
+} orc_adm_params;
+
+/* ADM state of one channel (sizes: f N, z 2N, lam 2N). */
+typedef struct {
+    double *f, *z, *lam;
+    double alpha_prev;  /* c(G^{k-1}) for rule BB1; < 0 before the first step */
+} orc_adm_state;
+
+/*
+ * One ADM iteration, Eq. (10), for the channel problem
+ *   min ||grad f|| + mu/2 ||A f - g||^2:
+ *   z^{k+1}  = shrink(grad f^k - lam^k / rho, 1/rho)                      Eq. (8)
+ *   G^k      = mu A^T (A f^k - g) + rho grad^T(grad f^k - z^{k+1})
+ *              - grad^T lam^k                                             Eq. (9)
+ *   alpha^k  = BB-like step (R6)
+ *   f^{k+1}  = f^k - alpha^k G^k                                          Eq. (9)
+ *   lam^{k+1}= lam^k - xi (grad f^{k+1} - z^{k+1})                        Eq. (7)
+ * Returns the step used.  Optional outputs (may be NULL): G (N), and
+ * norms[3] = { |G|^2, |A G|^2, |grad G|^2 }.
+ */
+double orc_adm_iterate(int n, int64_t m, const int64_t *rowptr, const int32_t *idx,
+                       const double *len, const double *g, const orc_adm_params *prm,
+                       orc_adm_state *st, double *G_out, double *norms)
+{
+    const int64_t N = (int64_t)n * n;
+    const double mu = prm->mu, rho = prm->rho, xi = prm->xi;
+    double *gf = (double *)malloc(sizeof(double) * (size_t)(2 * N));
+    double *w = (double *)malloc(sizeof(double) * (size_t)(2 * N));
+    double *r = (double *)malloc(sizeof(double) * (size_t)m);
+    double *t1 = (double *)malloc(sizeof(double) * (size_t)N);
+    double *t2 = (double *)malloc(sizeof(double) * (size_t)N);
+    double *t3 = (double *)malloc(sizeof(double) * (size_t)N);
+    double *G = (double *)malloc(sizeof(double) * (size_t)N);
+    double *AG = (double *)malloc(sizeof(double) * (size_t)m);
+    double *gG = (double *)malloc(sizeof(double) * (size_t)(2 * N));
+
+    /* z-step, Eq. (8) */
+    orc_grad(n, st->f, gf);
+    for (int64_t p = 0; p < 2 * N; ++p) w[p] = gf[p] - st->lam[p] / rho;
+    orc_shrink(N, w, 1.0 / rho, st->z);
+
+    /* G_f, Eq. (9): three terms */
+    orc_project(m, rowptr, idx, len, st->f, r);
+    for (int64_t i = 0; i < m; ++i) r[i] -= g[i];
+    orc_backproject(m, N, rowptr, idx, len, r, t1);
+    for (int64_t p = 0; p < 2 * N; ++p) w[p] = gf[p] - st->z[p];
+    orc_grad_t(n, w, t2);
+    orc_grad_t(n, st->lam, t3);
+    for (int64_t p = 0; p < N; ++p) G[p] = mu * t1[p] + rho * t2[p] - t3[p];
+
+    /* step size (R6) */
+    orc_project(m, rowptr, idx, len, G, AG);
+    orc_grad(n, G, gG);
+    double gg = dot(N, G, G), aa = dot(m, AG, AG), dd = dot(2 * N, gG, gG);
+    double den = mu * aa + rho * dd;
+    double c = (den > 0.0) ? gg / den : 0.0;
+    double alpha;
+    if (prm->step_rule == 1 || st->alpha_prev < 0.0) alpha = c;
+    else alpha = st->alpha_prev;
+    st->alpha_prev = c;
+
+    /* f-step and multiplier step */
+    for (int64_t p = 0; p < N; ++p) st->f[p] -= alpha * G[p];
+    orc_grad(n, st->f, gf);
+    for (int64_t p = 0; p < 2 * N; ++p) st->lam[p] -= xi * (gf[p] - st->z[p]);
+
+    if (G_out) memcpy(G_out, G, sizeof(double) * (size_t)N);
+    if (norms) { norms[0] = gg; norms[1] = aa; norms[2] = dd; }
+    free(gf); free(w); free(r); free(t1); free(t2); free(t3); free(G); free(AG); free(gG);
+    return alpha;
+}
+
+/* Phi(f) = ||grad f||_TV + mu/2 ||A f - g||^2, the objective of Eq. (4) per channel. */
+double orc_objective(int n, int64_t m, const int64_t *rowptr, const int32_t *idx,
+                     const double *len, const double *g, double mu, const double *f)
+{
+    double *r = (double *)malloc(sizeof(double) * (size_t)m);
+    orc_project(m, rowptr, idx, len, f, r);
+    double s = 0.0;
+    for (int64_t i = 0; i < m; ++i) { double e = r[i] - g[i]; s += e * e; }
+    free(r);
+    return orc_tv(n, f) + 0.5 * mu * s;
+}
+
+/*
+ * The ADM loop of Eq. (10) for one channel, from f (in/out) with z = lam = 0.
+ * phi[0..iters] receives Phi(f^k); alpha[0..iters-1] the steps.
+ * Stops after max_iter iterations, or once the relative objective change is
+ * below tol (tol > 0).  Returns the number of iterations done.
+ */
+int orc_adm_run(int n, int64_t m, const int64_t *rowptr, const int32_t *idx, const double *len,
+                const double *g, const orc_adm_params *prm, double *f, double *phi, double *alpha)
+{
+    const int64_t N = (int64_t)n * n;
+    orc_adm_state st;
+    st.f = f;
+    st.z = (double *)calloc((size_t)(2 * N), sizeof(double));
+    st.lam = (double *)calloc((size_t)(2 * N), sizeof(double));
+    st.alpha_prev = -1.0;
+    double prev = orc_objective(n, m, rowptr, idx, len, g, prm->mu, f);
+    if (phi) phi[0] = prev;
+    int k = 0;
+    while (k < prm->max_iter) {
+        double a = orc_adm_iterate(n, m, rowptr, idx, len, g, prm, &st, NULL, NULL);
+        if (alpha) alpha[k] = a;
+        ++k;
+        double cur = orc_objective(n, m, rowptr, idx, len, g, prm->mu, f);
+        if (phi) phi[k] = cur;
+        if (prm->tol > 0.0 && prev > 0.0 && fabs(cur - prev) / prev < prm->tol) break;
+        prev = cur;
+    }
+    free(st.z);
+    free(st.lam);
+    return k;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Sec. 2.3: decomposition                                                    */
+/* ------------------------------------------------------------------------ */
+
+/*
+ * d = D^{-1} x per pixel, Eq. (11)-(12).  eta[m*2 + e]: material m (0, 1),
+ * energy e (0 = high, 1 = low).  D = [[eta_1H, eta_2H], [eta_1L, eta_2L]].
+ */
+void orc_direct_decompose(int64_t npix, const double *eta, const double *xh, const double *xl,
+                          double *d1, double *d2)
+{
+    double a = eta[0], b = eta[2];   /* row H: eta_1H, eta_2H */
+    double c = eta[1], e = eta[3];   /* row L: eta_1L, eta_2L */
+    double det = a * e - b * c;
+    for (int64_t p = 0; p < npix; ++p) {
+        d1[p] = (e * xh[p] - b * xl[p]) / det;
+        d2[p] = (-c * xh[p] + a * xl[p]) / det;
+    }
+}
+
+/* 3x3 Prewitt gradient magnitude with replicate padding (R14). */
+void orc_prewitt(int n, const double *x, double *mag)
+{
+    for (int i = 0; i < n; ++i)
+        for (int j = 0; j < n; ++j) {
+            double gx = 0.0, gy = 0.0;
+            for (int t = -1; t <= 1; ++t) {
+                int ii = i + t < 0 ? 0 : (i + t >= n ? n - 1 : i + t);
+                int jj = j + t < 0 ? 0 : (j + t >= n ? n - 1 : j + t);
+                int jl = j - 1 < 0 ? 0 : j - 1, jr = j + 1 >= n ? n - 1 : j + 1;
+                int iu = i - 1 < 0 ? 0 : i - 1, id = i + 1 >= n ? n - 1 : i + 1;
+                gx += x[(int64_t)ii * n + jr] - x[(int64_t)ii * n + jl];
+                gy += x[(int64_t)id * n + jj] - x[(int64_t)iu * n + jj];
+            }
+            mag[(int64_t)i * n + j] = sqrt(gx * gx + gy * gy);
+        }
+}
+
+/* Edge mask (1 = edge) from both energy images (R14). */
+void orc_edge_mask(int n, const double *xh, const double *xl, double tau, uint8_t *mask)
+{
+    int64_t N = (int64_t)n * n;
+    double *mh = (double *)malloc(sizeof(double) * (size_t)N);
+    double *ml = (double *)malloc(sizeof(double) * (size_t)N);
+    orc_prewitt(n, xh, mh);
+    orc_prewitt(n, xl, ml);
+    double Mh = 0.0, Ml = 0.0;
+    for (int64_t p = 0; p < N; ++p) { Mh = fmax(Mh, mh[p]); Ml = fmax(Ml, ml[p]); }
+    for (int64_t p = 0; p < N; ++p) {
+        int eh = Mh > 0.0 && mh[p] / Mh > tau;
+        int el = Ml > 0.0 && ml[p] / Ml > tau;
+        mask[p] = (uint8_t)(eh || el);
+    }
+    free(mh);
+    free(ml);
+}
+
+/* Weight e_ik of Eq. (14) between 4-neighbours p and q. */
+static double edge_w(const uint8_t *mask, int64_t p, int64_t q, double eps)
+{
+    return (mask[p] || mask[q]) ? eps : 1.0;
+}
+
+/* out = (I + gamma L_e) u, (L_e u)_i = sum_{k in N_i} e_ik (u_i - u_k) (R13). */
+void orc_pls_apply(int n, const uint8_t *mask, double gamma, double eps, const double *u, double *out)
+{
+    for (int i = 0; i < n; ++i)
+        for (int j = 0; j < n; ++j) {
+            int64_t p = (int64_t)i * n + j;
+            double s = 0.0;
+            if (i > 0) s += edge_w(mask, p, p - n, eps) * (u[p] - u[p - n]);
+            if (i + 1 < n) s += edge_w(mask, p, p + n, eps) * (u[p] - u[p + n]);
+            if (j > 0) s += edge_w(mask, p, p - 1, eps) * (u[p] - u[p - 1]);
+            if (j + 1 < n) s += edge_w(mask, p, p + 1, eps) * (u[p] - u[p + 1]);
+            out[p] = u[p] + gamma * s;
+        }
+}
+
+/* Jacobi diagonal 1 + gamma sum_k e_ik. */
+void orc_pls_diag(int n, const uint8_t *mask, double gamma, double eps, double *diag)
+{
+    for (int i = 0; i < n; ++i)
+        for (int j = 0; j < n; ++j) {
+            int64_t p = (int64_t)i * n + j;
+            double s = 0.0;
+            if (i > 0) s += edge_w(mask, p, p - n, eps);
+            if (i + 1 < n) s += edge_w(mask, p, p + n, eps);
+            if (j > 0) s += edge_w(mask, p, p - 1, eps);
+            if (j + 1 < n) s += edge_w(mask, p, p + 1, eps);
+            diag[p] = 1.0 + gamma * s;
+        }
+}
+
+/*
+ * Jacobi-preconditioned CG for (I + gamma L_e) u = d (Eq. (15), R13, R16),
+ * starting from u = d.  Runs max_iter iterations, or stops once
+ * |r| / |d| < tol (tol > 0).  Returns the iterations done; *relres = |r|/|d|.
+ */
+int orc_pls_pcg(int n, const uint8_t *mask, double gamma, double eps, const double *d,
+                double *u, int max_iter, double tol, double *relres)
+{
+    int64_t N = (int64_t)n * n;
+    double *r = (double *)malloc(sizeof(double) * (size_t)N);
+    double *z = (double *)malloc(sizeof(double) * (size_t)N);
+    double *p = (double *)malloc(sizeof(double) * (size_t)N);
+    double *Ap = (double *)malloc(sizeof(double) * (size_t)N);
+    double *M = (double *)malloc(sizeof(double) * (size_t)N);
+    orc_pls_diag(n, mask, gamma, eps, M);
+    memcpy(u, d, sizeof(double) * (size_t)N);
+    orc_pls_apply(n, mask, gamma, eps, u, Ap);
+    for (int64_t i = 0; i < N; ++i) r[i] = d[i] - Ap[i];
+    double bn = sqrt(dot(N, d, d));
+    for (int64_t i = 0; i < N; ++i) { z[i] = r[i] / M[i]; p[i] = z[i]; }
+    double rz = dot(N, r, z);
+    int it = 0;
+    double rn = sqrt(dot(N, r, r));
+    while (it < max_iter) {
+        if (tol > 0.0 && (bn == 0.0 || rn / bn < tol)) break;
+        orc_pls_apply(n, mask, gamma, eps, p, Ap);
+        double pAp = dot(N, p, Ap);
+        if (pAp <= 0.0) break;
+        double a = rz / pAp;
+        for (int64_t i = 0; i < N; ++i) { u[i] += a * p[i]; r[i] -= a * Ap[i]; }
+        ++it;
+        rn = sqrt(dot(N, r, r));
+        for (int64_t i = 0; i < N; ++i) z[i] = r[i] / M[i];
+        double rz_new = dot(N, r, z);
+        double beta = (rz != 0.0) ? rz_new / rz : 0.0;
+        rz = rz_new;
+        for (int64_t i = 0; i < N; ++i) p[i] = z[i] + beta * p[i];
+    }
+    if (relres) *relres = (bn > 0.0) ? rn / bn : 0.0;
+    free(r); free(z); free(p); free(Ap); free(M);
+    return it;
+}
