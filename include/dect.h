@@ -1,0 +1,223 @@
+/*
+ * dect.h -- C ABI of libdect, the GB300 (sm_103a) hot path of sparse-view
+ * dual-energy CT reconstruction and image-domain decomposition:
+ *
+ *   Li, Cai, Wang, Yan et al., "Efficient Image Reconstruction and Practical
+ *   Decomposition for Dual-energy Computed Tomography" (arXiv:1607.01650).
+ *
+ * Stage 1 reconstructs the high- and low-energy images x_h, x_l from their
+ * sinograms m_h, m_l by the alternating direction method (ADM) on the
+ * TV-regularised least-squares model of Eq. (4) (Sec. 2.2).  Stage 2
+ * decomposes the two images into two basis-material maps u_1, u_2 by the
+ * penalised least-squares (PLS) estimate of Eq. (13) (Sec. 2.3).
+ *
+ * Conventions (all entry points):
+ *   - Arrays are FP32, row-major, contiguous, in DEVICE memory of the plan's
+ *     device, allocated and owned by the caller, unless stated otherwise.
+ *   - Image of n x n pixels: index row * n + col, row = y, col = x; pixel
+ *     (0, 0) has its centre at (-(n-1) px / 2, -(n-1) px / 2) mm; the image is
+ *     centred on the rotation axis.  Units: mm, 1/mm, rad.
+ *   - Sinogram: [view][bin], n_views x n_bins.  Ray (v, b) goes from the
+ *     source S_v = SOD (cos t_v, sin t_v), t_v = start + v * (arc / n_views),
+ *     to the centre of bin b of a flat detector, at
+ *     (SOD - SDD)(cos t_v, sin t_v) + u_b (-sin t_v, cos t_v),
+ *     u_b = (b - (n_bins - 1) / 2) pitch + det_offset (Sec. 2.1, Fig. 1).
+ *   - Every call is ordered on `stream` (a cudaStream_t; NULL = legacy
+ *     default stream) and returns once its work is enqueued, except where a
+ *     call says that it synchronises.
+ *   - Arguments are checked on the host before anything is enqueued; a bad
+ *     argument returns DECT_ERR_INVALID_ARG and enqueues nothing.  CUDA
+ *     errors are returned as DECT_ERR_CUDA; dect_last_error() gives the text.
+ *   - There is no CPU fallback: without a usable sm_103a device every call
+ *     that needs one returns DECT_ERR_CUDA.
+ */
+#ifndef DECT_H
+#define DECT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    DECT_OK = 0,
+    DECT_ERR_INVALID_ARG = 1,
+    DECT_ERR_CUDA = 2,
+    DECT_ERR_OOM = 3,
+    DECT_ERR_TIMEOUT = 4,
+    DECT_ERR_NONFINITE = 5,
+    DECT_ERR_NOT_CONVERGED = 6
+} dect_status;
+
+/* Opaque CUDA stream (binary-compatible with cudaStream_t). */
+typedef struct CUstream_st *dect_stream;
+
+/* Fan-beam slice geometry: the centre slice of the cone-beam system of
+ * Sec. 2.1 / Fig. 1 and Sec. 3 (flat 1-D detector, circular source orbit). */
+typedef struct {
+    int n;               /* image is n x n pixels, 1 <= n <= 8192            */
+    double pixel_mm;     /* pixel side (> 0)                                  */
+    int n_views;         /* views, >= 1                                       */
+    int n_bins;          /* detector bins, >= 1                               */
+    double pitch_mm;     /* bin pitch (> 0)                                   */
+    double sod_mm;       /* source to rotation axis (> image half-diagonal)   */
+    double sdd_mm;       /* source to detector (> sod_mm)                     */
+    double start_rad;    /* angle of view 0                                   */
+    double arc_rad;      /* angular range of the n_views views (> 0)          */
+    double det_offset_mm;/* detector shift along its axis                     */
+} dect_geometry;
+
+/* Opaque plan: one geometry, its Siddon system matrix A of Eq. (1) stored on
+ * the device twice -- ray-major (for A x) and pixel-major (for A^T y). */
+typedef struct dect_plan dect_plan;
+
+typedef struct {
+    int64_t n_pixels;     /* N = n * n                                        */
+    int64_t n_rays;       /* M = n_views * n_bins                             */
+    int64_t nnz;          /* (ray, pixel) intersections of A                  */
+    int64_t table_bytes;  /* device bytes held by both tables                 */
+    int64_t n_grid_aligned; /* rays within 1e-9 mm of running along a grid line */
+} dect_plan_info;
+
+/*
+ * Build the plan of `geom` on CUDA device `device` (Eq. (1) and Siddon's
+ * method, ref. [42] of the paper): each ray's pieces between consecutive
+ * crossings of pixel-grid lines inside the image box, each given to the pixel
+ * that holds the piece's midpoint, crossing parameters in FP64, lengths
+ * stored as FP32 mm.  Zero-length pieces are dropped.  Synchronises `stream`.
+ * *out receives the plan (owned by the caller; free with dect_plan_destroy).
+ * Errors: DECT_ERR_INVALID_ARG for a bad geometry or NULL out;
+ * DECT_ERR_OOM when the tables do not fit; DECT_ERR_CUDA otherwise.
+ */
+dect_status dect_plan_create(const dect_geometry *geom, int device, dect_stream stream,
+                             dect_plan **out);
+
+/* Free a plan and its device tables (NULL is a no-op). Synchronises the device. */
+dect_status dect_plan_destroy(dect_plan *plan);
+
+/* Sizes of a plan (host struct written by the call). */
+dect_status dect_plan_get_info(const dect_plan *plan, dect_plan_info *info);
+
+/*
+ * Copy the ray-major table of A to HOST memory: rowptr[n_rays + 1] (int64),
+ * pix[nnz] (int32 pixel index), len[nnz] (FP32, mm); row r = v * n_bins + b,
+ * entries of a row in the order the ray meets them.  Any pointer may be NULL
+ * to skip it.  Synchronises `stream`.  For tests and inspection.
+ */
+dect_status dect_plan_copy_table(const dect_plan *plan, int64_t *rowptr, int32_t *pix,
+                                 float *len, dect_stream stream);
+
+/*
+ * y = A x, Eq. (1), for `batch` images: x [batch][n][n] -> y [batch][n_views][n_bins].
+ * FP32 multiply-add in the table's order; deterministic.
+ * Errors: DECT_ERR_INVALID_ARG (NULL plan/pointer, batch < 0).  batch = 0 is a no-op.
+ */
+dect_status dect_project(const dect_plan *plan, const float *x, float *y, int batch,
+                         dect_stream stream);
+
+/*
+ * x = A^T y, the exact transpose used by the gradient G_f of Eq. (9), for
+ * `batch` sinograms: y [batch][n_views][n_bins] -> x [batch][n][n].
+ * Gather form over the pixel-major table: every pixel sums its rays in
+ * increasing ray order; no atomics, bitwise reproducible.
+ */
+dect_status dect_backproject(const dect_plan *plan, const float *y, float *x, int batch,
+                             dect_stream stream);
+
+/* Step rules for the f-subproblem (Eq. (9)); c(G) = |G|^2/(mu|AG|^2 + rho|grad G|^2). */
+enum { DECT_STEP_BB1 = 0,     /* alpha^k = c(G^{k-1}), alpha^0 = c(G^0) (lagged, BB-like) */
+       DECT_STEP_CAUCHY = 1   /* alpha^k = c(G^k) (exact line search along -G)           */ };
+
+typedef struct {
+    double mu;          /* data weight of Eq. (4), > 0                                  */
+    double rho;         /* penalty of Eq. (6), > 0                                      */
+    double xi;          /* multiplier step of Eq. (7); <= 0 means xi = rho              */
+    double beta[2];     /* Eq. (3) weights: beta[0] on x_h (energy 0), beta[1] on x_l   */
+    int step_rule;      /* DECT_STEP_BB1 or DECT_STEP_CAUCHY                            */
+    int max_iter;       /* iterations, >= 0                                             */
+    double rel_obj_tol; /* stop a channel once |Phi_k - Phi_{k-1}| / Phi_{k-1} < tol;
+                           <= 0: always run max_iter                                    */
+    int check_every;    /* host checks "all channels stopped" every this many
+                           iterations (>= 1; 0 = 10); only used when rel_obj_tol > 0    */
+    int warm_start;     /* 0: start from x = 0; 1: start from the x passed in           */
+} dect_adm_params;
+
+typedef struct {
+    int iters;          /* iterations done (f^iters is the result)                      */
+    int converged;      /* 1 if the relative-objective test fired                       */
+    double objective;   /* Phi = |grad f|_TV + mu/2 |A f - g|^2 at the result (f = beta x) */
+    double rel_change;  /* last relative objective change                               */
+} dect_adm_report;
+
+/*
+ * ADM-TV reconstruction, Eq. (3)-(10), of `n_slices` dual-energy slices that
+ * share `plan`.  m: [n_slices][2][n_views][n_bins] measured line integrals
+ * (energy 0 = high kVp, 1 = low).  x: [n_slices][2][n][n]; on input the warm
+ * start (read only when params->warm_start = 1), on output the images x_h, x_l.
+ *
+ * Each channel c runs the iteration of Eq. (10) on f = beta_c x against
+ * g = beta_c m (the stacked system of Eq. (3) separates per channel because
+ * the TV of Eq. (4) is taken per channel):
+ *   z     = shrink(grad f - lambda/rho, 1/rho)                         Eq. (8)
+ *   G     = mu A^T (A f - g) + rho grad^T(grad f - z) - grad^T lambda  Eq. (9)
+ *   f    <- f - alpha G   (alpha from the step rule)                   Eq. (9)
+ *   lambda <- lambda - xi (grad f - z)                                 Eq. (7)
+ * with grad the backward differences of Eq. (2) and Phi the objective of
+ * Eq. (4).  Bulk arithmetic is FP32; the norms that give alpha and Phi are
+ * accumulated in FP64 across warps and blocks.
+ * reports: HOST array [n_slices * 2] (may be NULL).  Synchronises `stream`.
+ * Device scratch is taken from the stream-ordered allocator and returned
+ * before the call ends.
+ * Errors: DECT_ERR_INVALID_ARG, DECT_ERR_OOM, DECT_ERR_CUDA.
+ */
+dect_status dect_adm_tv(const dect_plan *plan, const float *m, float *x, int n_slices,
+                        const dect_adm_params *params, dect_adm_report *reports,
+                        dect_stream stream);
+
+typedef struct {
+    double eta[2][2];   /* eta[material][energy]: attenuation (1/mm) of basis material
+                           1 / 2 at energy 0 (high) / 1 (low); D of Eq. (12)            */
+    double gamma;       /* smoothness weight of Eq. (13), >= 0                           */
+    double edge_tau;    /* edge threshold on the max-normalised Prewitt magnitude        */
+    double edge_eps;    /* e_ik for pairs touching an edge pixel (Eq. (14)), >= 0        */
+    int max_iter;       /* PCG iterations, >= 0                                          */
+    double tol;         /* stop when |r| / |b| < tol (<= 0: run max_iter)                */
+} dect_pls_params;
+
+typedef struct {
+    int iters[2];       /* PCG iterations per material                                  */
+    double relres[2];   /* final |r| / |b| per material                                 */
+} dect_pls_report;
+
+/*
+ * PLS decomposition, Eq. (11)-(15), of `batch` slices of n x n pixels:
+ *   d = D^{-1} x per pixel (2x2 closed form in FP64), Eq. (11)-(12);
+ *   edge map: 3x3 Prewitt magnitude of x_h and of x_l (replicate padding),
+ *   each divided by its own maximum, edge where either exceeds edge_tau;
+ *   e_ik = edge_eps if pixel i or k is an edge, else 1, Eq. (14);
+ *   solve (I + gamma L_e) u_m = d_m for m = 1, 2, (L_e u)_i = sum over the
+ *   4-neighbours k inside the image of e_ik (u_i - u_k) -- Eq. (15), whose
+ *   Hessian of R is 2 L_e -- by Jacobi-preconditioned CG from u = d.
+ * xh, xl: [batch][n][n]; u1, u2: [batch][n][n] outputs.
+ * reports: HOST array [batch] (may be NULL).  Synchronises `stream`.
+ */
+dect_status dect_pls_decompose(const float *xh, const float *xl, int n, int batch,
+                               const dect_pls_params *params, float *u1, float *u2,
+                               dect_pls_report *reports, dect_stream stream);
+
+/* Text of a status code (static storage). */
+const char *dect_status_string(dect_status s);
+
+/* Text of the last CUDA error seen by this thread (static per thread). */
+const char *dect_last_error(void);
+
+/* Library version: major * 10000 + minor * 100 + patch. */
+int dect_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DECT_H */

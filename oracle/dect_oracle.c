@@ -35,7 +35,9 @@
  *      i = row (y), j = column (x).
  *   R8 no projection onto x >= 0 (Eq. (10) has none).
  *   R10 Siddon segments between consecutive sorted crossing parameters go to
- *      the pixel that holds the segment midpoint; zero-length ones are dropped.
+ *      the pixel that holds the segment midpoint; zero-length ones are dropped;
+ *      consecutive pieces given to the same pixel (a crossing within rounding
+ *      of a grid corner) are summed into one element a_ij.
  *   R13 Eq. (15) with Hessian(R) = 2 L_e reads (I + gamma L_e) u = D^{-1} x.
  *   R14 edges: 3x3 Prewitt magnitude of x_h and x_l (replicate padding), each
  *      divided by its maximum; a pixel is an edge if either exceeds tau;
@@ -134,7 +136,7 @@ int orc_siddon_ray(const orc_geom *g, int v, int b, int32_t *idx, double *len, i
     }
     qsort(a, (size_t)na, sizeof(double), cmp_double);
 
-    int cnt = 0;
+    int cnt = 0, last = -1;
     for (int k = 0; k + 1 < na; ++k) {
         double a0 = a[k], a1 = a[k + 1];
         if (!(a1 > a0)) continue;                 /* duplicate (corner) */
@@ -143,10 +145,20 @@ int orc_siddon_ray(const orc_geom *g, int v, int b, int32_t *idx, double *len, i
         int col = (int)floor((xm - lo) / g->px);
         int row = (int)floor((ym - lo) / g->px);
         if (col < 0 || col >= n || row < 0 || row >= n) continue;
-        if (cnt < cap) {
-            idx[cnt] = row * n + col;
-            len[cnt] = (a1 - a0) * L;
+        int pix = row * n + col;
+        double seg = (a1 - a0) * L;
+        /* a_ij is the whole length of ray i in pixel j: a crossing within
+           rounding of a grid corner can split it into two pieces that the
+           midpoint rule gives to the same pixel; they are summed. */
+        if (cnt > 0 && last == pix) {
+            if (cnt - 1 < cap) len[cnt - 1] += seg;
+            continue;
         }
+        if (cnt < cap) {
+            idx[cnt] = pix;
+            len[cnt] = seg;
+        }
+        last = pix;
         ++cnt;
     }
     free(a);

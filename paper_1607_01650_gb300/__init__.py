@@ -1,0 +1,315 @@
+"""GB300 (sm_103a) hot path of sparse-view dual-energy CT: ADM-TV reconstruction
+and PLS two-material decomposition (Li et al., arXiv:1607.01650, Sec. 2).
+
+This module is a thin ctypes binding of ``libdect.so`` (C ABI declared in
+``include/dect.h``).  It only marshals arguments: PyTorch supplies device
+memory and streams, and every step of the computation runs in the library's
+CUDA kernels.  There is no CPU fallback -- if the library or a CUDA device is
+missing, calls raise.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import dataclasses
+import math
+import os
+from typing import List, Optional, Sequence, Tuple
+
+from . import _build
+
+__all__ = ["Geometry", "Plan", "AdmParams", "PlsParams", "DectError", "load",
+           "project", "backproject", "adm_tv", "pls_decompose", "library_path"]
+
+
+class DectError(RuntimeError):
+    pass
+
+
+class _Geometry(C.Structure):
+    _fields_ = [("n", C.c_int), ("pixel_mm", C.c_double), ("n_views", C.c_int),
+                ("n_bins", C.c_int), ("pitch_mm", C.c_double), ("sod_mm", C.c_double),
+                ("sdd_mm", C.c_double), ("start_rad", C.c_double), ("arc_rad", C.c_double),
+                ("det_offset_mm", C.c_double)]
+
+
+class _PlanInfo(C.Structure):
+    _fields_ = [("n_pixels", C.c_int64), ("n_rays", C.c_int64), ("nnz", C.c_int64),
+                ("table_bytes", C.c_int64), ("n_grid_aligned", C.c_int64)]
+
+
+class _AdmParams(C.Structure):
+    _fields_ = [("mu", C.c_double), ("rho", C.c_double), ("xi", C.c_double),
+                ("beta", C.c_double * 2), ("step_rule", C.c_int), ("max_iter", C.c_int),
+                ("rel_obj_tol", C.c_double), ("check_every", C.c_int), ("warm_start", C.c_int)]
+
+
+class _AdmReport(C.Structure):
+    _fields_ = [("iters", C.c_int), ("converged", C.c_int), ("objective", C.c_double),
+                ("rel_change", C.c_double)]
+
+
+class _PlsParams(C.Structure):
+    _fields_ = [("eta", (C.c_double * 2) * 2), ("gamma", C.c_double), ("edge_tau", C.c_double),
+                ("edge_eps", C.c_double), ("max_iter", C.c_int), ("tol", C.c_double)]
+
+
+class _PlsReport(C.Structure):
+    _fields_ = [("iters", C.c_int * 2), ("relres", C.c_double * 2)]
+
+
+_lib = None
+
+# name: (restype, argtypes) -- every entry point of include/dect.h
+_P = C.c_void_p
+_SIGS = {
+    "dect_plan_create": (C.c_int, [C.POINTER(_Geometry), C.c_int, _P, C.POINTER(_P)]),
+    "dect_plan_destroy": (C.c_int, [_P]),
+    "dect_plan_get_info": (C.c_int, [_P, C.POINTER(_PlanInfo)]),
+    "dect_plan_copy_table": (C.c_int, [_P, _P, _P, _P, _P]),
+    "dect_project": (C.c_int, [_P, _P, _P, C.c_int, _P]),
+    "dect_backproject": (C.c_int, [_P, _P, _P, C.c_int, _P]),
+    "dect_adm_tv": (C.c_int, [_P, _P, _P, C.c_int, C.POINTER(_AdmParams), _P, _P]),
+    "dect_pls_decompose": (C.c_int, [_P, _P, C.c_int, C.c_int, C.POINTER(_PlsParams), _P, _P,
+                                     _P, _P]),
+    "dect_status_string": (C.c_char_p, [C.c_int]),
+    "dect_last_error": (C.c_char_p, []),
+    "dect_version": (C.c_int, []),
+}
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Load libdect.so (compiling it first when it is missing or stale)."""
+    global _lib
+    if _lib is None:
+        if build_if_missing and not _build.up_to_date():
+            _build.build()
+        if not os.path.exists(_build.LIB):
+            raise DectError("libdect.so is not built (run __graft_entry__.build())")
+        lib = C.CDLL(_build.LIB)
+        for name, (res, args) in _SIGS.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+    return _lib
+
+
+def _check(status: int, what: str):
+    if status != 0:
+        lib = load()
+        raise DectError("%s: %s (%s)" % (what, lib.dect_status_string(status).decode(),
+                                         lib.dect_last_error().decode()))
+
+
+def _stream(stream=None):
+    import torch
+    s = torch.cuda.current_stream() if stream is None else stream
+    return C.c_void_p(s.cuda_stream)
+
+
+def _ptr(t, dtype=None, device=None):
+    import torch
+    if not isinstance(t, torch.Tensor):
+        raise TypeError("expected a torch.Tensor")
+    if not t.is_cuda:
+        raise DectError("tensor must live in CUDA device memory")
+    if dtype is not None and t.dtype != dtype:
+        raise DectError("expected dtype %s, got %s" % (dtype, t.dtype))
+    if not t.is_contiguous():
+        raise DectError("tensor must be contiguous")
+    if device is not None and t.device.index != device:
+        raise DectError("tensor on cuda:%d, plan on cuda:%d" % (t.device.index, device))
+    return C.c_void_p(t.data_ptr())
+
+
+@dataclasses.dataclass(frozen=True)
+class Geometry:
+    """Fan-beam slice geometry (Sec. 2.1, Fig. 1).  Units mm / rad."""
+    n: int
+    px: float
+    nv: int
+    nb: int
+    pitch: float
+    sod: float
+    sdd: float
+    start: float = 0.0
+    arc: float = 2.0 * math.pi
+    det_offset: float = 0.0
+
+    @classmethod
+    def of(cls, g) -> "Geometry":
+        return cls(g.n, g.px, g.nv, g.nb, g.pitch, g.sod, g.sdd, g.start, g.arc, g.det_offset)
+
+    def _c(self) -> _Geometry:
+        return _Geometry(self.n, self.px, self.nv, self.nb, self.pitch, self.sod, self.sdd,
+                         self.start, self.arc, self.det_offset)
+
+
+class Plan:
+    """Siddon system matrix of one geometry on one device (dect_plan_*)."""
+
+    def __init__(self, geom, device: int = 0, stream=None):
+        import torch
+        self.geom = Geometry.of(geom)
+        self.device = device
+        lib = load()
+        h = C.c_void_p()
+        with torch.cuda.device(device):
+            _check(lib.dect_plan_create(C.byref(self.geom._c()), device, _stream(stream),
+                                        C.byref(h)), "dect_plan_create")
+        self._h = h
+        info = _PlanInfo()
+        _check(lib.dect_plan_get_info(h, C.byref(info)), "dect_plan_get_info")
+        self.nnz = int(info.nnz)
+        self.table_bytes = int(info.table_bytes)
+        self.n_grid_aligned = int(info.n_grid_aligned)
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().dect_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def table(self):
+        """(rowptr int64 [M+1], pix int32 [nnz], len float32 [nnz]) as numpy arrays."""
+        import numpy as np
+        M = self.geom.nv * self.geom.nb
+        rowptr = np.zeros(M + 1, np.int64)
+        pix = np.zeros(max(self.nnz, 1), np.int32)
+        ln = np.zeros(max(self.nnz, 1), np.float32)
+        _check(load().dect_plan_copy_table(self._h, rowptr.ctypes.data, pix.ctypes.data,
+                                           ln.ctypes.data, _stream()), "dect_plan_copy_table")
+        return rowptr, pix[:self.nnz], ln[:self.nnz]
+
+
+def project(plan: Plan, x, y=None, stream=None):
+    """y = A x for x [..., n, n] float32 CUDA -> y [..., nv, nb] (Eq. (1))."""
+    import torch
+    g = plan.geom
+    batch = x.numel() // (g.n * g.n)
+    if x.shape[-2:] != (g.n, g.n):
+        raise DectError("x must end in (n, n)")
+    if y is None:
+        y = torch.empty(x.shape[:-2] + (g.nv, g.nb), device=x.device, dtype=torch.float32)
+    _check(load().dect_project(plan.handle, _ptr(x, torch.float32, plan.device),
+                               _ptr(y, torch.float32, plan.device), batch, _stream(stream)),
+           "dect_project")
+    return y
+
+
+def backproject(plan: Plan, y, x=None, stream=None):
+    """x = A^T y for y [..., nv, nb] float32 CUDA -> x [..., n, n] (transpose in G_f, Eq. (9))."""
+    import torch
+    g = plan.geom
+    if y.shape[-2:] != (g.nv, g.nb):
+        raise DectError("y must end in (nv, nb)")
+    batch = y.numel() // (g.nv * g.nb)
+    if x is None:
+        x = torch.empty(y.shape[:-2] + (g.n, g.n), device=y.device, dtype=torch.float32)
+    _check(load().dect_backproject(plan.handle, _ptr(y, torch.float32, plan.device),
+                                   _ptr(x, torch.float32, plan.device), batch, _stream(stream)),
+           "dect_backproject")
+    return x
+
+
+BB1, CAUCHY = 0, 1
+
+
+@dataclasses.dataclass
+class AdmParams:
+    """Parameters of Eq. (3)-(10); see dect_adm_params in include/dect.h."""
+    mu: float = 16.0
+    rho: float = 256.0
+    xi: float = 0.0                     # <= 0: xi = rho
+    beta: Tuple[float, float] = (1.0, 0.6)
+    step_rule: int = CAUCHY
+    max_iter: int = 100
+    rel_obj_tol: float = 0.0
+    check_every: int = 10
+    warm_start: bool = False
+
+    def _c(self) -> _AdmParams:
+        b = (C.c_double * 2)(*self.beta)
+        return _AdmParams(self.mu, self.rho, self.xi, b, self.step_rule, self.max_iter,
+                          self.rel_obj_tol, self.check_every, 1 if self.warm_start else 0)
+
+
+@dataclasses.dataclass
+class AdmReport:
+    iters: int
+    converged: bool
+    objective: float
+    rel_change: float
+
+
+def adm_tv(plan: Plan, m, params: AdmParams, x=None, stream=None):
+    """ADM-TV reconstruction (Eq. (3)-(10)) of slices sharing `plan`.
+
+    m: [S, 2, nv, nb] float32 CUDA (energy 0 = high, 1 = low).  Returns
+    (x [S, 2, n, n], reports[S * 2]).
+    """
+    import torch
+    g = plan.geom
+    if m.dim() != 4 or m.shape[1:] != (2, g.nv, g.nb):
+        raise DectError("m must be [S, 2, nv, nb]")
+    S = m.shape[0]
+    if x is None:
+        x = torch.zeros((S, 2, g.n, g.n), device=m.device, dtype=torch.float32)
+    rep = (_AdmReport * max(2 * S, 1))()
+    _check(load().dect_adm_tv(plan.handle, _ptr(m, torch.float32, plan.device),
+                              _ptr(x, torch.float32, plan.device), S, C.byref(params._c()),
+                              C.cast(rep, C.c_void_p), _stream(stream)), "dect_adm_tv")
+    reps = [AdmReport(r.iters, bool(r.converged), r.objective, r.rel_change) for r in rep[:2 * S]]
+    return x, reps
+
+
+@dataclasses.dataclass
+class PlsParams:
+    """Parameters of Eq. (11)-(15); see dect_pls_params in include/dect.h."""
+    eta: Sequence[Sequence[float]] = ((0.0184, 0.0227), (0.0342, 0.0573))
+    gamma: float = 0.1
+    edge_tau: float = 0.2
+    edge_eps: float = 0.05
+    max_iter: int = 500
+    tol: float = 1e-6
+
+    def _c(self) -> _PlsParams:
+        e = ((C.c_double * 2) * 2)()
+        for i in range(2):
+            for j in range(2):
+                e[i][j] = self.eta[i][j]
+        return _PlsParams(e, self.gamma, self.edge_tau, self.edge_eps, self.max_iter, self.tol)
+
+
+def pls_decompose(xh, xl, params: PlsParams, u1=None, u2=None, stream=None):
+    """PLS decomposition (Eq. (11)-(15)): xh, xl [B, n, n] -> (u1, u2, reports)."""
+    import torch
+    if xh.shape != xl.shape or xh.dim() < 2 or xh.shape[-1] != xh.shape[-2]:
+        raise DectError("xh, xl must be [..., n, n] of equal shape")
+    n = xh.shape[-1]
+    batch = xh.numel() // (n * n)
+    if u1 is None:
+        u1 = torch.empty_like(xh)
+    if u2 is None:
+        u2 = torch.empty_like(xh)
+    dev = xh.device.index
+    rep = (_PlsReport * max(batch, 1))()
+    _check(load().dect_pls_decompose(_ptr(xh, torch.float32, dev), _ptr(xl, torch.float32, dev), n,
+                                     batch, C.byref(params._c()), _ptr(u1, torch.float32, dev),
+                                     _ptr(u2, torch.float32, dev), C.cast(rep, C.c_void_p),
+                                     _stream(stream)), "dect_pls_decompose")
+    reps = [(tuple(r.iters), tuple(r.relres)) for r in rep[:batch]]
+    return u1, u2, reps

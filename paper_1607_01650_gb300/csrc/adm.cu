@@ -1,0 +1,608 @@
+// ADM-TV reconstruction, Eq. (3)-(10) (Sec. 2.2), for a batch of images that
+// share one plan.
+//
+// Each channel c (slice s, energy e) solves min |grad f|_TV + mu/2 |A f - g|^2
+// with f = beta_e x, g = beta_e m (Eq. (3)-(4); the TV is taken per channel,
+// so the stacked problem separates).  Iteration k of Eq. (10):
+//   z^{k+1}      = shrink(grad f^k - lambda^k / rho, 1/rho)           Eq. (8)
+//   G^k          = mu A^T r^k + grad^T p,  p = rho(grad f^k - z^{k+1}) - lambda^k
+//                  (= mu A^T(A f - g) + rho grad^T(grad f - z) - grad^T lambda, Eq. (9))
+//   alpha^k      = exact step c(G^k) = |G|^2 / (mu |A G|^2 + rho |grad G|^2)
+//                  (CAUCHY) or the lagged c(G^{k-1}) (BB1)
+//   f^{k+1}      = f^k - alpha^k G^k,   r^{k+1} = r^k - alpha^k A G^k  Eq. (9)
+//   lambda^{k+1} = lambda^k - xi (grad f^{k+1} - z^{k+1})             Eq. (7)
+// The residual r = A f - g is carried by linearity, so an iteration costs one
+// A^T (of r) and one A (of G).  The lambda step of iteration k is applied at
+// the start of iteration k+1, where grad f^{k+1} is formed anyway.
+//
+// Layout: up to 32 channels are interleaved pixel-major, f[pixel][NB], so a
+// table entry gathers one contiguous vector of all channels.
+//
+// Kernel sequence per iteration (captured in a CUDA graph):
+//   k_step   f -= alpha G, r -= alpha q                 ; |r|^2
+//   k_tv     lambda step, z-shrink, p                    ; |grad f|_TV
+//   k_bwd    G = mu A^T r + grad^T p  (pixel-major table) ; |G|^2
+//   k_gnorm                                              ; |grad G|^2
+//   k_fwd    q = A G  (ray-major table)                  ; |q|^2, then the
+//            last block forms Phi^k, the stopping test and alpha^k in FP64.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "dect_internal.cuh"
+#include "kernels.cuh"
+
+namespace dect {
+namespace {
+
+constexpr int kBlock = 256;
+constexpr int kGrid = kSMs * 8;  // fixed grid of every reducing kernel
+
+enum { R_RR = 0, R_TV, R_GG, R_DD, R_QQ, R_COUNT };
+
+struct AdmDev {
+    // per-channel scalars
+    double *red;       // [R_COUNT][NB] reduction results
+    double *part;      // [R_COUNT][kGrid][NB] block partials
+    unsigned *ctr;     // [R_COUNT] last-block counters
+    double *alpha;     // [NB] step applied by the next k_step
+    double *c_prev;    // [NB]
+    double *phi_prev;  // [NB]
+    double *rel;       // [NB]
+    int *iters;        // [NB]
+    int *conv;         // [NB]
+    int *active;       // [NB]
+    int *k;            // iteration counter
+    int *all_done;     // 1 once no channel is active
+    int *bad;          // 1 once a non-finite objective was seen
+};
+
+struct AdmConst {
+    int n;
+    int64_t N, M;
+    float mu, rho, xi;   // FP32 copies for the bulk kernels
+    double mu_d, rho_d;  // FP64 for the step and objective
+    double tol;
+    int rule;
+    int nimg;
+};
+
+// ---------------------------------------------------------------------------
+template <int NB>
+__global__ void __launch_bounds__(kBlock) k_step(float *__restrict__ f, const float *__restrict__ G,
+                                                 float *__restrict__ r, const float *__restrict__ q,
+                                                 AdmConst C, AdmDev D)
+{
+    constexpr int VW = Batch<NB>::VW, CPB = Batch<NB>::CPB;
+    __shared__ double smem[(kBlock / 32) * NB];
+    const int vl = threadIdx.x % CPB;
+    Vec<VW> a;
+#pragma unroll
+    for (int c = 0; c < VW; ++c) a.v[c] = (float)D.alpha[vl * VW + c];
+    Vec<VW> acc;
+    acc.zero();
+    const int64_t total = (C.N + C.M) * CPB;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        if (t < C.N * CPB) {
+            float *fp = f + t * VW;
+            Vec<VW> fv = ld_v<VW>(fp), gv = ld_v<VW>(G + t * VW);
+#pragma unroll
+            for (int c = 0; c < VW; ++c) fv.v[c] = fmaf(-a.v[c], gv.v[c], fv.v[c]);
+            st_v<VW>(fp, fv);
+        } else {
+            int64_t u = t - C.N * CPB;
+            float *rp = r + u * VW;
+            Vec<VW> rv = ld_v<VW>(rp), qv = ld_v<VW>(q + u * VW);
+#pragma unroll
+            for (int c = 0; c < VW; ++c) {
+                rv.v[c] = fmaf(-a.v[c], qv.v[c], rv.v[c]);
+                acc.v[c] = fmaf(rv.v[c], rv.v[c], acc.v[c]);
+            }
+            st_v<VW>(rp, rv);
+        }
+    }
+    reduce_images<NB>(acc, D.part + (size_t)R_RR * kGrid * NB, D.red + R_RR * NB, D.ctr + R_RR, smem);
+}
+
+// z-shrink of Eq. (8) per pixel on the 2-vector w (reading: w / |w| for sign).
+__device__ __forceinline__ void shrink2(float w0, float w1, float t, float &z0, float &z1)
+{
+    float nrm = sqrtf(w0 * w0 + w1 * w1);
+    float s = nrm - t;
+    if (s > 0.f && nrm > 0.f) {
+        float k = s / nrm;
+        z0 = k * w0;
+        z1 = k * w1;
+    } else {
+        z0 = 0.f;
+        z1 = 0.f;
+    }
+}
+
+template <int NB>
+__global__ void __launch_bounds__(kBlock) k_tv(const float *__restrict__ f, float *__restrict__ lam,
+                                               float *__restrict__ z, float *__restrict__ p,
+                                               AdmConst C, AdmDev D, int final_pass)
+{
+    constexpr int VW = Batch<NB>::VW, CPB = Batch<NB>::CPB;
+    __shared__ double smem[(kBlock / 32) * NB];
+    const int k = *D.k;
+    const float inv_rho = 1.0f / C.rho;
+    Vec<VW> acc;
+    acc.zero();
+    const int64_t total = C.N * CPB;
+    const int64_t sN = C.N * NB;  // component stride of lam, z, p
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t pix = t / CPB;
+        const int vl = (int)(t % CPB);
+        const int i = (int)(pix / C.n), j = (int)(pix % C.n);
+        const int64_t o = pix * NB + vl * VW;
+        Vec<VW> fc = ld_v<VW>(f + o), fu, fl;
+        if (i > 0) fu = ld_v<VW>(f + o - (int64_t)C.n * NB); else fu = fc;
+        if (j > 0) fl = ld_v<VW>(f + o - NB); else fl = fc;
+        Vec<VW> l0, l1, z0, z1;
+        if (!final_pass) {
+            l0 = ld_v<VW>(lam + o);
+            l1 = ld_v<VW>(lam + sN + o);
+            if (k > 0) {
+                z0 = ld_v<VW>(z + o);
+                z1 = ld_v<VW>(z + sN + o);
+            }
+        }
+        Vec<VW> p0, p1;
+#pragma unroll
+        for (int c = 0; c < VW; ++c) {
+            float g0 = fc.v[c] - fu.v[c];   // Eq. (2), 0 on the first row
+            float g1 = fc.v[c] - fl.v[c];   // Eq. (2), 0 on the first column
+            acc.v[c] += sqrtf(g0 * g0 + g1 * g1);
+            if (final_pass) continue;
+            float a0 = l0.v[c], a1 = l1.v[c];
+            if (k > 0) {  // lambda^k = lambda^{k-1} - xi (grad f^k - z^k), Eq. (7)
+                a0 -= C.xi * (g0 - z0.v[c]);
+                a1 -= C.xi * (g1 - z1.v[c]);
+            }
+            float s0, s1;
+            shrink2(g0 - a0 * inv_rho, g1 - a1 * inv_rho, inv_rho, s0, s1);
+            l0.v[c] = a0;
+            l1.v[c] = a1;
+            z0.v[c] = s0;
+            z1.v[c] = s1;
+            p0.v[c] = C.rho * (g0 - s0) - a0;
+            p1.v[c] = C.rho * (g1 - s1) - a1;
+        }
+        if (!final_pass) {
+            st_v<VW>(lam + o, l0);
+            st_v<VW>(lam + sN + o, l1);
+            st_v<VW>(z + o, z0);
+            st_v<VW>(z + sN + o, z1);
+            st_v<VW>(p + o, p0);
+            st_v<VW>(p + sN + o, p1);
+        }
+    }
+    reduce_images<NB>(acc, D.part + (size_t)R_TV * kGrid * NB, D.red + R_TV * NB, D.ctr + R_TV, smem);
+}
+
+// G = mu A^T r + grad^T p over the pixel-major table (one row = one pixel).
+template <int NB, int G_>
+__global__ void __launch_bounds__(kBlock) k_bwd(const int64_t *__restrict__ colptr,
+                                                const Entry *__restrict__ tent,
+                                                const float *__restrict__ r, const float *__restrict__ p,
+                                                float *__restrict__ G, AdmConst C, AdmDev D)
+{
+    constexpr int VW = Batch<NB>::VW, LPE = Batch<NB>::CPB;
+    __shared__ double smem[(kBlock / 32) * NB];
+    const int lr = threadIdx.x % G_, grp = lr / LPE, vl = lr % LPE;
+    const int64_t rpb = kBlock / G_;
+    const int64_t sN = C.N * NB;
+    Vec<VW> nrm;
+    nrm.zero();
+    for (int64_t row0 = (int64_t)blockIdx.x * rpb; row0 < C.N; row0 += (int64_t)gridDim.x * rpb) {
+        const int64_t pix = row0 + threadIdx.x / G_;
+        int64_t b = 0, e = 0;
+        if (pix < C.N) {
+            b = colptr[pix];
+            e = colptr[pix + 1];
+        }
+        Vec<VW> acc = row_dot<NB, G_, true>(tent, b, e, r, 0, lr);
+        if (pix < C.N && grp == 0) {
+            const int i = (int)(pix / C.n), j = (int)(pix % C.n);
+            const int64_t o = pix * NB + vl * VW;
+            Vec<VW> p0 = ld_v<VW>(p + o), p1 = ld_v<VW>(p + sN + o), pd, pr;
+            if (i + 1 < C.n) pd = ld_v<VW>(p + o + (int64_t)C.n * NB); else pd.zero();
+            if (j + 1 < C.n) pr = ld_v<VW>(p + sN + o + NB); else pr.zero();
+            Vec<VW> out;
+#pragma unroll
+            for (int c = 0; c < VW; ++c) {
+                float gt = (i > 0 ? p0.v[c] : 0.f) - pd.v[c] + (j > 0 ? p1.v[c] : 0.f) - pr.v[c];
+                out.v[c] = fmaf(C.mu, acc.v[c], gt);
+                nrm.v[c] = fmaf(out.v[c], out.v[c], nrm.v[c]);
+            }
+            st_v<VW>(G + o, out);
+        }
+    }
+    reduce_images<NB>(nrm, D.part + (size_t)R_GG * kGrid * NB, D.red + R_GG * NB, D.ctr + R_GG, smem);
+}
+
+template <int NB>
+__global__ void __launch_bounds__(kBlock) k_gnorm(const float *__restrict__ G, AdmConst C, AdmDev D)
+{
+    constexpr int VW = Batch<NB>::VW, CPB = Batch<NB>::CPB;
+    __shared__ double smem[(kBlock / 32) * NB];
+    Vec<VW> acc;
+    acc.zero();
+    const int64_t total = C.N * CPB;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t pix = t / CPB;
+        const int vl = (int)(t % CPB);
+        const int i = (int)(pix / C.n), j = (int)(pix % C.n);
+        const int64_t o = pix * NB + vl * VW;
+        Vec<VW> gc = ld_v<VW>(G + o), gu, gl;
+        if (i > 0) gu = ld_v<VW>(G + o - (int64_t)C.n * NB); else gu = gc;
+        if (j > 0) gl = ld_v<VW>(G + o - NB); else gl = gc;
+#pragma unroll
+        for (int c = 0; c < VW; ++c) {
+            float d0 = gc.v[c] - gu.v[c], d1 = gc.v[c] - gl.v[c];
+            acc.v[c] += d0 * d0 + d1 * d1;
+        }
+    }
+    reduce_images<NB>(acc, D.part + (size_t)R_DD * kGrid * NB, D.red + R_DD * NB, D.ctr + R_DD, smem);
+}
+
+// Step size and stopping test, FP64, one thread per channel (last block of k_fwd).
+template <int NB>
+__device__ void adm_finish(const AdmConst &C, const AdmDev &D)
+{
+    const int k = *D.k;
+    if (threadIdx.x < NB) {
+        const int b = threadIdx.x;
+        double alpha = 0.0;
+        if (D.active[b]) {
+            const double phi = D.red[R_TV * NB + b] + 0.5 * C.mu_d * D.red[R_RR * NB + b];
+            if (!isfinite(phi)) *D.bad = 1;
+            bool stop = false;
+            if (k > 0) {
+                const double prev = D.phi_prev[b];
+                const double rel = prev > 0.0 ? fabs(phi - prev) / prev : 0.0;
+                D.rel[b] = rel;
+                if (C.tol > 0.0 && rel < C.tol) stop = true;
+            }
+            if (stop) {
+                D.active[b] = 0;
+                D.conv[b] = 1;
+                D.iters[b] = k;
+            } else {
+                D.phi_prev[b] = phi;
+                const double gg = D.red[R_GG * NB + b], qq = D.red[R_QQ * NB + b],
+                             dd = D.red[R_DD * NB + b];
+                const double den = C.mu_d * qq + C.rho_d * dd;
+                const double c = den > 0.0 ? gg / den : 0.0;
+                alpha = (C.rule == DECT_STEP_CAUCHY || k == 0) ? c : D.c_prev[b];
+                D.c_prev[b] = c;
+                D.iters[b] = k + 1;
+            }
+        }
+        D.alpha[b] = alpha;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int any = 0;
+        for (int b = 0; b < NB; ++b) any |= D.active[b];
+        *D.all_done = any ? 0 : 1;
+        *D.k = k + 1;
+    }
+}
+
+// q = A G over the ray-major table (MODE 1), or r = A f - beta m (MODE 0).
+template <int NB, int G_, int MODE>
+__global__ void __launch_bounds__(kBlock) k_fwd(const int64_t *__restrict__ rowptr,
+                                                const Entry *__restrict__ ent,
+                                                const float *__restrict__ src, float *__restrict__ dst,
+                                                const float *__restrict__ m_planar,
+                                                const float *__restrict__ beta_img, AdmConst C, AdmDev D)
+{
+    constexpr int VW = Batch<NB>::VW, LPE = Batch<NB>::CPB;
+    __shared__ double smem[(kBlock / 32) * NB];
+    const int lr = threadIdx.x % G_, grp = lr / LPE, vl = lr % LPE;
+    const int64_t rpb = kBlock / G_;
+    Vec<VW> nrm;
+    nrm.zero();
+    for (int64_t row0 = (int64_t)blockIdx.x * rpb; row0 < C.M; row0 += (int64_t)gridDim.x * rpb) {
+        const int64_t ray = row0 + threadIdx.x / G_;
+        int64_t b = 0, e = 0;
+        if (ray < C.M) {
+            b = rowptr[ray];
+            e = rowptr[ray + 1];
+        }
+        Vec<VW> acc = row_dot<NB, G_, true>(ent, b, e, src, 0, lr);
+        if (ray < C.M && grp == 0) {
+            if (MODE == 0) {
+#pragma unroll
+                for (int c = 0; c < VW; ++c) {
+                    const int img = vl * VW + c;
+                    float g = img < C.nimg ? beta_img[img] * m_planar[(int64_t)img * C.M + ray] : 0.f;
+                    acc.v[c] -= g;
+                }
+            } else {
+#pragma unroll
+                for (int c = 0; c < VW; ++c) nrm.v[c] = fmaf(acc.v[c], acc.v[c], nrm.v[c]);
+            }
+            st_v<VW>(dst + ray * NB + vl * VW, acc);
+        }
+    }
+    if (MODE == 1) {
+        if (reduce_images<NB>(nrm, D.part + (size_t)R_QQ * kGrid * NB, D.red + R_QQ * NB,
+                              D.ctr + R_QQ, smem))
+            adm_finish<NB>(C, D);
+    }
+}
+
+// planar x[img][N] (times beta) -> interleaved f[N][NB]; and back (divided by beta).
+template <int NB>
+__global__ void k_pack(const float *__restrict__ x, float *__restrict__ f, int64_t N, int nimg,
+                       const float *__restrict__ beta_img)
+{
+    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= N * NB) return;
+    int64_t pix = t / NB;
+    int img = (int)(t % NB);
+    f[t] = img < nimg ? beta_img[img] * x[(int64_t)img * N + pix] : 0.f;
+}
+
+template <int NB>
+__global__ void k_unpack(const float *__restrict__ f, float *__restrict__ x, int64_t N, int nimg,
+                         const float *__restrict__ beta_img)
+{
+    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= N * NB) return;
+    int64_t pix = t / NB;
+    int img = (int)(t % NB);
+    if (img < nimg) x[(int64_t)img * N + pix] = f[t] / beta_img[img];
+}
+
+// ---------------------------------------------------------------------------
+// Host side
+// ---------------------------------------------------------------------------
+template <int NB>
+struct Kern {
+    static constexpr int GB = NB >= 32 ? 32 : 16;  // lanes per pixel row
+    static constexpr int GF = 32;                  // lanes per ray row
+};
+
+struct Work {
+    float *f, *G, *lam, *z, *p, *r, *q, *beta;
+    double *dbl;
+    int *ints;
+    unsigned *ctr;
+    AdmDev D;
+};
+
+template <int NB>
+void enqueue_iteration(const dect_plan *P, const Work &W, const AdmConst &C, cudaStream_t s)
+{
+    k_step<NB><<<kGrid, kBlock, 0, s>>>(W.f, W.G, W.r, W.q, C, W.D);
+    k_tv<NB><<<kGrid, kBlock, 0, s>>>(W.f, W.lam, W.z, W.p, C, W.D, 0);
+    k_bwd<NB, Kern<NB>::GB><<<kGrid, kBlock, 0, s>>>(P->colptr, P->tent, W.r, W.p, W.G, C, W.D);
+    k_gnorm<NB><<<kGrid, kBlock, 0, s>>>(W.G, C, W.D);
+    k_fwd<NB, Kern<NB>::GF, 1><<<kGrid, kBlock, 0, s>>>(P->rowptr, P->ent, W.G, W.q, nullptr, nullptr,
+                                                         C, W.D);
+}
+
+template <int NB>
+dect_status run_chunk(const dect_plan *P, const float *m, float *x, int nimg,
+                      const dect_adm_params *prm, const float *beta_host, dect_adm_report *rep,
+                      cudaStream_t s)
+{
+    const int64_t N = P->N, M = P->M;
+    AdmConst C;
+    C.n = P->n;
+    C.N = N;
+    C.M = M;
+    C.mu = (float)prm->mu;
+    C.rho = (float)prm->rho;
+    double xi = prm->xi > 0 ? prm->xi : prm->rho;
+    C.xi = (float)xi;
+    C.mu_d = prm->mu;
+    C.rho_d = prm->rho;
+    C.tol = prm->rel_obj_tol;
+    C.rule = prm->step_rule;
+    C.nimg = nimg;
+
+    // one allocation for everything
+    const size_t nf = (size_t)N * NB, nr = (size_t)M * NB;
+    const size_t floats = nf * (1 + 1 + 2 + 2 + 2) + nr * 2 + 64;
+    const size_t ndbl = (size_t)R_COUNT * NB + (size_t)R_COUNT * kGrid * NB + 4 * NB;
+    const size_t nint = 4 * NB + 8;
+    const size_t bytes = floats * 4 + ndbl * 8 + nint * 4 + R_COUNT * 4 + 1024;
+    char *base = nullptr;
+    DECT_CUDA(cudaMallocAsync((void **)&base, bytes, s));
+    auto align = [](size_t o) { return (o + 255) & ~(size_t)255; };
+    size_t o = 0;
+    Work W;
+    auto takef = [&](size_t cnt) { float *ptr = (float *)(base + o); o = align(o + cnt * 4); return ptr; };
+    W.f = takef(nf);
+    W.G = takef(nf);
+    W.lam = takef(2 * nf);
+    W.z = takef(2 * nf);
+    W.p = takef(2 * nf);
+    W.r = takef(nr);
+    W.q = takef(nr);
+    W.beta = takef(64);
+    W.dbl = (double *)(base + o);
+    o = align(o + ndbl * 8);
+    W.ints = (int *)(base + o);
+    o = align(o + nint * 4);
+    W.ctr = (unsigned *)(base + o);
+    o = align(o + R_COUNT * 4);
+    size_t used_end = o;
+    (void)used_end;
+
+    AdmDev &D = W.D;
+    D.red = W.dbl;
+    D.part = D.red + R_COUNT * NB;
+    D.alpha = D.part + (size_t)R_COUNT * kGrid * NB;
+    D.c_prev = D.alpha + NB;
+    D.phi_prev = D.c_prev + NB;
+    D.rel = D.phi_prev + NB;
+    D.iters = W.ints;
+    D.conv = D.iters + NB;
+    D.active = D.conv + NB;
+    D.k = D.active + NB;
+    D.all_done = D.k + 1;
+    D.bad = D.all_done + 1;
+    D.ctr = W.ctr;
+
+    std::vector<float> hbeta(64, 1.f);
+    std::vector<int> hact(NB, 0);
+    for (int b = 0; b < nimg; ++b) {
+        hbeta[b] = beta_host[b];
+        hact[b] = 1;
+    }
+    // zero state; G = q = 0 and alpha = 0 make the first k_step a no-op
+    DECT_CUDA(cudaMemsetAsync(base, 0, bytes, s));
+    DECT_CUDA(cudaMemcpyAsync(W.beta, hbeta.data(), 64 * 4, cudaMemcpyHostToDevice, s));
+    DECT_CUDA(cudaMemcpyAsync(D.active, hact.data(), NB * 4, cudaMemcpyHostToDevice, s));
+
+    const int64_t tn = (int64_t)N * NB;
+    if (prm->warm_start) {
+        k_pack<NB><<<(unsigned)((tn + 255) / 256), 256, 0, s>>>(x, W.f, N, nimg, W.beta);
+        DECT_LAUNCH_CHECK();
+    }
+    // r^0 = A f^0 - beta m
+    k_fwd<NB, Kern<NB>::GF, 0><<<kGrid, kBlock, 0, s>>>(P->rowptr, P->ent, W.f, W.r, m, W.beta, C, D);
+    DECT_LAUNCH_CHECK();
+
+    // iterations: CUDA graphs of `block` iterations
+    const int K = prm->max_iter;
+    const bool use_tol = prm->rel_obj_tol > 0.0;
+    int block = use_tol ? (prm->check_every > 0 ? prm->check_every : 10) : 10;
+    block = std::max(1, std::min(block, std::max(K, 1)));
+    cudaStream_t cs = nullptr;
+    DECT_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    cudaEvent_t ev = nullptr;
+    DECT_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+    auto cleanup = [&]() {
+        if (ev) cudaEventDestroy(ev);
+        if (cs) cudaStreamDestroy(cs);
+    };
+    cudaGraphExec_t gx_block = nullptr, gx_one = nullptr;
+    auto make_graph = [&](int iters, cudaGraphExec_t *out) -> cudaError_t {
+        cudaGraph_t gr = nullptr;
+        cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) return e;
+        for (int it = 0; it < iters; ++it) enqueue_iteration<NB>(P, W, C, cs);
+        e = cudaStreamEndCapture(cs, &gr);
+        if (e != cudaSuccess) return e;
+        e = cudaGraphInstantiate(out, gr, 0);
+        cudaGraphDestroy(gr);
+        return e;
+    };
+    // the caller's stream orders the set-up; the capture stream runs the loop
+    cudaError_t err = cudaEventRecord(ev, s);
+    if (err == cudaSuccess) err = cudaStreamWaitEvent(cs, ev, 0);
+    if (err == cudaSuccess && K >= block) err = make_graph(block, &gx_block);
+    if (err == cudaSuccess && K % block) err = make_graph(1, &gx_one);
+    int *h_done = nullptr;
+    if (err == cudaSuccess) err = cudaMallocHost((void **)&h_done, sizeof(int));
+    int done_iters = 0;
+    while (err == cudaSuccess && done_iters + block <= K) {
+        err = cudaGraphLaunch(gx_block, cs);
+        done_iters += block;
+        if (err == cudaSuccess && use_tol) {
+            err = cudaMemcpyAsync(h_done, D.all_done, sizeof(int), cudaMemcpyDeviceToHost, cs);
+            if (err == cudaSuccess) err = cudaStreamSynchronize(cs);
+            if (err == cudaSuccess && *h_done) break;
+        }
+    }
+    bool finished = use_tol && err == cudaSuccess && *h_done;
+    while (err == cudaSuccess && !finished && done_iters < K) {
+        err = cudaGraphLaunch(gx_one, cs);
+        ++done_iters;
+    }
+    // final update f^K = f^{K-1} - alpha G and the objective at the result
+    if (err == cudaSuccess) {
+        k_step<NB><<<kGrid, kBlock, 0, cs>>>(W.f, W.G, W.r, W.q, C, D);
+        k_tv<NB><<<kGrid, kBlock, 0, cs>>>(W.f, W.lam, W.z, W.p, C, D, 1);
+        k_unpack<NB><<<(unsigned)((tn + 255) / 256), 256, 0, cs>>>(W.f, x, N, nimg, W.beta);
+        err = cudaGetLastError();
+    }
+    if (err == cudaSuccess) err = cudaEventRecord(ev, cs);
+    if (err == cudaSuccess) err = cudaStreamWaitEvent(s, ev, 0);
+
+    std::vector<double> hred(R_COUNT * NB), hrel(NB);
+    std::vector<int> hit(NB), hconv(NB);
+    int hbad = 0;
+    if (err == cudaSuccess) err = cudaMemcpyAsync(hred.data(), D.red, sizeof(double) * R_COUNT * NB, cudaMemcpyDeviceToHost, s);
+    if (err == cudaSuccess) err = cudaMemcpyAsync(hrel.data(), D.rel, sizeof(double) * NB, cudaMemcpyDeviceToHost, s);
+    if (err == cudaSuccess) err = cudaMemcpyAsync(hit.data(), D.iters, sizeof(int) * NB, cudaMemcpyDeviceToHost, s);
+    if (err == cudaSuccess) err = cudaMemcpyAsync(hconv.data(), D.conv, sizeof(int) * NB, cudaMemcpyDeviceToHost, s);
+    if (err == cudaSuccess) err = cudaMemcpyAsync(&hbad, D.bad, sizeof(int), cudaMemcpyDeviceToHost, s);
+    cudaFreeAsync(base, s);
+    if (err == cudaSuccess) err = cudaStreamSynchronize(s);
+    if (gx_block) cudaGraphExecDestroy(gx_block);
+    if (gx_one) cudaGraphExecDestroy(gx_one);
+    if (h_done) cudaFreeHost(h_done);
+    cleanup();
+    if (err != cudaSuccess) {
+        set_error("dect_adm_tv", err);
+        return err == cudaErrorMemoryAllocation ? DECT_ERR_OOM : DECT_ERR_CUDA;
+    }
+    if (rep) {
+        for (int b = 0; b < nimg; ++b) {
+            rep[b].iters = K == 0 ? 0 : hit[b];
+            rep[b].converged = hconv[b];
+            rep[b].objective = hred[R_TV * NB + b] + 0.5 * prm->mu * hred[R_RR * NB + b];
+            rep[b].rel_change = hrel[b];
+        }
+    }
+    return hbad ? DECT_ERR_NONFINITE : DECT_OK;
+}
+
+}  // namespace
+}  // namespace dect
+
+using namespace dect;
+
+extern "C" dect_status dect_adm_tv(const dect_plan *plan, const float *m, float *x, int n_slices,
+                                   const dect_adm_params *prm, dect_adm_report *reports,
+                                   dect_stream stream)
+{
+    if (!plan || !prm || n_slices < 0) return DECT_ERR_INVALID_ARG;
+    if (n_slices == 0) return DECT_OK;
+    if (!m || !x) return DECT_ERR_INVALID_ARG;
+    if (!(prm->mu > 0) || !(prm->rho > 0) || !(prm->beta[0] > 0) || !(prm->beta[1] > 0) ||
+        prm->max_iter < 0 || (prm->step_rule != DECT_STEP_BB1 && prm->step_rule != DECT_STEP_CAUCHY) ||
+        !std::isfinite(prm->mu) || !std::isfinite(prm->rho) || !std::isfinite(prm->xi) ||
+        prm->check_every < 0)
+        return DECT_ERR_INVALID_ARG;
+    DECT_CUDA(cudaSetDevice(plan->device));
+    cudaStream_t s = (cudaStream_t)stream;
+    const int total = 2 * n_slices;
+    dect_status worst = DECT_OK;
+    for (int c0 = 0; c0 < total; c0 += kMaxBatchImages) {
+        const int nimg = std::min(kMaxBatchImages, total - c0);
+        std::vector<float> beta(nimg);
+        for (int b = 0; b < nimg; ++b) beta[b] = (float)prm->beta[(c0 + b) % 2];
+        const float *mc = m + (int64_t)c0 * plan->M;
+        float *xc = x + (int64_t)c0 * plan->N;
+        dect_adm_report *rc = reports ? reports + c0 : nullptr;
+        dect_status st;
+        if (nimg <= 2)
+            st = run_chunk<2>(plan, mc, xc, nimg, prm, beta.data(), rc, s);
+        else if (nimg <= 4)
+            st = run_chunk<4>(plan, mc, xc, nimg, prm, beta.data(), rc, s);
+        else if (nimg <= 8)
+            st = run_chunk<8>(plan, mc, xc, nimg, prm, beta.data(), rc, s);
+        else if (nimg <= 16)
+            st = run_chunk<16>(plan, mc, xc, nimg, prm, beta.data(), rc, s);
+        else
+            st = run_chunk<32>(plan, mc, xc, nimg, prm, beta.data(), rc, s);
+        if (st == DECT_ERR_NONFINITE) worst = st;
+        else if (st != DECT_OK) return st;
+    }
+    return worst;
+}

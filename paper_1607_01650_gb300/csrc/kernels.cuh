@@ -1,0 +1,203 @@
+// Device building blocks shared by the operator and ADM translation units:
+// the row kernels that stream a table of A (ray-major for A x, pixel-major
+// for A^T y), and the deterministic per-image FP64 reduction.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "dect_internal.cuh"
+
+namespace dect {
+
+// ---------------------------------------------------------------------------
+// Image batches.  NB images are processed together.  In the interleaved
+// layout ("IL") pixel j of image b sits at base[j * NB + b]; in the planar
+// layout at base[b * stride + j].  A thread moves VW consecutive images.
+// ---------------------------------------------------------------------------
+template <int NB>
+struct Batch {
+    static constexpr int VW = NB >= 4 ? 4 : NB;  // floats per vector
+    static constexpr int CPB = NB / VW;          // vectors per pixel
+};
+
+template <int VW>
+struct Vec {
+    float v[VW];
+    __device__ __forceinline__ void zero()
+    {
+#pragma unroll
+        for (int c = 0; c < VW; ++c) v[c] = 0.f;
+    }
+};
+
+template <int VW>
+__device__ __forceinline__ Vec<VW> ld_il(const float *__restrict__ p)
+{
+    Vec<VW> r;
+    if constexpr (VW == 4) {
+        float4 t = __ldg(reinterpret_cast<const float4 *>(p));
+        r.v[0] = t.x; r.v[1] = t.y; r.v[2] = t.z; r.v[3] = t.w;
+    } else if constexpr (VW == 2) {
+        float2 t = __ldg(reinterpret_cast<const float2 *>(p));
+        r.v[0] = t.x; r.v[1] = t.y;
+    } else {
+        r.v[0] = __ldg(p);
+    }
+    return r;
+}
+
+// plain (coherent) load, for data written earlier in the same kernel sequence
+template <int VW>
+__device__ __forceinline__ Vec<VW> ld_v(const float *p)
+{
+    Vec<VW> r;
+    if constexpr (VW == 4) {
+        float4 t = *reinterpret_cast<const float4 *>(p);
+        r.v[0] = t.x; r.v[1] = t.y; r.v[2] = t.z; r.v[3] = t.w;
+    } else if constexpr (VW == 2) {
+        float2 t = *reinterpret_cast<const float2 *>(p);
+        r.v[0] = t.x; r.v[1] = t.y;
+    } else {
+        r.v[0] = *p;
+    }
+    return r;
+}
+
+template <int VW>
+__device__ __forceinline__ void st_v(float *p, const Vec<VW> &a)
+{
+    if constexpr (VW == 4) {
+        *reinterpret_cast<float4 *>(p) = make_float4(a.v[0], a.v[1], a.v[2], a.v[3]);
+    } else if constexpr (VW == 2) {
+        *reinterpret_cast<float2 *>(p) = make_float2(a.v[0], a.v[1]);
+    } else {
+        *p = a.v[0];
+    }
+}
+
+__device__ __forceinline__ Entry ld_entry(const Entry *p)
+{
+    // table entries are read once per pass: stream them past L1
+    return __ldcs(p);
+}
+
+// ---------------------------------------------------------------------------
+// Deterministic per-image reduction: every thread holds VW partial values for
+// images (lane % CPB) * VW + c.  Values are summed in FP32 inside a warp and
+// in FP64 across warps and blocks, always in the same order.  The block that
+// finishes last writes the grid total per image to out[] and returns true
+// (in every thread of that block); `counter` is reset for the next launch.
+// smem must hold (blockDim.x / 32) * NB doubles.
+// ---------------------------------------------------------------------------
+template <int NB>
+__device__ __forceinline__ bool reduce_images(Vec<Batch<NB>::VW> v, double *__restrict__ part,
+                                              double *__restrict__ out, unsigned *counter,
+                                              double *smem)
+{
+    constexpr int VW = Batch<NB>::VW, CPB = Batch<NB>::CPB;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+    for (int off = CPB; off < 32; off <<= 1)
+#pragma unroll
+        for (int c = 0; c < VW; ++c) v.v[c] += __shfl_xor_sync(0xffffffffu, v.v[c], off);
+    if (lane < CPB)
+#pragma unroll
+        for (int c = 0; c < VW; ++c) smem[warp * NB + lane * VW + c] = (double)v.v[c];
+    __syncthreads();
+    if (threadIdx.x < NB) {
+        double s = 0.0;
+        for (int w = 0; w < nw; ++w) s += smem[w * NB + threadIdx.x];
+        part[(size_t)blockIdx.x * NB + threadIdx.x] = s;
+    }
+    __threadfence();
+    __syncthreads();
+    __shared__ bool last;
+    if (threadIdx.x == 0) last = (atomicAdd(counter, 1u) == gridDim.x - 1);
+    __syncthreads();
+    if (!last) return false;
+    __threadfence();
+    if (threadIdx.x < NB) {
+        double s = 0.0;
+        for (unsigned b = 0; b < gridDim.x; ++b) s += __ldcg(&part[(size_t)b * NB + threadIdx.x]);
+        out[threadIdx.x] = s;
+    }
+    if (threadIdx.x == 0) *counter = 0u;
+    __syncthreads();
+    return true;
+}
+
+// ---------------------------------------------------------------------------
+// Row kernel core: one row (a ray of the ray-major table or a pixel of the
+// pixel-major table) is handled by G lanes.  With LPE = CPB lanes per entry
+// (one vector each), a row's entries are split over EG = G / LPE groups,
+// visited in order k = begin + group, + EG, ...; the groups are summed by a
+// fixed xor-butterfly, so the result is bitwise reproducible.
+// After the call, the lanes with group == 0 hold the row's VW sums.
+// ---------------------------------------------------------------------------
+template <int NB, int G, bool IL>
+__device__ __forceinline__ Vec<Batch<NB>::VW> row_dot(const Entry *__restrict__ ent, int64_t b,
+                                                      int64_t e, const float *__restrict__ src,
+                                                      int64_t src_stride, int lr, int nimg = NB)
+{
+    constexpr int VW = Batch<NB>::VW, LPE = Batch<NB>::CPB, EG = G / LPE;
+    static_assert(G % LPE == 0 && G <= 32, "bad row split");
+    const int grp = lr / LPE, vl = lr % LPE;
+    Vec<VW> acc;
+    acc.zero();
+#pragma unroll 4
+    for (int64_t k = b + grp; k < e; k += EG) {
+        Entry t = ld_entry(ent + k);
+        float w = __int_as_float(t.y);
+        Vec<VW> xv;
+        if constexpr (IL) {
+            xv = ld_il<VW>(src + (int64_t)t.x * NB + vl * VW);
+        } else {
+#pragma unroll
+            for (int c = 0; c < VW; ++c) {
+                const int img = vl * VW + c;
+                xv.v[c] = img < nimg ? __ldg(src + (int64_t)img * src_stride + t.x) : 0.f;
+            }
+        }
+#pragma unroll
+        for (int c = 0; c < VW; ++c) acc.v[c] = fmaf(w, xv.v[c], acc.v[c]);
+    }
+#pragma unroll
+    for (int off = LPE; off < G; off <<= 1)
+#pragma unroll
+        for (int c = 0; c < VW; ++c) acc.v[c] += __shfl_xor_sync(0xffffffffu, acc.v[c], off);
+    return acc;
+}
+
+// Plain operator kernel: dst[row] = sum over the row's entries of len * src[index].
+// Planar layout: image i of a batch chunk at src + i * src_stride; only the
+// first nimg <= NB images are read or written.
+template <int NB, int G>
+__global__ void __launch_bounds__(256) k_rows_planar(const int64_t *__restrict__ ptr,
+                                                     const Entry *__restrict__ ent, int64_t rows,
+                                                     const float *__restrict__ src, int64_t src_stride,
+                                                     float *__restrict__ dst, int64_t dst_stride,
+                                                     int nimg)
+{
+    constexpr int VW = Batch<NB>::VW, LPE = Batch<NB>::CPB;
+    const int lr = threadIdx.x % G, grp = lr / LPE, vl = lr % LPE;
+    const int64_t rpb = blockDim.x / G;
+    for (int64_t row0 = (int64_t)blockIdx.x * rpb; row0 < rows; row0 += (int64_t)gridDim.x * rpb) {
+        int64_t row = row0 + threadIdx.x / G;
+        int64_t b = 0, e = 0;
+        if (row < rows) {
+            b = ptr[row];
+            e = ptr[row + 1];
+        }
+        Vec<VW> acc = row_dot<NB, G, false>(ent, b, e, src, src_stride, lr, nimg);
+        if (row < rows && grp == 0) {
+#pragma unroll
+            for (int c = 0; c < VW; ++c) {
+                int img = vl * VW + c;
+                if (img < nimg) dst[(int64_t)img * dst_stride + row] = acc.v[c];
+            }
+        }
+    }
+}
+
+}  // namespace dect

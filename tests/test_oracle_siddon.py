@@ -123,3 +123,14 @@ def test_nnz_estimate_small():
     assert 1.7e6 < t.nnz < 2.1e6
     assert t.idx.min() >= 0 and t.idx.max() < 128 * 128
     assert np.all(t.len > 0)
+
+
+def test_one_element_per_ray_and_pixel():
+    """Rays through grid corners (rational slopes) still give one element a_ij per pixel."""
+    g = synth.tiny_geometry(n=64, nv=30, nb=96, px=0.5, sod=60.0, sdd=130.0, arc=math.pi)
+    t = oracle.table(g)
+    for r in range(g.nv * g.nb):
+        idx = t.idx[t.rowptr[r]:t.rowptr[r + 1]]
+        assert len(np.unique(idx)) == len(idx)
+    sub = synth.tiny_geometry(n=16, nv=6, nb=24, px=0.5, sod=60.0, sdd=130.0, arc=math.pi)
+    np.testing.assert_allclose(oracle.table(sub).dense(), indep.clip_matrix(sub), rtol=0, atol=1e-11)
