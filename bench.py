@@ -1,0 +1,385 @@
+"""Benchmark: dual-energy slices per second through ADM-TV (to 1e-4 relative
+objective change) and PLS decomposition, 512 x 512 at 0.5 mm, 60 views over
+360 deg, 736 bins x 0.6 mm (SOD 500, SDD 1000), seeded head-like phantoms,
+Poisson noise at I0 = 2e5 photons/bin.
+
+One step = one batch of S slices (both energies): dect_adm_tv until every
+channel's relative objective change is below 1e-4 (at most --max-iter
+iterations), then dect_pls_decompose (gamma 0.1, PCG to |r|/|b| < 1e-6).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+N > 1 runs under torch.distributed.run: each rank processes its own slices
+(weak scaling, no collective on the data path); only the step timings are
+reduced (max over ranks).  Rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+METRIC = "DECT slices/s to 1e-4 rel. objective at 512^2/60 views (2 energies + PLS)"
+UNIT = "slices/s"
+MU, RHO, BETA = 16.0, 256.0, (1.0, 0.6)
+TOL = 1e-4
+I0 = 2e5
+PLS = dict(gamma=0.1, edge_tau=0.2, edge_eps=0.05, max_iter=500, tol=1e-6)
+FALLBACK_HBM_GBS = 6800.0
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--slices", type=int, default=16, help="slices per step per GPU")
+    ap.add_argument("--max-iter", type=int, default=1000)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def make_inputs(geom, seeds):
+    m = np.stack([synth.make_slice(geom, s, kind="head", i0=I0).m for s in seeds]).astype(np.float32)
+    return m
+
+
+def seeds_for(rank, count):
+    return [1000 + 100000 * rank + i for i in range(count)]
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return FALLBACK_HBM_GBS, "fallback"
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1607_01650_gb300", "csrc")
+    for name in sorted(os.listdir(csrc)):
+        if name.endswith((".cu", ".cuh")):
+            with open(os.path.join(csrc, name), "rb") as f:
+                h.update(name.encode())
+                h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def committed_traffic(kernel):
+    """DRAM bytes per launch from the committed ncu summary, if it matches the current sources."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as f:
+        d = json.load(f)
+    if d.get("source_hash") != kernel_source_hash():
+        return None
+    k = d.get("kernels", {}).get(kernel)
+    return None if k is None else k.get("dram_bytes_per_launch")
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle-reason samples while the timed region runs."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if self.proc is None or not self.path or not os.path.exists(self.path):
+            return None
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    smax.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for nm, v in zip(names, parts[5:9]):
+                    if v.lower() in ("active", "1"):
+                        reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax),
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+# ---------------------------------------------------------------------------
+# CPU side: the FP64 oracle as it stands (baseline and reference arm)
+# ---------------------------------------------------------------------------
+
+def oracle_sample(geom, m_slice, iters_sample, x_for_pls):
+    """Time the oracle on one slice: `iters_sample` ADM iterations per energy and a full PLS.
+
+    Returns (seconds per ADM iteration per energy, seconds of one PLS decomposition).
+    """
+    import oracle
+    t = oracle.table(geom)
+    prm = oracle.AdmParams(mu=MU, rho=RHO, beta=BETA, step_rule=oracle.CAUCHY,
+                           max_iter=iters_sample, tol=0.0)
+    t0 = time.perf_counter()
+    oracle.adm_dual(t, m_slice.astype(np.float64), prm)
+    t_adm = (time.perf_counter() - t0) / (2 * iters_sample)
+    pp = oracle.PlsParams(gamma=PLS["gamma"], tau=PLS["edge_tau"], eps=PLS["edge_eps"],
+                          max_iter=PLS["max_iter"], tol=1e-10)
+    t0 = time.perf_counter()
+    oracle.pls_decompose(x_for_pls[0], x_for_pls[1], pp)
+    t_pls = time.perf_counter() - t0
+    return t_adm, t_pls
+
+
+def reference_iterations():
+    """Mean oracle iterations to the 1e-4 stop on this workload (stored by
+    tests/golden/make_workload_iterations.py, which runs only the oracle)."""
+    p = os.path.join(ROOT, "tests", "golden", "workload_iterations.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            return float(json.load(f)["mean_iterations"]), "oracle, stored"
+    return None, None
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return 0
+    geom = synth.paper_geometry()
+    iters, src = reference_iterations()
+    if iters is None:
+        iters, src = 200.0, "assumed (no stored oracle count)"
+    m = make_inputs(geom, seeds_for(0, 1))[0]
+    sl = synth.make_slice(geom, seeds_for(0, 1)[0], kind="head", i0=I0)
+    x_pls = sl.truth()[1]
+    sample_iters = 4
+    vals = []
+    total = args.warmup + args.steps
+    for k in range(total):
+        t_adm, t_pls = oracle_sample(geom, m, sample_iters, x_pls)
+        sec_slice = 2 * iters * t_adm + t_pls
+        if k >= args.warmup:
+            vals.append(sec_slice)
+    sec = statistics.mean(vals)
+    value = 1.0 / sec
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": sec * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": "paper-shaped 512x512/0.5mm, 60 views, 736 bins, head phantom, I0=2e5",
+                   "slices_per_step": 1},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": "per step: 1 slice, %d ADM iterations per energy + full PLS; "
+                                   "ADM time scaled to %.1f iterations (%s)" % (sample_iters, iters, src)},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------------
+# GPU side
+# ---------------------------------------------------------------------------
+
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+
+    import torch
+    import paper_1607_01650_gb300 as dect
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    geom = synth.paper_geometry()
+    S = args.slices
+    t0 = time.perf_counter()
+    plan = dect.Plan(geom, device=local)
+    plan_s = time.perf_counter() - t0
+    m_host = torch.from_numpy(make_inputs(geom, seeds_for(rank, S))).pin_memory()
+    m_dev = m_host.to("cuda")
+    x_dev = torch.zeros((S, 2, geom.n, geom.n), device="cuda")
+    u_dev = torch.empty_like(x_dev)
+    u_host = torch.empty(u_dev.shape, dtype=torch.float32).pin_memory()
+    prm = dect.AdmParams(mu=MU, rho=RHO, beta=BETA, step_rule=dect.CAUCHY, max_iter=args.max_iter,
+                         rel_obj_tol=TOL, check_every=10)
+    pp = dect.PlsParams(**PLS)
+
+    state = {"iters": [], "pls_iters": [], "prof": []}
+
+    def step(profile):
+        if profile:
+            x, reps, prof = dect.adm_tv(plan, m_dev, prm, x=x_dev, profile=True)
+            state["prof"].append(prof)
+        else:
+            x, reps = dect.adm_tv(plan, m_dev, prm, x=x_dev)
+        u, preps = dect.pls_decompose(x, pp, u=u_dev)
+        state["iters"] = [r.iters for r in reps]
+        state["pls_iters"] = [max(p[0]) for p in preps]
+        state["conv"] = all(r.converged for r in reps)
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    def max_over_ranks(v):
+        if dist is None:
+            return v
+        t = torch.tensor([v], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    for _ in range(args.warmup):
+        step(False)
+    torch.cuda.synchronize()
+    barrier()
+    torch.cuda.synchronize()
+    launches0 = dect.kernel_launches()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        ev0.record()
+        for _ in range(args.steps):
+            step(True)
+        ev1.record()
+        torch.cuda.synchronize()
+    barrier()
+    torch.cuda.synchronize()
+    launches = dect.kernel_launches() - launches0
+    ms = max_over_ranks(ev0.elapsed_time(ev1))
+    value = world * S * args.steps / (ms / 1e3)
+
+    # end to end: host buffers in, decomposition out, every step
+    e2e = None
+    if not args.no_e2e:
+        def step_e2e():
+            m_dev.copy_(m_host, non_blocking=True)
+            x, reps = dect.adm_tv(plan, m_dev, prm, x=x_dev)
+            u, _ = dect.pls_decompose(x, pp, u=u_dev)
+            u_host.copy_(u, non_blocking=True)
+        step_e2e()
+        torch.cuda.synchronize()
+        barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(args.steps):
+            step_e2e()
+        e1.record()
+        torch.cuda.synchronize()
+        barrier()
+        ems = max_over_ranks(e0.elapsed_time(e1))
+        e2e = {"value": world * S * args.steps / (ems / 1e3), "unit": UNIT,
+               "h2d_bytes_per_step": int(m_host.numel() * 4),
+               "d2h_bytes_per_step": int(u_host.numel() * 4)}
+
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return 0
+
+    # roofline of the dominant table kernel, from events inside the timed region
+    fwd_ms = sum(p.fwd_ms_total for p in state["prof"])
+    bwd_ms = sum(p.bwd_ms_total for p in state["prof"])
+    fwd_n = sum(p.fwd_launches for p in state["prof"])
+    bwd_n = sum(p.bwd_launches for p in state["prof"])
+    p0 = state["prof"][-1]
+    if fwd_ms >= bwd_ms:
+        kname, avg_ms, bytes_ = "k_fwd", fwd_ms / max(fwd_n, 1), p0.table_bytes_fwd
+    else:
+        kname, avg_ms, bytes_ = "k_bwd", bwd_ms / max(bwd_n, 1), p0.table_bytes_bwd
+    peak, peak_src = measured_peaks()
+    achieved = bytes_ / (avg_ms / 1e3) / 1e9
+    traffic = committed_traffic(kname)
+    roofline = {"bound": "hbm", "kernel": kname, "achieved": round(achieved, 1), "peak": peak,
+                "peak_source": peak_src, "unit": "GB/s", "frac": round(achieved / peak, 4),
+                "traffic": traffic, "algorithmic_bytes": int(bytes_), "avg_launch_ms": avg_ms,
+                "fwd_ms_avg": fwd_ms / max(fwd_n, 1), "bwd_ms_avg": bwd_ms / max(bwd_n, 1)}
+
+    clocks = clk.summary()
+    mean_it = float(np.mean(state["iters"]))
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        x_first = x_dev[0].double().cpu().numpy()
+        t_adm, t_pls = oracle_sample(geom, m_host[0].numpy(), 3, x_first)
+        sec_slice = 2 * mean_it * t_adm + t_pls
+        cpu = {"value": 1.0 / sec_slice, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": "1 slice: 3 ADM iterations per energy (%.3f s each) scaled to the GPU run's "
+                         "mean %.1f iterations, plus one full PLS (%.2f s)" % (t_adm, mean_it, t_pls)}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "paper-shaped 512x512/0.5mm, 60 views over 360deg, 736 bins x 0.6mm, "
+                               "SOD 500/SDD 1000, head phantom, I0=2e5, ADM to 1e-4 rel. objective "
+                               "(both energies) + PLS gamma 0.1",
+                   "slices_per_step_per_gpu": S, "mean_adm_iterations": mean_it,
+                   "max_adm_iterations": int(max(state["iters"])),
+                   "all_converged": bool(state.get("conv", False)),
+                   "mean_pcg_iterations": float(np.mean(state["pls_iters"])),
+                   "plan_seconds": round(plan_s, 3), "nnz": plan.nnz,
+                   "l2": "inputs larger than L2 (tables %.0f MB)" % (plan.table_bytes / 1e6),
+                   "parallelism": "replicas" if world > 1 else "1 GPU"},
+        "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+        "gpu_launches": int(launches), "clocks": clocks,
+    }
+    print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -195,17 +195,45 @@ typedef struct {
  * PLS decomposition, Eq. (11)-(15), of `batch` slices of n x n pixels:
  *   d = D^{-1} x per pixel (2x2 closed form in FP64), Eq. (11)-(12);
  *   edge map: 3x3 Prewitt magnitude of x_h and of x_l (replicate padding),
- *   each divided by its own maximum, edge where either exceeds edge_tau;
+ *   each divided by its own maximum, edge where either exceeds edge_tau
+ *   (decided in FP32 with a fixed order of operations);
  *   e_ik = edge_eps if pixel i or k is an edge, else 1, Eq. (14);
  *   solve (I + gamma L_e) u_m = d_m for m = 1, 2, (L_e u)_i = sum over the
  *   4-neighbours k inside the image of e_ik (u_i - u_k) -- Eq. (15), whose
  *   Hessian of R is 2 L_e -- by Jacobi-preconditioned CG from u = d.
- * xh, xl: [batch][n][n]; u1, u2: [batch][n][n] outputs.
+ * x: [batch][2][n][n] (x_h, x_l per slice: the layout dect_adm_tv writes);
+ * u: [batch][2][n][n] output (u_1, u_2 per slice).  x and u must not overlap.
  * reports: HOST array [batch] (may be NULL).  Synchronises `stream`.
+ * Device scratch is taken from the stream-ordered allocator and returned
+ * before the call ends.
  */
-dect_status dect_pls_decompose(const float *xh, const float *xl, int n, int batch,
-                               const dect_pls_params *params, float *u1, float *u2,
-                               dect_pls_report *reports, dect_stream stream);
+dect_status dect_pls_decompose(const float *x, int n, int batch, const dect_pls_params *params,
+                               float *u, dect_pls_report *reports, dect_stream stream);
+
+/* Kernel timing of one dect_adm_tv_ex call, from CUDA events recorded
+ * around the launches of the two table kernels inside the iteration graph. */
+typedef struct {
+    double fwd_ms_total;   /* q = A G launches (ray-major table)      */
+    double bwd_ms_total;   /* G = mu A^T r + ... (pixel-major table)  */
+    int64_t fwd_launches;
+    int64_t bwd_launches;
+    int64_t table_bytes_fwd;  /* algorithmic bytes of one fwd launch  */
+    int64_t table_bytes_bwd;  /* algorithmic bytes of one bwd launch  */
+} dect_adm_profile;
+
+/*
+ * dect_adm_tv with optional kernel timing (prof may be NULL, which makes it
+ * identical to dect_adm_tv).  With prof != NULL, events are recorded around
+ * every A G and A^T r launch and read back after each block of check_every
+ * iterations; the totals cover all chunks of the call.
+ */
+dect_status dect_adm_tv_ex(const dect_plan *plan, const float *m, float *x, int n_slices,
+                           const dect_adm_params *params, dect_adm_report *reports,
+                           dect_adm_profile *prof, dect_stream stream);
+
+/* Number of kernels libdect has launched in this process so far (kernel
+ * launches plus the kernel nodes of every graph launch). */
+int64_t dect_kernel_launches(void);
 
 /* Text of a status code (static storage). */
 const char *dect_status_string(dect_status s);

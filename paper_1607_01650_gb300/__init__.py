@@ -17,8 +17,9 @@ from typing import List, Optional, Sequence, Tuple
 
 from . import _build
 
-__all__ = ["Geometry", "Plan", "AdmParams", "PlsParams", "DectError", "load",
-           "project", "backproject", "adm_tv", "pls_decompose", "library_path"]
+__all__ = ["Geometry", "Plan", "AdmParams", "PlsParams", "AdmReport", "AdmProfile", "DectError",
+           "load", "project", "backproject", "adm_tv", "pls_decompose", "kernel_launches",
+           "library_path"]
 
 
 class DectError(RuntimeError):
@@ -48,6 +49,12 @@ class _AdmReport(C.Structure):
                 ("rel_change", C.c_double)]
 
 
+class _AdmProfile(C.Structure):
+    _fields_ = [("fwd_ms_total", C.c_double), ("bwd_ms_total", C.c_double),
+                ("fwd_launches", C.c_int64), ("bwd_launches", C.c_int64),
+                ("table_bytes_fwd", C.c_int64), ("table_bytes_bwd", C.c_int64)]
+
+
 class _PlsParams(C.Structure):
     _fields_ = [("eta", (C.c_double * 2) * 2), ("gamma", C.c_double), ("edge_tau", C.c_double),
                 ("edge_eps", C.c_double), ("max_iter", C.c_int), ("tol", C.c_double)]
@@ -69,8 +76,9 @@ _SIGS = {
     "dect_project": (C.c_int, [_P, _P, _P, C.c_int, _P]),
     "dect_backproject": (C.c_int, [_P, _P, _P, C.c_int, _P]),
     "dect_adm_tv": (C.c_int, [_P, _P, _P, C.c_int, C.POINTER(_AdmParams), _P, _P]),
-    "dect_pls_decompose": (C.c_int, [_P, _P, C.c_int, C.c_int, C.POINTER(_PlsParams), _P, _P,
-                                     _P, _P]),
+    "dect_adm_tv_ex": (C.c_int, [_P, _P, _P, C.c_int, C.POINTER(_AdmParams), _P, _P, _P]),
+    "dect_pls_decompose": (C.c_int, [_P, C.c_int, C.c_int, C.POINTER(_PlsParams), _P, _P, _P]),
+    "dect_kernel_launches": (C.c_int64, []),
     "dect_status_string": (C.c_char_p, [C.c_int]),
     "dect_last_error": (C.c_char_p, []),
     "dect_version": (C.c_int, []),
@@ -255,11 +263,22 @@ class AdmReport:
     rel_change: float
 
 
-def adm_tv(plan: Plan, m, params: AdmParams, x=None, stream=None):
+@dataclasses.dataclass
+class AdmProfile:
+    """CUDA-event timing of the two table kernels inside one adm_tv call."""
+    fwd_ms_total: float
+    bwd_ms_total: float
+    fwd_launches: int
+    bwd_launches: int
+    table_bytes_fwd: int
+    table_bytes_bwd: int
+
+
+def adm_tv(plan: Plan, m, params: AdmParams, x=None, stream=None, profile: bool = False):
     """ADM-TV reconstruction (Eq. (3)-(10)) of slices sharing `plan`.
 
     m: [S, 2, nv, nb] float32 CUDA (energy 0 = high, 1 = low).  Returns
-    (x [S, 2, n, n], reports[S * 2]).
+    (x [S, 2, n, n], reports[S * 2]) and, with profile=True, an AdmProfile.
     """
     import torch
     g = plan.geom
@@ -268,12 +287,25 @@ def adm_tv(plan: Plan, m, params: AdmParams, x=None, stream=None):
     S = m.shape[0]
     if x is None:
         x = torch.zeros((S, 2, g.n, g.n), device=m.device, dtype=torch.float32)
+    elif x.shape != (S, 2, g.n, g.n):
+        raise DectError("x must be [S, 2, n, n]")
     rep = (_AdmReport * max(2 * S, 1))()
-    _check(load().dect_adm_tv(plan.handle, _ptr(m, torch.float32, plan.device),
-                              _ptr(x, torch.float32, plan.device), S, C.byref(params._c()),
-                              C.cast(rep, C.c_void_p), _stream(stream)), "dect_adm_tv")
+    prof = _AdmProfile() if profile else None
+    _check(load().dect_adm_tv_ex(plan.handle, _ptr(m, torch.float32, plan.device),
+                                 _ptr(x, torch.float32, plan.device), S, C.byref(params._c()),
+                                 C.cast(rep, C.c_void_p),
+                                 C.cast(C.pointer(prof), C.c_void_p) if prof is not None else None,
+                                 _stream(stream)), "dect_adm_tv")
     reps = [AdmReport(r.iters, bool(r.converged), r.objective, r.rel_change) for r in rep[:2 * S]]
+    if profile:
+        return x, reps, AdmProfile(prof.fwd_ms_total, prof.bwd_ms_total, prof.fwd_launches,
+                                   prof.bwd_launches, prof.table_bytes_fwd, prof.table_bytes_bwd)
     return x, reps
+
+
+def kernel_launches() -> int:
+    """Kernels launched by libdect so far in this process."""
+    return int(load().dect_kernel_launches())
 
 
 @dataclasses.dataclass
@@ -294,22 +326,22 @@ class PlsParams:
         return _PlsParams(e, self.gamma, self.edge_tau, self.edge_eps, self.max_iter, self.tol)
 
 
-def pls_decompose(xh, xl, params: PlsParams, u1=None, u2=None, stream=None):
-    """PLS decomposition (Eq. (11)-(15)): xh, xl [B, n, n] -> (u1, u2, reports)."""
+def pls_decompose(x, params: PlsParams, u=None, stream=None):
+    """PLS decomposition (Eq. (11)-(15)): x [B, 2, n, n] (x_h, x_l) -> u [B, 2, n, n] (u_1, u_2).
+
+    Returns (u, reports) with reports[b] = ((iters_1, iters_2), (relres_1, relres_2)).
+    """
     import torch
-    if xh.shape != xl.shape or xh.dim() < 2 or xh.shape[-1] != xh.shape[-2]:
-        raise DectError("xh, xl must be [..., n, n] of equal shape")
-    n = xh.shape[-1]
-    batch = xh.numel() // (n * n)
-    if u1 is None:
-        u1 = torch.empty_like(xh)
-    if u2 is None:
-        u2 = torch.empty_like(xh)
-    dev = xh.device.index
+    if x.dim() != 4 or x.shape[1] != 2 or x.shape[2] != x.shape[3]:
+        raise DectError("x must be [B, 2, n, n]")
+    n = x.shape[-1]
+    batch = x.shape[0]
+    if u is None:
+        u = torch.empty_like(x)
+    dev = x.device.index
     rep = (_PlsReport * max(batch, 1))()
-    _check(load().dect_pls_decompose(_ptr(xh, torch.float32, dev), _ptr(xl, torch.float32, dev), n,
-                                     batch, C.byref(params._c()), _ptr(u1, torch.float32, dev),
-                                     _ptr(u2, torch.float32, dev), C.cast(rep, C.c_void_p),
+    _check(load().dect_pls_decompose(_ptr(x, torch.float32, dev), n, batch, C.byref(params._c()),
+                                     _ptr(u, torch.float32, dev), C.cast(rep, C.c_void_p),
                                      _stream(stream)), "dect_pls_decompose")
     reps = [(tuple(r.iters), tuple(r.relres)) for r in rep[:batch]]
-    return u1, u2, reps
+    return u, reps

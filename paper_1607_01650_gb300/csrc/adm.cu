@@ -381,21 +381,33 @@ struct Work {
     AdmDev D;
 };
 
+// Optional timing events around the two table kernels of one iteration.
+struct IterEvents {
+    cudaEvent_t b0, b1, f0, f1;
+};
+
 template <int NB>
-void enqueue_iteration(const dect_plan *P, const Work &W, const AdmConst &C, cudaStream_t s)
+void enqueue_iteration(const dect_plan *P, const Work &W, const AdmConst &C, cudaStream_t s,
+                       const IterEvents *ev)
 {
     k_step<NB><<<kGrid, kBlock, 0, s>>>(W.f, W.G, W.r, W.q, C, W.D);
     k_tv<NB><<<kGrid, kBlock, 0, s>>>(W.f, W.lam, W.z, W.p, C, W.D, 0);
+    if (ev) cudaEventRecordWithFlags(ev->b0, s, cudaEventRecordExternal);
     k_bwd<NB, Kern<NB>::GB><<<kGrid, kBlock, 0, s>>>(P->colptr, P->tent, W.r, W.p, W.G, C, W.D);
+    if (ev) cudaEventRecordWithFlags(ev->b1, s, cudaEventRecordExternal);
     k_gnorm<NB><<<kGrid, kBlock, 0, s>>>(W.G, C, W.D);
+    if (ev) cudaEventRecordWithFlags(ev->f0, s, cudaEventRecordExternal);
     k_fwd<NB, Kern<NB>::GF, 1><<<kGrid, kBlock, 0, s>>>(P->rowptr, P->ent, W.G, W.q, nullptr, nullptr,
                                                          C, W.D);
+    if (ev) cudaEventRecordWithFlags(ev->f1, s, cudaEventRecordExternal);
 }
+
+constexpr int kKernelsPerIteration = 5;
 
 template <int NB>
 dect_status run_chunk(const dect_plan *P, const float *m, float *x, int nimg,
                       const dect_adm_params *prm, const float *beta_host, dect_adm_report *rep,
-                      cudaStream_t s)
+                      dect_adm_profile *prof, cudaStream_t s)
 {
     const int64_t N = P->N, M = P->M;
     AdmConst C;
@@ -412,34 +424,31 @@ dect_status run_chunk(const dect_plan *P, const float *m, float *x, int nimg,
     C.rule = prm->step_rule;
     C.nimg = nimg;
 
-    // one allocation for everything
+    // one allocation for everything: lay out once to size, then for real
     const size_t nf = (size_t)N * NB, nr = (size_t)M * NB;
-    const size_t floats = nf * (1 + 1 + 2 + 2 + 2) + nr * 2 + 64;
     const size_t ndbl = (size_t)R_COUNT * NB + (size_t)R_COUNT * kGrid * NB + 4 * NB;
     const size_t nint = 4 * NB + 8;
-    const size_t bytes = floats * 4 + ndbl * 8 + nint * 4 + R_COUNT * 4 + 1024;
+    Work W;
+    auto layout = [&](char *b) -> size_t {
+        size_t o = 0;
+        auto take = [&](size_t nbytes) { char *p = b ? b + o : nullptr; o = (o + nbytes + 255) & ~(size_t)255; return p; };
+        W.f = (float *)take(nf * 4);
+        W.G = (float *)take(nf * 4);
+        W.lam = (float *)take(2 * nf * 4);
+        W.z = (float *)take(2 * nf * 4);
+        W.p = (float *)take(2 * nf * 4);
+        W.r = (float *)take(nr * 4);
+        W.q = (float *)take(nr * 4);
+        W.beta = (float *)take(64 * 4);
+        W.dbl = (double *)take(ndbl * 8);
+        W.ints = (int *)take(nint * 4);
+        W.ctr = (unsigned *)take(R_COUNT * 4);
+        return o;
+    };
+    const size_t bytes = layout(nullptr);
     char *base = nullptr;
     DECT_CUDA(cudaMallocAsync((void **)&base, bytes, s));
-    auto align = [](size_t o) { return (o + 255) & ~(size_t)255; };
-    size_t o = 0;
-    Work W;
-    auto takef = [&](size_t cnt) { float *ptr = (float *)(base + o); o = align(o + cnt * 4); return ptr; };
-    W.f = takef(nf);
-    W.G = takef(nf);
-    W.lam = takef(2 * nf);
-    W.z = takef(2 * nf);
-    W.p = takef(2 * nf);
-    W.r = takef(nr);
-    W.q = takef(nr);
-    W.beta = takef(64);
-    W.dbl = (double *)(base + o);
-    o = align(o + ndbl * 8);
-    W.ints = (int *)(base + o);
-    o = align(o + nint * 4);
-    W.ctr = (unsigned *)(base + o);
-    o = align(o + R_COUNT * 4);
-    size_t used_end = o;
-    (void)used_end;
+    layout(base);
 
     AdmDev &D = W.D;
     D.red = W.dbl;
@@ -471,10 +480,12 @@ dect_status run_chunk(const dect_plan *P, const float *m, float *x, int nimg,
     if (prm->warm_start) {
         k_pack<NB><<<(unsigned)((tn + 255) / 256), 256, 0, s>>>(x, W.f, N, nimg, W.beta);
         DECT_LAUNCH_CHECK();
+        count_launches(1);
     }
     // r^0 = A f^0 - beta m
     k_fwd<NB, Kern<NB>::GF, 0><<<kGrid, kBlock, 0, s>>>(P->rowptr, P->ent, W.f, W.r, m, W.beta, C, D);
     DECT_LAUNCH_CHECK();
+    count_launches(1);
 
     // iterations: CUDA graphs of `block` iterations
     const int K = prm->max_iter;
@@ -485,33 +496,66 @@ dect_status run_chunk(const dect_plan *P, const float *m, float *x, int nimg,
     DECT_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
     cudaEvent_t ev = nullptr;
     DECT_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
-    auto cleanup = [&]() {
-        if (ev) cudaEventDestroy(ev);
-        if (cs) cudaStreamDestroy(cs);
+    std::vector<IterEvents> evs;  // [block] for the block graph, then [1] for the single graph
+    auto destroy_events = [&]() {
+        for (auto &e : evs) {
+            cudaEventDestroy(e.b0); cudaEventDestroy(e.b1);
+            cudaEventDestroy(e.f0); cudaEventDestroy(e.f1);
+        }
+        evs.clear();
     };
+    cudaError_t err = cudaSuccess;
+    if (prof) {
+        evs.resize(block + 1);
+        for (auto &e : evs) {
+            if (err == cudaSuccess) err = cudaEventCreate(&e.b0);
+            if (err == cudaSuccess) err = cudaEventCreate(&e.b1);
+            if (err == cudaSuccess) err = cudaEventCreate(&e.f0);
+            if (err == cudaSuccess) err = cudaEventCreate(&e.f1);
+        }
+    }
     cudaGraphExec_t gx_block = nullptr, gx_one = nullptr;
-    auto make_graph = [&](int iters, cudaGraphExec_t *out) -> cudaError_t {
+    auto make_graph = [&](int iters, int ev0, cudaGraphExec_t *out) -> cudaError_t {
         cudaGraph_t gr = nullptr;
         cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
         if (e != cudaSuccess) return e;
-        for (int it = 0; it < iters; ++it) enqueue_iteration<NB>(P, W, C, cs);
+        for (int it = 0; it < iters; ++it)
+            enqueue_iteration<NB>(P, W, C, cs, prof ? &evs[ev0 + it] : nullptr);
         e = cudaStreamEndCapture(cs, &gr);
         if (e != cudaSuccess) return e;
         e = cudaGraphInstantiate(out, gr, 0);
         cudaGraphDestroy(gr);
         return e;
     };
+    // time read-back of the events of `iters` iterations starting at ev0
+    auto collect = [&](int iters, int ev0) -> cudaError_t {
+        if (!prof) return cudaSuccess;
+        cudaError_t e = cudaStreamSynchronize(cs);
+        for (int it = 0; it < iters && e == cudaSuccess; ++it) {
+            float mb = 0.f, mf = 0.f;
+            e = cudaEventElapsedTime(&mb, evs[ev0 + it].b0, evs[ev0 + it].b1);
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&mf, evs[ev0 + it].f0, evs[ev0 + it].f1);
+            prof->bwd_ms_total += mb;
+            prof->fwd_ms_total += mf;
+            prof->bwd_launches += 1;
+            prof->fwd_launches += 1;
+        }
+        return e;
+    };
     // the caller's stream orders the set-up; the capture stream runs the loop
-    cudaError_t err = cudaEventRecord(ev, s);
+    if (err == cudaSuccess) err = cudaEventRecord(ev, s);
     if (err == cudaSuccess) err = cudaStreamWaitEvent(cs, ev, 0);
-    if (err == cudaSuccess && K >= block) err = make_graph(block, &gx_block);
-    if (err == cudaSuccess && K % block) err = make_graph(1, &gx_one);
+    if (err == cudaSuccess && K >= block) err = make_graph(block, 0, &gx_block);
+    if (err == cudaSuccess && K % block) err = make_graph(1, block, &gx_one);
     int *h_done = nullptr;
     if (err == cudaSuccess) err = cudaMallocHost((void **)&h_done, sizeof(int));
+    if (h_done) *h_done = 0;
     int done_iters = 0;
     while (err == cudaSuccess && done_iters + block <= K) {
         err = cudaGraphLaunch(gx_block, cs);
+        count_launches((int64_t)kKernelsPerIteration * block);
         done_iters += block;
+        if (err == cudaSuccess) err = collect(block, 0);
         if (err == cudaSuccess && use_tol) {
             err = cudaMemcpyAsync(h_done, D.all_done, sizeof(int), cudaMemcpyDeviceToHost, cs);
             if (err == cudaSuccess) err = cudaStreamSynchronize(cs);
@@ -521,7 +565,9 @@ dect_status run_chunk(const dect_plan *P, const float *m, float *x, int nimg,
     bool finished = use_tol && err == cudaSuccess && *h_done;
     while (err == cudaSuccess && !finished && done_iters < K) {
         err = cudaGraphLaunch(gx_one, cs);
+        count_launches(kKernelsPerIteration);
         ++done_iters;
+        if (err == cudaSuccess) err = collect(1, block);
     }
     // final update f^K = f^{K-1} - alpha G and the objective at the result
     if (err == cudaSuccess) {
@@ -529,9 +575,14 @@ dect_status run_chunk(const dect_plan *P, const float *m, float *x, int nimg,
         k_tv<NB><<<kGrid, kBlock, 0, cs>>>(W.f, W.lam, W.z, W.p, C, D, 1);
         k_unpack<NB><<<(unsigned)((tn + 255) / 256), 256, 0, cs>>>(W.f, x, N, nimg, W.beta);
         err = cudaGetLastError();
+        count_launches(3);
     }
     if (err == cudaSuccess) err = cudaEventRecord(ev, cs);
     if (err == cudaSuccess) err = cudaStreamWaitEvent(s, ev, 0);
+    if (prof) {
+        prof->table_bytes_fwd = 8 * P->nnz + 8 * (P->M + 1) + 4LL * NB * (P->N + P->M);
+        prof->table_bytes_bwd = 8 * P->nnz + 8 * (P->N + 1) + 4LL * NB * (P->M + 4 * P->N);
+    }
 
     std::vector<double> hred(R_COUNT * NB), hrel(NB);
     std::vector<int> hit(NB), hconv(NB);
@@ -546,7 +597,9 @@ dect_status run_chunk(const dect_plan *P, const float *m, float *x, int nimg,
     if (gx_block) cudaGraphExecDestroy(gx_block);
     if (gx_one) cudaGraphExecDestroy(gx_one);
     if (h_done) cudaFreeHost(h_done);
-    cleanup();
+    destroy_events();
+    cudaEventDestroy(ev);
+    cudaStreamDestroy(cs);
     if (err != cudaSuccess) {
         set_error("dect_adm_tv", err);
         return err == cudaErrorMemoryAllocation ? DECT_ERR_OOM : DECT_ERR_CUDA;
@@ -567,9 +620,9 @@ dect_status run_chunk(const dect_plan *P, const float *m, float *x, int nimg,
 
 using namespace dect;
 
-extern "C" dect_status dect_adm_tv(const dect_plan *plan, const float *m, float *x, int n_slices,
-                                   const dect_adm_params *prm, dect_adm_report *reports,
-                                   dect_stream stream)
+extern "C" dect_status dect_adm_tv_ex(const dect_plan *plan, const float *m, float *x, int n_slices,
+                                      const dect_adm_params *prm, dect_adm_report *reports,
+                                      dect_adm_profile *prof, dect_stream stream)
 {
     if (!plan || !prm || n_slices < 0) return DECT_ERR_INVALID_ARG;
     if (n_slices == 0) return DECT_OK;
@@ -577,10 +630,14 @@ extern "C" dect_status dect_adm_tv(const dect_plan *plan, const float *m, float 
     if (!(prm->mu > 0) || !(prm->rho > 0) || !(prm->beta[0] > 0) || !(prm->beta[1] > 0) ||
         prm->max_iter < 0 || (prm->step_rule != DECT_STEP_BB1 && prm->step_rule != DECT_STEP_CAUCHY) ||
         !std::isfinite(prm->mu) || !std::isfinite(prm->rho) || !std::isfinite(prm->xi) ||
-        prm->check_every < 0)
+        !std::isfinite(prm->beta[0]) || !std::isfinite(prm->beta[1]) || prm->check_every < 0)
         return DECT_ERR_INVALID_ARG;
     DECT_CUDA(cudaSetDevice(plan->device));
     cudaStream_t s = (cudaStream_t)stream;
+    if (prof) {
+        prof->fwd_ms_total = prof->bwd_ms_total = 0.0;
+        prof->fwd_launches = prof->bwd_launches = 0;
+    }
     const int total = 2 * n_slices;
     dect_status worst = DECT_OK;
     for (int c0 = 0; c0 < total; c0 += kMaxBatchImages) {
@@ -592,17 +649,24 @@ extern "C" dect_status dect_adm_tv(const dect_plan *plan, const float *m, float 
         dect_adm_report *rc = reports ? reports + c0 : nullptr;
         dect_status st;
         if (nimg <= 2)
-            st = run_chunk<2>(plan, mc, xc, nimg, prm, beta.data(), rc, s);
+            st = run_chunk<2>(plan, mc, xc, nimg, prm, beta.data(), rc, prof, s);
         else if (nimg <= 4)
-            st = run_chunk<4>(plan, mc, xc, nimg, prm, beta.data(), rc, s);
+            st = run_chunk<4>(plan, mc, xc, nimg, prm, beta.data(), rc, prof, s);
         else if (nimg <= 8)
-            st = run_chunk<8>(plan, mc, xc, nimg, prm, beta.data(), rc, s);
+            st = run_chunk<8>(plan, mc, xc, nimg, prm, beta.data(), rc, prof, s);
         else if (nimg <= 16)
-            st = run_chunk<16>(plan, mc, xc, nimg, prm, beta.data(), rc, s);
+            st = run_chunk<16>(plan, mc, xc, nimg, prm, beta.data(), rc, prof, s);
         else
-            st = run_chunk<32>(plan, mc, xc, nimg, prm, beta.data(), rc, s);
+            st = run_chunk<32>(plan, mc, xc, nimg, prm, beta.data(), rc, prof, s);
         if (st == DECT_ERR_NONFINITE) worst = st;
         else if (st != DECT_OK) return st;
     }
     return worst;
+}
+
+extern "C" dect_status dect_adm_tv(const dect_plan *plan, const float *m, float *x, int n_slices,
+                                   const dect_adm_params *prm, dect_adm_report *reports,
+                                   dect_stream stream)
+{
+    return dect_adm_tv_ex(plan, m, x, n_slices, prm, reports, nullptr, stream);
 }

@@ -1,6 +1,7 @@
 // Status strings, error text and version of libdect.
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <cstring>
 #include <string>
 
@@ -9,6 +10,9 @@
 namespace dect {
 
 static thread_local char g_err[512] = "";
+static std::atomic<int64_t> g_launches{0};
+
+void count_launches(int64_t k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
 
 void set_error(const char *where, cudaError_t e)
 {
@@ -40,3 +44,5 @@ extern "C" const char *dect_status_string(dect_status s)
 extern "C" const char *dect_last_error(void) { return dect::g_err; }
 
 extern "C" int dect_version(void) { return 100; }
+
+extern "C" int64_t dect_kernel_launches(void) { return dect::g_launches.load(); }

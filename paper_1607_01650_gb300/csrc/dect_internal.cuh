@@ -29,6 +29,9 @@ void set_error_text(const std::string &s);
 
 #define DECT_LAUNCH_CHECK() DECT_CUDA(cudaGetLastError())
 
+// Count of kernels launched by the library (dect_kernel_launches()).
+void count_launches(int64_t k);
+
 // Packed table entry: .x = pixel (or ray) index, .y = __float_as_int(length in mm).
 typedef int2 Entry;
 

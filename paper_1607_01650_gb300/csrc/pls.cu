@@ -1,9 +1,474 @@
-// PLS decomposition (Eq. (11)-(15)).
+// PLS image-domain decomposition, Eq. (11)-(15) (Sec. 2.3).
+//
+//   d   = D^{-1} x per pixel, D = [[eta_1H, eta_2H], [eta_1L, eta_2L]]     Eq. (11)-(12)
+//         (closed-form 2x2 inverse in FP64)
+//   e_ik= edge_eps if pixel i or k is an edge, else 1                     Eq. (14)
+//         (edge: 3x3 Prewitt magnitude of x_h or x_l over its maximum > tau)
+//   (I + gamma L_e) u_m = d_m,  (L_e u)_i = sum_{k in N_i} e_ik (u_i - u_k)
+//         -- Eq. (15) with Hessian R = 2 L_e -- by Jacobi-preconditioned CG
+//         from u = d, FP32 vectors, FP64 scalars.
+//
+// Vectors: v = 2 s + m (slice s, material m) at u + v N (the [slice][2][n][n]
+// layout of the input and output); the CG runs
+// all vectors of the batch in lockstep with per-vector step sizes and stop
+// flags.  The edge decision is taken in FP32 with a fixed order of
+// operations (the paper fixes no precision for it).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
 #include "dect_internal.cuh"
 
-extern "C" dect_status dect_pls_decompose(const float *, const float *, int, int,
-                                          const dect_pls_params *, float *, float *,
-                                          dect_pls_report *, dect_stream)
+namespace dect {
+namespace {
+
+constexpr int kBlock = 256;
+
+struct PlsDev {
+    // scalars per vector
+    double *red;      // [3][nvec] results of the last reduction
+    double *part;     // [gx * nvec * 3] block partials
+    unsigned *ctr;    // [2] last-block counters
+    double *alpha, *beta, *rz, *bnorm, *relres;  // [nvec]
+    int *iters, *done, *it;                      // [nvec], [nvec], [1]
+    int *all_done;
+    int *maxbits;     // [2 * nslices] float bits of max Prewitt magnitude
+};
+
+struct PlsConst {
+    int n;
+    int64_t N;
+    int nvec;
+    float gamma, eps;
+    double tol;
+};
+
+// FP32 warp sums, FP64 across warps and blocks (fixed order).  The block
+// that finishes last writes out[y * K + k] (y = blockIdx.y) and returns true.
+template <int K>
+__device__ bool reduce_planar(const float (&v)[K], double *part, double *out, unsigned *counter)
 {
-    return DECT_ERR_INVALID_ARG;
+    __shared__ double smem[(kBlock / 32) * K];
+    __shared__ bool last;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    float w[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        w[k] = v[k];
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) w[k] += __shfl_xor_sync(0xffffffffu, w[k], off);
+    }
+    if (lane == 0)
+#pragma unroll
+        for (int k = 0; k < K; ++k) smem[warp * K + k] = (double)w[k];
+    __syncthreads();
+    const unsigned gx = gridDim.x, gy = gridDim.y;
+    if (threadIdx.x < K) {
+        double s = 0.0;
+        for (int q = 0; q < nw; ++q) s += smem[q * K + threadIdx.x];
+        part[((size_t)blockIdx.y * gx + blockIdx.x) * K + threadIdx.x] = s;
+    }
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) last = (atomicAdd(counter, 1u) == gx * gy - 1);
+    __syncthreads();
+    if (!last) return false;
+    __threadfence();
+    for (unsigned t = threadIdx.x; t < gy * K; t += blockDim.x) {
+        const unsigned y = t / K, k = t % K;
+        double s = 0.0;
+        for (unsigned b = 0; b < gx; ++b) s += __ldcg(&part[((size_t)y * gx + b) * K + k]);
+        out[t] = s;
+    }
+    if (threadIdx.x == 0) *counter = 0u;
+    __syncthreads();
+    return true;
+}
+
+__device__ __forceinline__ int clampi(int a, int lo, int hi) { return a < lo ? lo : (a > hi ? hi : a); }
+
+// Prewitt magnitude, FP32, explicit rounding (same order of operations as
+// the decision rule states).
+__device__ __forceinline__ float prewitt_at(const float *__restrict__ x, int n, int i, int j)
+{
+    const int jl = clampi(j - 1, 0, n - 1), jr = clampi(j + 1, 0, n - 1);
+    const int iu = clampi(i - 1, 0, n - 1), id = clampi(i + 1, 0, n - 1);
+    float gx = 0.f, gy = 0.f;
+#pragma unroll
+    for (int t = -1; t <= 1; ++t) {
+        const int ii = clampi(i + t, 0, n - 1), jj = clampi(j + t, 0, n - 1);
+        gx = __fadd_rn(gx, __fsub_rn(x[(int64_t)ii * n + jr], x[(int64_t)ii * n + jl]));
+        gy = __fadd_rn(gy, __fsub_rn(x[(int64_t)id * n + jj], x[(int64_t)iu * n + jj]));
+    }
+    return __fsqrt_rn(__fadd_rn(__fmul_rn(gx, gx), __fmul_rn(gy, gy)));
+}
+
+// d = D^{-1} x (FP64), written as the initial u; Prewitt magnitudes and their maxima.
+__global__ void k_prep(const float *__restrict__ x, int n, int64_t N, double a, double b, double c,
+                       double e, float *__restrict__ u, float *__restrict__ mh,
+                       float *__restrict__ ml, int *__restrict__ maxbits)
+{
+    const int s = blockIdx.y;
+    const float *xs = x + (int64_t)(2 * s) * N, *ls = xs + N;
+    float lmax_h = 0.f, lmax_l = 0.f;
+    const double det = __dsub_rn(__dmul_rn(a, e), __dmul_rn(b, c));
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < N;
+         p += (int64_t)gridDim.x * blockDim.x) {
+        const double h = xs[p], l = ls[p];
+        const double d1 = __ddiv_rn(__dsub_rn(__dmul_rn(e, h), __dmul_rn(b, l)), det);
+        const double d2 = __ddiv_rn(__dadd_rn(__dmul_rn(-c, h), __dmul_rn(a, l)), det);
+        u[(int64_t)(2 * s) * N + p] = (float)d1;
+        u[(int64_t)(2 * s + 1) * N + p] = (float)d2;
+        const int i = (int)(p / n), j = (int)(p % n);
+        const float g1 = prewitt_at(xs, n, i, j), g2 = prewitt_at(ls, n, i, j);
+        mh[(int64_t)s * N + p] = g1;
+        ml[(int64_t)s * N + p] = g2;
+        lmax_h = fmaxf(lmax_h, g1);
+        lmax_l = fmaxf(lmax_l, g2);
+    }
+    // maxima of non-negative floats: integer max of their bit patterns
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        lmax_h = fmaxf(lmax_h, __shfl_xor_sync(0xffffffffu, lmax_h, off));
+        lmax_l = fmaxf(lmax_l, __shfl_xor_sync(0xffffffffu, lmax_l, off));
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicMax(&maxbits[2 * s], __float_as_int(lmax_h));
+        atomicMax(&maxbits[2 * s + 1], __float_as_int(lmax_l));
+    }
+}
+
+__global__ void k_mask(const float *__restrict__ mh, const float *__restrict__ ml, int64_t N,
+                       const int *__restrict__ maxbits, float tau, unsigned char *__restrict__ mask)
+{
+    const int s = blockIdx.y;
+    const float Mh = __int_as_float(maxbits[2 * s]), Ml = __int_as_float(maxbits[2 * s + 1]);
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < N;
+         p += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t q = (int64_t)s * N + p;
+        const bool eh = Mh > 0.f && __fdiv_rn(mh[q], Mh) > tau;
+        const bool el = Ml > 0.f && __fdiv_rn(ml[q], Ml) > tau;
+        mask[q] = (unsigned char)(eh || el);
+    }
+}
+
+// (I + gamma L_e) applied at pixel (i, j) to vector `u` of slice mask `mk`;
+// also returns the Jacobi diagonal.
+struct Stencil {
+    const unsigned char *mk;
+    int n;
+    float gamma, eps;
+    __device__ __forceinline__ float w(int64_t p, int64_t q) const { return (mk[p] | mk[q]) ? eps : 1.f; }
+};
+
+template <typename F>
+__device__ __forceinline__ float apply_op(const Stencil &S, int i, int j, int64_t p, F val, float &diag)
+{
+    const float c = val(p);
+    float acc = 0.f, wsum = 0.f;
+    if (i > 0) { float w = S.w(p, p - S.n); acc += w * (c - val(p - S.n)); wsum += w; }
+    if (i + 1 < S.n) { float w = S.w(p, p + S.n); acc += w * (c - val(p + S.n)); wsum += w; }
+    if (j > 0) { float w = S.w(p, p - 1); acc += w * (c - val(p - 1)); wsum += w; }
+    if (j + 1 < S.n) { float w = S.w(p, p + 1); acc += w * (c - val(p + 1)); wsum += w; }
+    diag = 1.f + S.gamma * wsum;
+    return c + S.gamma * acc;
+}
+
+
+// r = d - A d, z = r / diag, p = 0; reductions <r,z>, <r,r>, <d,d>.
+__global__ void k_init(float *__restrict__ uall, const unsigned char *__restrict__ mask,
+                       float *__restrict__ r, float *__restrict__ z, float *__restrict__ p,
+                       PlsConst C, PlsDev D)
+{
+    const int v = blockIdx.y;
+    const float *u = uall + (int64_t)v * C.N;
+    Stencil S{mask + (int64_t)(v >> 1) * C.N, C.n, C.gamma, C.eps};
+    float acc[3] = {0.f, 0.f, 0.f};
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < C.N;
+         q += (int64_t)gridDim.x * blockDim.x) {
+        const int i = (int)(q / C.n), j = (int)(q % C.n);
+        float diag;
+        const float Ad = apply_op(S, i, j, q, [&](int64_t k) { return u[k]; }, diag);
+        const float d = u[q];
+        const float rr = d - Ad, zz = rr / diag;
+        const int64_t o = (int64_t)v * C.N + q;
+        r[o] = rr;
+        z[o] = zz;
+        p[o] = 0.f;
+        acc[0] = fmaf(rr, zz, acc[0]);
+        acc[1] = fmaf(rr, rr, acc[1]);
+        acc[2] = fmaf(d, d, acc[2]);
+    }
+    if (reduce_planar<3>(acc, D.part, D.red, D.ctr)) {
+        for (int w = threadIdx.x; w < C.nvec; w += blockDim.x) {
+            D.rz[w] = D.red[w * 3 + 0];
+            D.bnorm[w] = sqrt(D.red[w * 3 + 2]);
+            D.relres[w] = D.bnorm[w] > 0.0 ? sqrt(D.red[w * 3 + 1]) / D.bnorm[w] : 0.0;
+            D.beta[w] = 0.0;
+            D.alpha[w] = 0.0;
+            D.iters[w] = 0;
+            D.done[w] = (C.tol > 0.0 && D.relres[w] < C.tol) || D.bnorm[w] == 0.0;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            int all = 1;
+            for (int w = 0; w < C.nvec; ++w) all &= D.done[w];
+            *D.all_done = all;
+            *D.it = 0;
+        }
+    }
+}
+
+// p_new = z + beta p_old, Ap = (I + gamma L_e) p_new; reduction <p, Ap>; alpha.
+__global__ void k_cg_a(const float *__restrict__ z, const float *__restrict__ p_old,
+                       float *__restrict__ p_new, float *__restrict__ Ap,
+                       const unsigned char *__restrict__ mask, PlsConst C, PlsDev D)
+{
+    const int v = blockIdx.y;
+    const float beta = (float)D.beta[v];
+    const float *zv = z + (int64_t)v * C.N, *pv = p_old + (int64_t)v * C.N;
+    Stencil S{mask + (int64_t)(v >> 1) * C.N, C.n, C.gamma, C.eps};
+    float acc[1] = {0.f};
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < C.N;
+         q += (int64_t)gridDim.x * blockDim.x) {
+        const int i = (int)(q / C.n), j = (int)(q % C.n);
+        float diag;
+        auto pn = [&](int64_t k) { return fmaf(beta, pv[k], zv[k]); };
+        const float a = apply_op(S, i, j, q, pn, diag);
+        const float pc = pn(q);
+        p_new[(int64_t)v * C.N + q] = pc;
+        Ap[(int64_t)v * C.N + q] = a;
+        acc[0] = fmaf(pc, a, acc[0]);
+    }
+    if (reduce_planar<1>(acc, D.part, D.red, D.ctr)) {
+        for (int w = threadIdx.x; w < C.nvec; w += blockDim.x) {
+            const double pap = D.red[w];
+            D.alpha[w] = (!D.done[w] && pap > 0.0) ? D.rz[w] / pap : 0.0;
+        }
+    }
+}
+
+// u += alpha p, r -= alpha Ap, z = r / diag; reductions <r,z>, <r,r>; beta and stop test.
+__global__ void k_cg_b(float *__restrict__ uall, const float *__restrict__ p,
+                       const float *__restrict__ Ap, float *__restrict__ r, float *__restrict__ z,
+                       const unsigned char *__restrict__ mask, PlsConst C, PlsDev D)
+{
+    const int v = blockIdx.y;
+    const float alpha = (float)D.alpha[v];
+    float *u = uall + (int64_t)v * C.N;
+    Stencil S{mask + (int64_t)(v >> 1) * C.N, C.n, C.gamma, C.eps};
+    float acc[2] = {0.f, 0.f};
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < C.N;
+         q += (int64_t)gridDim.x * blockDim.x) {
+        const int i = (int)(q / C.n), j = (int)(q % C.n);
+        const int64_t o = (int64_t)v * C.N + q;
+        float wsum = 0.f;
+        if (i > 0) wsum += S.w(q, q - C.n);
+        if (i + 1 < C.n) wsum += S.w(q, q + C.n);
+        if (j > 0) wsum += S.w(q, q - 1);
+        if (j + 1 < C.n) wsum += S.w(q, q + 1);
+        const float diag = 1.f + C.gamma * wsum;
+        u[q] = fmaf(alpha, p[o], u[q]);
+        const float rr = fmaf(-alpha, Ap[o], r[o]);
+        const float zz = rr / diag;
+        r[o] = rr;
+        z[o] = zz;
+        acc[0] = fmaf(rr, zz, acc[0]);
+        acc[1] = fmaf(rr, rr, acc[1]);
+    }
+    if (reduce_planar<2>(acc, D.part, D.red, D.ctr)) {
+        const int it = *D.it;
+        for (int w = threadIdx.x; w < C.nvec; w += blockDim.x) {
+            if (D.done[w]) {
+                D.beta[w] = 0.0;
+                continue;
+            }
+            const double rz_new = D.red[w * 2 + 0];
+            D.beta[w] = D.rz[w] != 0.0 ? rz_new / D.rz[w] : 0.0;
+            D.rz[w] = rz_new;
+            D.relres[w] = D.bnorm[w] > 0.0 ? sqrt(D.red[w * 2 + 1]) / D.bnorm[w] : 0.0;
+            D.iters[w] = it + 1;
+            if (C.tol > 0.0 && D.relres[w] < C.tol) D.done[w] = 1;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            int all = 1;
+            for (int w = 0; w < C.nvec; ++w) all &= D.done[w];
+            *D.all_done = all;
+            *D.it = it + 1;
+        }
+    }
+}
+
+}  // namespace
+}  // namespace dect
+
+using namespace dect;
+
+extern "C" dect_status dect_pls_decompose(const float *x, int n, int batch, const dect_pls_params *prm,
+                                          float *u, dect_pls_report *reports, dect_stream stream)
+{
+    if (!prm || n < 1 || batch < 0 || n > 16384) return DECT_ERR_INVALID_ARG;
+    if (batch == 0) return DECT_OK;
+    if (!x || !u) return DECT_ERR_INVALID_ARG;
+    {
+        const size_t span = (size_t)batch * 2 * n * n * sizeof(float);
+        const char *xa = (const char *)x, *ua = (const char *)u;
+        if (xa < ua + span && ua < xa + span) return DECT_ERR_INVALID_ARG;
+    }
+    if (!(prm->gamma >= 0) || !(prm->edge_eps >= 0) || prm->max_iter < 0 || !std::isfinite(prm->gamma))
+        return DECT_ERR_INVALID_ARG;
+    const double a = prm->eta[0][0], b = prm->eta[1][0], c = prm->eta[0][1], e = prm->eta[1][1];
+    const double det = a * e - b * c;
+    if (!(std::fabs(det) > 0) || !std::isfinite(det)) return DECT_ERR_INVALID_ARG;
+    if (batch > 65535 / 2) return DECT_ERR_INVALID_ARG;  // grid.y holds a vector index
+    cudaStream_t s = (cudaStream_t)stream;
+    int dev = 0;
+    DECT_CUDA(cudaGetDevice(&dev));
+
+    const int64_t N = (int64_t)n * n;
+    const int nvec = 2 * batch;
+    const int64_t want = (N + kBlock - 1) / kBlock;
+    const int gx = (int)std::max<int64_t>(1, std::min<int64_t>(want, std::max(1, (kSMs * 8) / nvec)));
+
+    // scratch from the stream-ordered pool: lay out once to size, then for real
+    const size_t nf = (size_t)nvec * N;
+    float *r = nullptr, *z = nullptr, *pa = nullptr, *pb = nullptr, *Ap = nullptr;
+    float *mh = nullptr, *ml = nullptr;
+    unsigned char *mask = nullptr;
+    PlsDev D;
+    auto layout = [&](char *base) -> size_t {
+        size_t o = 0;
+        auto take = [&](size_t nb) { char *p = base ? base + o : nullptr; o = (o + nb + 255) & ~(size_t)255; return p; };
+        r = (float *)take(nf * 4);
+        z = (float *)take(nf * 4);
+        pa = (float *)take(nf * 4);
+        pb = (float *)take(nf * 4);
+        Ap = (float *)take(nf * 4);
+        mh = (float *)take((size_t)batch * N * 4);
+        ml = (float *)take((size_t)batch * N * 4);
+        mask = (unsigned char *)take((size_t)batch * N);
+        D.part = (double *)take((size_t)gx * nvec * 3 * 8);
+        D.red = (double *)take((size_t)nvec * 3 * 8);
+        D.alpha = (double *)take((size_t)nvec * 8);
+        D.beta = (double *)take((size_t)nvec * 8);
+        D.rz = (double *)take((size_t)nvec * 8);
+        D.bnorm = (double *)take((size_t)nvec * 8);
+        D.relres = (double *)take((size_t)nvec * 8);
+        D.iters = (int *)take((size_t)nvec * 4);
+        D.done = (int *)take((size_t)nvec * 4);
+        D.it = (int *)take(4);
+        D.all_done = (int *)take(4);
+        D.ctr = (unsigned *)take(8);
+        D.maxbits = (int *)take((size_t)2 * batch * 4);
+        return o;
+    };
+    const size_t bytes = layout(nullptr);
+    char *base = nullptr;
+    DECT_CUDA(cudaMallocAsync((void **)&base, bytes, s));
+    layout(base);
+    DECT_CUDA(cudaMemsetAsync(D.ctr, 0, 8, s));
+    DECT_CUDA(cudaMemsetAsync(D.maxbits, 0, (size_t)2 * batch * 4, s));
+
+    PlsConst C;
+    C.n = n;
+    C.N = N;
+    C.nvec = nvec;
+    C.gamma = (float)prm->gamma;
+    C.eps = (float)prm->edge_eps;
+    C.tol = prm->tol;
+
+    dim3 gs((unsigned)gx, (unsigned)batch), gv((unsigned)gx, (unsigned)nvec);
+    k_prep<<<gs, kBlock, 0, s>>>(x, n, N, a, b, c, e, u, mh, ml, D.maxbits);
+    DECT_LAUNCH_CHECK();
+    k_mask<<<gs, kBlock, 0, s>>>(mh, ml, N, D.maxbits, (float)prm->edge_tau, mask);
+    DECT_LAUNCH_CHECK();
+    k_init<<<gv, kBlock, 0, s>>>(u, mask, r, z, pa, C, D);
+    DECT_LAUNCH_CHECK();
+    count_launches(3);
+
+    const int K = prm->max_iter;
+    const bool use_tol = prm->tol > 0.0;
+    const int block = 10;
+    cudaError_t err = cudaSuccess;
+    cudaStream_t cs = nullptr;
+    cudaEvent_t ev = nullptr;
+    cudaGraphExec_t gx2 = nullptr;
+    int *h_done = nullptr;
+    err = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+    if (err == cudaSuccess) err = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+    if (err == cudaSuccess) err = cudaEventRecord(ev, s);
+    if (err == cudaSuccess) err = cudaStreamWaitEvent(cs, ev, 0);
+    // two CG iterations per unit keep the p ping-pong in place
+    auto two_iters = [&](cudaStream_t st) {
+        k_cg_a<<<gv, kBlock, 0, st>>>(z, pa, pb, Ap, mask, C, D);
+        k_cg_b<<<gv, kBlock, 0, st>>>(u, pb, Ap, r, z, mask, C, D);
+        k_cg_a<<<gv, kBlock, 0, st>>>(z, pb, pa, Ap, mask, C, D);
+        k_cg_b<<<gv, kBlock, 0, st>>>(u, pa, Ap, r, z, mask, C, D);
+    };
+    if (err == cudaSuccess && K >= 2 * block) {
+        cudaGraph_t gr = nullptr;
+        err = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+        if (err == cudaSuccess) {
+            for (int q = 0; q < block; ++q) two_iters(cs);
+            err = cudaStreamEndCapture(cs, &gr);
+        }
+        if (err == cudaSuccess) err = cudaGraphInstantiate(&gx2, gr, 0);
+        if (gr) cudaGraphDestroy(gr);
+    }
+    if (err == cudaSuccess) err = cudaMallocHost((void **)&h_done, sizeof(int));
+    int done_it = 0;
+    bool finished = false;
+    if (err == cudaSuccess && use_tol) {
+        err = cudaMemcpyAsync(h_done, D.all_done, sizeof(int), cudaMemcpyDeviceToHost, cs);
+        if (err == cudaSuccess) err = cudaStreamSynchronize(cs);
+        finished = err == cudaSuccess && *h_done;
+    }
+    while (err == cudaSuccess && !finished && done_it + 2 * block <= K && gx2) {
+        err = cudaGraphLaunch(gx2, cs);
+        count_launches(4 * block);
+        done_it += 2 * block;
+        if (err == cudaSuccess && use_tol) {
+            err = cudaMemcpyAsync(h_done, D.all_done, sizeof(int), cudaMemcpyDeviceToHost, cs);
+            if (err == cudaSuccess) err = cudaStreamSynchronize(cs);
+            finished = err == cudaSuccess && *h_done;
+        }
+    }
+    // remaining iterations one by one (ping-pong parity by position)
+    float *p_cur = pa, *p_nxt = pb;
+    while (err == cudaSuccess && !finished && done_it < K) {
+        k_cg_a<<<gv, kBlock, 0, cs>>>(z, p_cur, p_nxt, Ap, mask, C, D);
+        k_cg_b<<<gv, kBlock, 0, cs>>>(u, p_nxt, Ap, r, z, mask, C, D);
+        std::swap(p_cur, p_nxt);
+        ++done_it;
+        count_launches(2);
+        err = cudaGetLastError();
+    }
+    if (err == cudaSuccess) err = cudaEventRecord(ev, cs);
+    if (err == cudaSuccess) err = cudaStreamWaitEvent(s, ev, 0);
+    std::vector<int> hit(nvec);
+    std::vector<double> hrel(nvec);
+    if (err == cudaSuccess) err = cudaMemcpyAsync(hit.data(), D.iters, nvec * 4, cudaMemcpyDeviceToHost, s);
+    if (err == cudaSuccess) err = cudaMemcpyAsync(hrel.data(), D.relres, nvec * 8, cudaMemcpyDeviceToHost, s);
+    cudaFreeAsync(base, s);
+    if (err == cudaSuccess) err = cudaStreamSynchronize(s);
+    if (gx2) cudaGraphExecDestroy(gx2);
+    if (h_done) cudaFreeHost(h_done);
+    if (ev) cudaEventDestroy(ev);
+    if (cs) cudaStreamDestroy(cs);
+    if (err != cudaSuccess) {
+        set_error("dect_pls_decompose", err);
+        return err == cudaErrorMemoryAllocation ? DECT_ERR_OOM : DECT_ERR_CUDA;
+    }
+    if (reports) {
+        for (int sl = 0; sl < batch; ++sl)
+            for (int m = 0; m < 2; ++m) {
+                reports[sl].iters[m] = hit[2 * sl + m];
+                reports[sl].relres[m] = hrel[2 * sl + m];
+            }
+    }
+    (void)dev;
+    return DECT_OK;
 }

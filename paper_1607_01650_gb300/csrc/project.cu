@@ -19,6 +19,7 @@ cudaError_t run_rows(const int64_t *ptr, const Entry *ent, int64_t rows, const f
     int64_t cap = (int64_t)kSMs * 8;
     unsigned grid = (unsigned)(want < cap ? want : cap);
     k_rows_planar<NB, G><<<grid, kBlock, 0, s>>>(ptr, ent, rows, src, src_stride, dst, dst_stride, nimg);
+    count_launches(1);
     return cudaGetLastError();
 }
 
