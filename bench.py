@@ -35,7 +35,7 @@ import synth  # noqa: E402
 
 METRIC = "DECT slices/s to 1e-4 rel. objective at 512^2/60 views (2 energies + PLS)"
 UNIT = "slices/s"
-MU, RHO, BETA = 16.0, 256.0, (1.0, 0.6)
+MU, RHO, BETA = 4.0, 256.0, (1.0, 0.6)
 TOL = 1e-4
 I0 = 2e5
 PLS = dict(gamma=0.1, edge_tau=0.2, edge_eps=0.05, max_iter=500, tol=1e-6)
@@ -49,7 +49,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--slices", type=int, default=16, help="slices per step per GPU")
-    ap.add_argument("--max-iter", type=int, default=1000)
+    ap.add_argument("--max-iter", type=int, default=2000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     return ap.parse_args()

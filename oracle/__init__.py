@@ -243,8 +243,8 @@ BB1, CAUCHY = 0, 1
 @dataclasses.dataclass
 class AdmParams:
     """Eq. (6)-(10) parameters (values are readings; the paper gives ranges only)."""
-    mu: float = 256.0
-    rho: float = 64.0
+    mu: float = 4.0
+    rho: float = 256.0
     xi: Optional[float] = None     # None -> xi = rho
     step_rule: int = CAUCHY
     max_iter: int = 100

@@ -239,7 +239,7 @@ BB1, CAUCHY = 0, 1
 @dataclasses.dataclass
 class AdmParams:
     """Parameters of Eq. (3)-(10); see dect_adm_params in include/dect.h."""
-    mu: float = 16.0
+    mu: float = 4.0
     rho: float = 256.0
     xi: float = 0.0                     # <= 0: xi = rho
     beta: Tuple[float, float] = (1.0, 0.6)

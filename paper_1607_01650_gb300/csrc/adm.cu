@@ -19,12 +19,12 @@
 // table entry gathers one contiguous vector of all channels.
 //
 // Kernel sequence per iteration (captured in a CUDA graph):
-//   k_step   f -= alpha G, r -= alpha q                 ; |r|^2
-//   k_tv     lambda step, z-shrink, p                    ; |grad f|_TV
+//   k_tv     f -= alpha G, r -= alpha q, lambda step, z-shrink, p
+//                                                        ; |grad f|_TV, |r|^2
 //   k_bwd    G = mu A^T r + grad^T p  (pixel-major table) ; |G|^2
-//   k_gnorm                                              ; |grad G|^2
-//   k_fwd    q = A G  (ray-major table)                  ; |q|^2, then the
-//            last block forms Phi^k, the stopping test and alpha^k in FP64.
+//   k_fwd    q = A G  (ray-major table)                  ; |grad G|^2, |q|^2,
+//            then the last block forms Phi^k, the stopping test and
+//            alpha^k in FP64.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -39,15 +39,18 @@ namespace {
 
 constexpr int kBlock = 256;
 constexpr int kGrid = kSMs * 8;  // fixed grid of every reducing kernel
+constexpr int kTile = 8;         // A^T kernel: 8 x 8 pixel tiles per block
 
-enum { R_RR = 0, R_TV, R_GG, R_DD, R_QQ, R_COUNT };
+// reduction slots; (TV, RR) and (DD, QQ) are reduced together
+enum { R_TV = 0, R_RR = 1, R_DD = 2, R_QQ = 3, R_GG = 4, R_COUNT = 5 };
+enum { C_TV = 0, C_BWD = 1, C_FWD = 2, C_COUNT = 3 };
 
 struct AdmDev {
     // per-channel scalars
     double *red;       // [R_COUNT][NB] reduction results
-    double *part;      // [R_COUNT][kGrid][NB] block partials
-    unsigned *ctr;     // [R_COUNT] last-block counters
-    double *alpha;     // [NB] step applied by the next k_step
+    double *part;      // [C_COUNT][2][kGrid][NB] block partials, per kernel
+    unsigned *ctr;     // [C_COUNT] last-block counters
+    double *alpha;     // [NB] step applied by the next k_tv
     double *c_prev;    // [NB]
     double *phi_prev;  // [NB]
     double *rel;       // [NB]
@@ -69,42 +72,10 @@ struct AdmConst {
     int nimg;
 };
 
-// ---------------------------------------------------------------------------
 template <int NB>
-__global__ void __launch_bounds__(kBlock) k_step(float *__restrict__ f, const float *__restrict__ G,
-                                                 float *__restrict__ r, const float *__restrict__ q,
-                                                 AdmConst C, AdmDev D)
+__device__ __forceinline__ double *part_of(const AdmDev &D, int kernel)
 {
-    constexpr int VW = Batch<NB>::VW, CPB = Batch<NB>::CPB;
-    __shared__ double smem[(kBlock / 32) * NB];
-    const int vl = threadIdx.x % CPB;
-    Vec<VW> a;
-#pragma unroll
-    for (int c = 0; c < VW; ++c) a.v[c] = (float)D.alpha[vl * VW + c];
-    Vec<VW> acc;
-    acc.zero();
-    const int64_t total = (C.N + C.M) * CPB;
-    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
-         t += (int64_t)gridDim.x * blockDim.x) {
-        if (t < C.N * CPB) {
-            float *fp = f + t * VW;
-            Vec<VW> fv = ld_v<VW>(fp), gv = ld_v<VW>(G + t * VW);
-#pragma unroll
-            for (int c = 0; c < VW; ++c) fv.v[c] = fmaf(-a.v[c], gv.v[c], fv.v[c]);
-            st_v<VW>(fp, fv);
-        } else {
-            int64_t u = t - C.N * CPB;
-            float *rp = r + u * VW;
-            Vec<VW> rv = ld_v<VW>(rp), qv = ld_v<VW>(q + u * VW);
-#pragma unroll
-            for (int c = 0; c < VW; ++c) {
-                rv.v[c] = fmaf(-a.v[c], qv.v[c], rv.v[c]);
-                acc.v[c] = fmaf(rv.v[c], rv.v[c], acc.v[c]);
-            }
-            st_v<VW>(rp, rv);
-        }
-    }
-    reduce_images<NB>(acc, D.part + (size_t)R_RR * kGrid * NB, D.red + R_RR * NB, D.ctr + R_RR, smem);
+    return D.part + (size_t)kernel * 2 * kGrid * NB;
 }
 
 // z-shrink of Eq. (8) per pixel on the 2-vector w (reading: w / |w| for sign).
@@ -122,28 +93,59 @@ __device__ __forceinline__ void shrink2(float w0, float w1, float t, float &z0, 
     }
 }
 
+// ---------------------------------------------------------------------------
+// Start of iteration k: apply the previous step (f^k = f^{k-1} - alpha G,
+// r^k = r^{k-1} - alpha q; alpha = 0 at k = 0), then the lambda step of the
+// previous iteration, the z-shrink and p = rho(grad f - z) - lambda.
+// Reduces |grad f^k|_TV and |r^k|^2.  f is double-buffered (f_in -> f_out)
+// because the stencil reads neighbours of the updated image.
+// final_pass: only the f / r step and the two norms (the result's objective).
+// ---------------------------------------------------------------------------
 template <int NB>
-__global__ void __launch_bounds__(kBlock) k_tv(const float *__restrict__ f, float *__restrict__ lam,
+__global__ void __launch_bounds__(kBlock) k_tv(const float *__restrict__ f_in, float *__restrict__ f_out,
+                                               const float *__restrict__ G, float *__restrict__ lam,
                                                float *__restrict__ z, float *__restrict__ p,
+                                               float *__restrict__ r, const float *__restrict__ q,
                                                AdmConst C, AdmDev D, int final_pass)
 {
     constexpr int VW = Batch<NB>::VW, CPB = Batch<NB>::CPB;
-    __shared__ double smem[(kBlock / 32) * NB];
+    __shared__ double smem[reduce_smem_doubles<NB>(2)];
     const int k = *D.k;
     const float inv_rho = 1.0f / C.rho;
-    Vec<VW> acc;
-    acc.zero();
-    const int64_t total = C.N * CPB;
+    const int vl = threadIdx.x % CPB;
+    Vec<VW> a;
+#pragma unroll
+    for (int c = 0; c < VW; ++c) a.v[c] = (float)D.alpha[vl * VW + c];
+    Vec<VW> acc[2];
+    acc[0].zero();
+    acc[1].zero();
     const int64_t sN = C.N * NB;  // component stride of lam, z, p
-    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
-         t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t row = (int64_t)C.n * NB;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < C.N * CPB; t += stride) {
         const int64_t pix = t / CPB;
-        const int vl = (int)(t % CPB);
         const int i = (int)(pix / C.n), j = (int)(pix % C.n);
         const int64_t o = pix * NB + vl * VW;
-        Vec<VW> fc = ld_v<VW>(f + o), fu, fl;
-        if (i > 0) fu = ld_v<VW>(f + o - (int64_t)C.n * NB); else fu = fc;
-        if (j > 0) fl = ld_v<VW>(f + o - NB); else fl = fc;
+        Vec<VW> fc = ld_v<VW>(f_in + o), gc = ld_v<VW>(G + o), fu, fl;
+#pragma unroll
+        for (int c = 0; c < VW; ++c) fc.v[c] = fmaf(-a.v[c], gc.v[c], fc.v[c]);
+        st_v<VW>(f_out + o, fc);
+        if (i > 0) {
+            fu = ld_v<VW>(f_in + o - row);
+            Vec<VW> gu = ld_v<VW>(G + o - row);
+#pragma unroll
+            for (int c = 0; c < VW; ++c) fu.v[c] = fmaf(-a.v[c], gu.v[c], fu.v[c]);
+        } else {
+            fu = fc;
+        }
+        if (j > 0) {
+            fl = ld_v<VW>(f_in + o - NB);
+            Vec<VW> gl = ld_v<VW>(G + o - NB);
+#pragma unroll
+            for (int c = 0; c < VW; ++c) fl.v[c] = fmaf(-a.v[c], gl.v[c], fl.v[c]);
+        } else {
+            fl = fc;
+        }
         Vec<VW> l0, l1, z0, z1;
         if (!final_pass) {
             l0 = ld_v<VW>(lam + o);
@@ -158,7 +160,7 @@ __global__ void __launch_bounds__(kBlock) k_tv(const float *__restrict__ f, floa
         for (int c = 0; c < VW; ++c) {
             float g0 = fc.v[c] - fu.v[c];   // Eq. (2), 0 on the first row
             float g1 = fc.v[c] - fl.v[c];   // Eq. (2), 0 on the first column
-            acc.v[c] += sqrtf(g0 * g0 + g1 * g1);
+            acc[0].v[c] += sqrtf(g0 * g0 + g1 * g1);
             if (final_pass) continue;
             float a0 = l0.v[c], a1 = l1.v[c];
             if (k > 0) {  // lambda^k = lambda^{k-1} - xi (grad f^k - z^k), Eq. (7)
@@ -183,10 +185,21 @@ __global__ void __launch_bounds__(kBlock) k_tv(const float *__restrict__ f, floa
             st_v<VW>(p + sN + o, p1);
         }
     }
-    reduce_images<NB>(acc, D.part + (size_t)R_TV * kGrid * NB, D.red + R_TV * NB, D.ctr + R_TV, smem);
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < C.M * CPB; t += stride) {
+        float *rp = r + t * VW;
+        Vec<VW> rv = ld_v<VW>(rp), qv = ld_v<VW>(q + t * VW);
+#pragma unroll
+        for (int c = 0; c < VW; ++c) {
+            rv.v[c] = fmaf(-a.v[c], qv.v[c], rv.v[c]);
+            acc[1].v[c] = fmaf(rv.v[c], rv.v[c], acc[1].v[c]);
+        }
+        st_v<VW>(rp, rv);
+    }
+    reduce_images<NB, 2>(acc, part_of<NB>(D, C_TV), D.red + R_TV * NB, D.ctr + C_TV, smem);
 }
 
-// G = mu A^T r + grad^T p over the pixel-major table (one row = one pixel).
+// G = mu A^T r + grad^T p over the pixel-major table.  A block takes 8 x 8
+// pixel tiles, so the sinogram lines its pixels gather are shared in L1.
 template <int NB, int G_>
 __global__ void __launch_bounds__(kBlock) k_bwd(const int64_t *__restrict__ colptr,
                                                 const Entry *__restrict__ tent,
@@ -194,63 +207,45 @@ __global__ void __launch_bounds__(kBlock) k_bwd(const int64_t *__restrict__ colp
                                                 float *__restrict__ G, AdmConst C, AdmDev D)
 {
     constexpr int VW = Batch<NB>::VW, LPE = Batch<NB>::CPB;
-    __shared__ double smem[(kBlock / 32) * NB];
+    constexpr int RPS = kBlock / G_;  // pixels per block step
+    static_assert((kTile * kTile) % RPS == 0, "tile split");
+    __shared__ double smem[reduce_smem_doubles<NB>(1)];
     const int lr = threadIdx.x % G_, grp = lr / LPE, vl = lr % LPE;
-    const int64_t rpb = kBlock / G_;
     const int64_t sN = C.N * NB;
-    Vec<VW> nrm;
-    nrm.zero();
-    for (int64_t row0 = (int64_t)blockIdx.x * rpb; row0 < C.N; row0 += (int64_t)gridDim.x * rpb) {
-        const int64_t pix = row0 + threadIdx.x / G_;
-        int64_t b = 0, e = 0;
-        if (pix < C.N) {
-            b = colptr[pix];
-            e = colptr[pix + 1];
-        }
-        Vec<VW> acc = row_dot<NB, G_, true>(tent, b, e, r, 0, lr);
-        if (pix < C.N && grp == 0) {
-            const int i = (int)(pix / C.n), j = (int)(pix % C.n);
-            const int64_t o = pix * NB + vl * VW;
-            Vec<VW> p0 = ld_v<VW>(p + o), p1 = ld_v<VW>(p + sN + o), pd, pr;
-            if (i + 1 < C.n) pd = ld_v<VW>(p + o + (int64_t)C.n * NB); else pd.zero();
-            if (j + 1 < C.n) pr = ld_v<VW>(p + sN + o + NB); else pr.zero();
-            Vec<VW> out;
-#pragma unroll
-            for (int c = 0; c < VW; ++c) {
-                float gt = (i > 0 ? p0.v[c] : 0.f) - pd.v[c] + (j > 0 ? p1.v[c] : 0.f) - pr.v[c];
-                out.v[c] = fmaf(C.mu, acc.v[c], gt);
-                nrm.v[c] = fmaf(out.v[c], out.v[c], nrm.v[c]);
+    const int tiles_x = (C.n + kTile - 1) / kTile;
+    const int ntiles = tiles_x * tiles_x;
+    Vec<VW> nrm[1];
+    nrm[0].zero();
+    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const int ty = tile / tiles_x, tx = tile % tiles_x;
+        for (int s0 = 0; s0 < kTile * kTile; s0 += RPS) {
+            const int slot = s0 + threadIdx.x / G_;
+            const int i = ty * kTile + slot / kTile, j = tx * kTile + slot % kTile;
+            const bool ok = i < C.n && j < C.n;
+            const int64_t pix = (int64_t)i * C.n + j;
+            int64_t b = 0, e = 0;
+            if (ok) {
+                b = colptr[pix];
+                e = colptr[pix + 1];
             }
-            st_v<VW>(G + o, out);
-        }
-    }
-    reduce_images<NB>(nrm, D.part + (size_t)R_GG * kGrid * NB, D.red + R_GG * NB, D.ctr + R_GG, smem);
-}
-
-template <int NB>
-__global__ void __launch_bounds__(kBlock) k_gnorm(const float *__restrict__ G, AdmConst C, AdmDev D)
-{
-    constexpr int VW = Batch<NB>::VW, CPB = Batch<NB>::CPB;
-    __shared__ double smem[(kBlock / 32) * NB];
-    Vec<VW> acc;
-    acc.zero();
-    const int64_t total = C.N * CPB;
-    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
-         t += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t pix = t / CPB;
-        const int vl = (int)(t % CPB);
-        const int i = (int)(pix / C.n), j = (int)(pix % C.n);
-        const int64_t o = pix * NB + vl * VW;
-        Vec<VW> gc = ld_v<VW>(G + o), gu, gl;
-        if (i > 0) gu = ld_v<VW>(G + o - (int64_t)C.n * NB); else gu = gc;
-        if (j > 0) gl = ld_v<VW>(G + o - NB); else gl = gc;
+            Vec<VW> acc = row_dot<NB, G_, true>(tent, b, e, r, 0, lr);
+            if (ok && grp == 0) {
+                const int64_t o = pix * NB + vl * VW;
+                Vec<VW> p0 = ld_v<VW>(p + o), p1 = ld_v<VW>(p + sN + o), pd, pr;
+                if (i + 1 < C.n) pd = ld_v<VW>(p + o + (int64_t)C.n * NB); else pd.zero();
+                if (j + 1 < C.n) pr = ld_v<VW>(p + sN + o + NB); else pr.zero();
+                Vec<VW> out;
 #pragma unroll
-        for (int c = 0; c < VW; ++c) {
-            float d0 = gc.v[c] - gu.v[c], d1 = gc.v[c] - gl.v[c];
-            acc.v[c] += d0 * d0 + d1 * d1;
+                for (int c = 0; c < VW; ++c) {
+                    float gt = (i > 0 ? p0.v[c] : 0.f) - pd.v[c] + (j > 0 ? p1.v[c] : 0.f) - pr.v[c];
+                    out.v[c] = fmaf(C.mu, acc.v[c], gt);
+                    nrm[0].v[c] = fmaf(out.v[c], out.v[c], nrm[0].v[c]);
+                }
+                st_v<VW>(G + o, out);
+            }
         }
     }
-    reduce_images<NB>(acc, D.part + (size_t)R_DD * kGrid * NB, D.red + R_DD * NB, D.ctr + R_DD, smem);
+    reduce_images<NB, 1>(nrm, part_of<NB>(D, C_BWD), D.red + R_GG * NB, D.ctr + C_BWD, smem);
 }
 
 // Step size and stopping test, FP64, one thread per channel (last block of k_fwd).
@@ -297,7 +292,8 @@ __device__ void adm_finish(const AdmConst &C, const AdmDev &D)
     }
 }
 
-// q = A G over the ray-major table (MODE 1), or r = A f - beta m (MODE 0).
+// MODE 1: |grad G|^2, then q = A G over the ray-major table and |q|^2; the
+// last block forms the step.  MODE 0: r = A f - beta m (set-up).
 template <int NB, int G_, int MODE>
 __global__ void __launch_bounds__(kBlock) k_fwd(const int64_t *__restrict__ rowptr,
                                                 const Entry *__restrict__ ent,
@@ -305,12 +301,30 @@ __global__ void __launch_bounds__(kBlock) k_fwd(const int64_t *__restrict__ rowp
                                                 const float *__restrict__ m_planar,
                                                 const float *__restrict__ beta_img, AdmConst C, AdmDev D)
 {
-    constexpr int VW = Batch<NB>::VW, LPE = Batch<NB>::CPB;
-    __shared__ double smem[(kBlock / 32) * NB];
+    constexpr int VW = Batch<NB>::VW, LPE = Batch<NB>::CPB, CPB = Batch<NB>::CPB;
+    __shared__ double smem[reduce_smem_doubles<NB>(2)];
     const int lr = threadIdx.x % G_, grp = lr / LPE, vl = lr % LPE;
     const int64_t rpb = kBlock / G_;
-    Vec<VW> nrm;
-    nrm.zero();
+    Vec<VW> nrm[2];
+    nrm[0].zero();
+    nrm[1].zero();
+    if (MODE == 1) {
+        const int64_t row = (int64_t)C.n * NB;
+        for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < C.N * CPB;
+             t += (int64_t)gridDim.x * blockDim.x) {
+            const int64_t pix = t / CPB;
+            const int i = (int)(pix / C.n), j = (int)(pix % C.n);
+            const int64_t o = pix * NB + (t % CPB) * VW;
+            Vec<VW> gc = ld_v<VW>(src + o), gu, gl;
+            if (i > 0) gu = ld_v<VW>(src + o - row); else gu = gc;
+            if (j > 0) gl = ld_v<VW>(src + o - NB); else gl = gc;
+#pragma unroll
+            for (int c = 0; c < VW; ++c) {
+                float d0 = gc.v[c] - gu.v[c], d1 = gc.v[c] - gl.v[c];
+                nrm[0].v[c] += d0 * d0 + d1 * d1;
+            }
+        }
+    }
     for (int64_t row0 = (int64_t)blockIdx.x * rpb; row0 < C.M; row0 += (int64_t)gridDim.x * rpb) {
         const int64_t ray = row0 + threadIdx.x / G_;
         int64_t b = 0, e = 0;
@@ -329,14 +343,13 @@ __global__ void __launch_bounds__(kBlock) k_fwd(const int64_t *__restrict__ rowp
                 }
             } else {
 #pragma unroll
-                for (int c = 0; c < VW; ++c) nrm.v[c] = fmaf(acc.v[c], acc.v[c], nrm.v[c]);
+                for (int c = 0; c < VW; ++c) nrm[1].v[c] = fmaf(acc.v[c], acc.v[c], nrm[1].v[c]);
             }
             st_v<VW>(dst + ray * NB + vl * VW, acc);
         }
     }
     if (MODE == 1) {
-        if (reduce_images<NB>(nrm, D.part + (size_t)R_QQ * kGrid * NB, D.red + R_QQ * NB,
-                              D.ctr + R_QQ, smem))
+        if (reduce_images<NB, 2>(nrm, part_of<NB>(D, C_FWD), D.red + R_DD * NB, D.ctr + C_FWD, smem))
             adm_finish<NB>(C, D);
     }
 }
@@ -374,7 +387,7 @@ struct Kern {
 };
 
 struct Work {
-    float *f, *G, *lam, *z, *p, *r, *q, *beta;
+    float *f[2], *G, *lam, *z, *p, *r, *q, *beta;
     double *dbl;
     int *ints;
     unsigned *ctr;
@@ -386,23 +399,22 @@ struct IterEvents {
     cudaEvent_t b0, b1, f0, f1;
 };
 
+// Iteration with f read from f[par] and written to f[1 - par].
 template <int NB>
-void enqueue_iteration(const dect_plan *P, const Work &W, const AdmConst &C, cudaStream_t s,
+void enqueue_iteration(const dect_plan *P, const Work &W, const AdmConst &C, int par, cudaStream_t s,
                        const IterEvents *ev)
 {
-    k_step<NB><<<kGrid, kBlock, 0, s>>>(W.f, W.G, W.r, W.q, C, W.D);
-    k_tv<NB><<<kGrid, kBlock, 0, s>>>(W.f, W.lam, W.z, W.p, C, W.D, 0);
+    k_tv<NB><<<kGrid, kBlock, 0, s>>>(W.f[par], W.f[1 - par], W.G, W.lam, W.z, W.p, W.r, W.q, C, W.D, 0);
     if (ev) cudaEventRecordWithFlags(ev->b0, s, cudaEventRecordExternal);
     k_bwd<NB, Kern<NB>::GB><<<kGrid, kBlock, 0, s>>>(P->colptr, P->tent, W.r, W.p, W.G, C, W.D);
     if (ev) cudaEventRecordWithFlags(ev->b1, s, cudaEventRecordExternal);
-    k_gnorm<NB><<<kGrid, kBlock, 0, s>>>(W.G, C, W.D);
     if (ev) cudaEventRecordWithFlags(ev->f0, s, cudaEventRecordExternal);
     k_fwd<NB, Kern<NB>::GF, 1><<<kGrid, kBlock, 0, s>>>(P->rowptr, P->ent, W.G, W.q, nullptr, nullptr,
                                                          C, W.D);
     if (ev) cudaEventRecordWithFlags(ev->f1, s, cudaEventRecordExternal);
 }
 
-constexpr int kKernelsPerIteration = 5;
+constexpr int kKernelsPerIteration = 3;
 
 template <int NB>
 dect_status run_chunk(const dect_plan *P, const float *m, float *x, int nimg,
@@ -426,13 +438,14 @@ dect_status run_chunk(const dect_plan *P, const float *m, float *x, int nimg,
 
     // one allocation for everything: lay out once to size, then for real
     const size_t nf = (size_t)N * NB, nr = (size_t)M * NB;
-    const size_t ndbl = (size_t)R_COUNT * NB + (size_t)R_COUNT * kGrid * NB + 4 * NB;
+    const size_t ndbl = (size_t)R_COUNT * NB + (size_t)C_COUNT * 2 * kGrid * NB + 4 * NB;
     const size_t nint = 4 * NB + 8;
     Work W;
     auto layout = [&](char *b) -> size_t {
         size_t o = 0;
         auto take = [&](size_t nbytes) { char *p = b ? b + o : nullptr; o = (o + nbytes + 255) & ~(size_t)255; return p; };
-        W.f = (float *)take(nf * 4);
+        W.f[0] = (float *)take(nf * 4);
+        W.f[1] = (float *)take(nf * 4);
         W.G = (float *)take(nf * 4);
         W.lam = (float *)take(2 * nf * 4);
         W.z = (float *)take(2 * nf * 4);
@@ -442,7 +455,7 @@ dect_status run_chunk(const dect_plan *P, const float *m, float *x, int nimg,
         W.beta = (float *)take(64 * 4);
         W.dbl = (double *)take(ndbl * 8);
         W.ints = (int *)take(nint * 4);
-        W.ctr = (unsigned *)take(R_COUNT * 4);
+        W.ctr = (unsigned *)take(C_COUNT * 4);
         return o;
     };
     const size_t bytes = layout(nullptr);
@@ -453,7 +466,7 @@ dect_status run_chunk(const dect_plan *P, const float *m, float *x, int nimg,
     AdmDev &D = W.D;
     D.red = W.dbl;
     D.part = D.red + R_COUNT * NB;
-    D.alpha = D.part + (size_t)R_COUNT * kGrid * NB;
+    D.alpha = D.part + (size_t)C_COUNT * 2 * kGrid * NB;
     D.c_prev = D.alpha + NB;
     D.phi_prev = D.c_prev + NB;
     D.rel = D.phi_prev + NB;
@@ -471,32 +484,34 @@ dect_status run_chunk(const dect_plan *P, const float *m, float *x, int nimg,
         hbeta[b] = beta_host[b];
         hact[b] = 1;
     }
-    // zero state; G = q = 0 and alpha = 0 make the first k_step a no-op
+    // zero state; G = q = 0 and alpha = 0 make the first step of k_tv a no-op
     DECT_CUDA(cudaMemsetAsync(base, 0, bytes, s));
     DECT_CUDA(cudaMemcpyAsync(W.beta, hbeta.data(), 64 * 4, cudaMemcpyHostToDevice, s));
     DECT_CUDA(cudaMemcpyAsync(D.active, hact.data(), NB * 4, cudaMemcpyHostToDevice, s));
 
     const int64_t tn = (int64_t)N * NB;
     if (prm->warm_start) {
-        k_pack<NB><<<(unsigned)((tn + 255) / 256), 256, 0, s>>>(x, W.f, N, nimg, W.beta);
+        k_pack<NB><<<(unsigned)((tn + 255) / 256), 256, 0, s>>>(x, W.f[0], N, nimg, W.beta);
         DECT_LAUNCH_CHECK();
         count_launches(1);
     }
     // r^0 = A f^0 - beta m
-    k_fwd<NB, Kern<NB>::GF, 0><<<kGrid, kBlock, 0, s>>>(P->rowptr, P->ent, W.f, W.r, m, W.beta, C, D);
+    k_fwd<NB, Kern<NB>::GF, 0><<<kGrid, kBlock, 0, s>>>(P->rowptr, P->ent, W.f[0], W.r, m, W.beta, C, D);
     DECT_LAUNCH_CHECK();
     count_launches(1);
 
-    // iterations: CUDA graphs of `block` iterations
+    // iterations: CUDA graphs of `block` iterations (an even number, so the
+    // f double buffer returns to the same parity) and single-iteration graphs
+    // of either parity for the remainder
     const int K = prm->max_iter;
     const bool use_tol = prm->rel_obj_tol > 0.0;
     int block = use_tol ? (prm->check_every > 0 ? prm->check_every : 10) : 10;
-    block = std::max(1, std::min(block, std::max(K, 1)));
+    block = std::max(2, block + (block & 1));
     cudaStream_t cs = nullptr;
     DECT_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
     cudaEvent_t ev = nullptr;
     DECT_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
-    std::vector<IterEvents> evs;  // [block] for the block graph, then [1] for the single graph
+    std::vector<IterEvents> evs;  // [block] for the block graph, then [2] for the single graphs
     auto destroy_events = [&]() {
         for (auto &e : evs) {
             cudaEventDestroy(e.b0); cudaEventDestroy(e.b1);
@@ -506,7 +521,7 @@ dect_status run_chunk(const dect_plan *P, const float *m, float *x, int nimg,
     };
     cudaError_t err = cudaSuccess;
     if (prof) {
-        evs.resize(block + 1);
+        evs.resize(block + 2);
         for (auto &e : evs) {
             if (err == cudaSuccess) err = cudaEventCreate(&e.b0);
             if (err == cudaSuccess) err = cudaEventCreate(&e.b1);
@@ -514,13 +529,13 @@ dect_status run_chunk(const dect_plan *P, const float *m, float *x, int nimg,
             if (err == cudaSuccess) err = cudaEventCreate(&e.f1);
         }
     }
-    cudaGraphExec_t gx_block = nullptr, gx_one = nullptr;
-    auto make_graph = [&](int iters, int ev0, cudaGraphExec_t *out) -> cudaError_t {
+    cudaGraphExec_t gx_block = nullptr, gx_one[2] = {nullptr, nullptr};
+    auto make_graph = [&](int iters, int par0, int ev0, cudaGraphExec_t *out) -> cudaError_t {
         cudaGraph_t gr = nullptr;
         cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
         if (e != cudaSuccess) return e;
         for (int it = 0; it < iters; ++it)
-            enqueue_iteration<NB>(P, W, C, cs, prof ? &evs[ev0 + it] : nullptr);
+            enqueue_iteration<NB>(P, W, C, (par0 + it) & 1, cs, prof ? &evs[ev0 + it] : nullptr);
         e = cudaStreamEndCapture(cs, &gr);
         if (e != cudaSuccess) return e;
         e = cudaGraphInstantiate(out, gr, 0);
@@ -545,8 +560,11 @@ dect_status run_chunk(const dect_plan *P, const float *m, float *x, int nimg,
     // the caller's stream orders the set-up; the capture stream runs the loop
     if (err == cudaSuccess) err = cudaEventRecord(ev, s);
     if (err == cudaSuccess) err = cudaStreamWaitEvent(cs, ev, 0);
-    if (err == cudaSuccess && K >= block) err = make_graph(block, 0, &gx_block);
-    if (err == cudaSuccess && K % block) err = make_graph(1, block, &gx_one);
+    if (err == cudaSuccess && K >= block) err = make_graph(block, 0, 0, &gx_block);
+    if (err == cudaSuccess && K % block) {
+        err = make_graph(1, 0, block, &gx_one[0]);
+        if (err == cudaSuccess) err = make_graph(1, 1, block + 1, &gx_one[1]);
+    }
     int *h_done = nullptr;
     if (err == cudaSuccess) err = cudaMallocHost((void **)&h_done, sizeof(int));
     if (h_done) *h_done = 0;
@@ -564,18 +582,19 @@ dect_status run_chunk(const dect_plan *P, const float *m, float *x, int nimg,
     }
     bool finished = use_tol && err == cudaSuccess && *h_done;
     while (err == cudaSuccess && !finished && done_iters < K) {
-        err = cudaGraphLaunch(gx_one, cs);
+        const int par = done_iters & 1;
+        err = cudaGraphLaunch(gx_one[par], cs);
         count_launches(kKernelsPerIteration);
         ++done_iters;
-        if (err == cudaSuccess) err = collect(1, block);
+        if (err == cudaSuccess) err = collect(1, block + par);
     }
-    // final update f^K = f^{K-1} - alpha G and the objective at the result
+    // final step f^K = f^{K-1} - alpha G and the objective at the result
+    const int par = done_iters & 1;
     if (err == cudaSuccess) {
-        k_step<NB><<<kGrid, kBlock, 0, cs>>>(W.f, W.G, W.r, W.q, C, D);
-        k_tv<NB><<<kGrid, kBlock, 0, cs>>>(W.f, W.lam, W.z, W.p, C, D, 1);
-        k_unpack<NB><<<(unsigned)((tn + 255) / 256), 256, 0, cs>>>(W.f, x, N, nimg, W.beta);
+        k_tv<NB><<<kGrid, kBlock, 0, cs>>>(W.f[par], W.f[1 - par], W.G, W.lam, W.z, W.p, W.r, W.q, C, D, 1);
+        k_unpack<NB><<<(unsigned)((tn + 255) / 256), 256, 0, cs>>>(W.f[1 - par], x, N, nimg, W.beta);
         err = cudaGetLastError();
-        count_launches(3);
+        count_launches(2);
     }
     if (err == cudaSuccess) err = cudaEventRecord(ev, cs);
     if (err == cudaSuccess) err = cudaStreamWaitEvent(s, ev, 0);
@@ -595,7 +614,8 @@ dect_status run_chunk(const dect_plan *P, const float *m, float *x, int nimg,
     cudaFreeAsync(base, s);
     if (err == cudaSuccess) err = cudaStreamSynchronize(s);
     if (gx_block) cudaGraphExecDestroy(gx_block);
-    if (gx_one) cudaGraphExecDestroy(gx_one);
+    if (gx_one[0]) cudaGraphExecDestroy(gx_one[0]);
+    if (gx_one[1]) cudaGraphExecDestroy(gx_one[1]);
     if (h_done) cudaFreeHost(h_done);
     destroy_events();
     cudaEventDestroy(ev);

@@ -83,32 +83,40 @@ __device__ __forceinline__ Entry ld_entry(const Entry *p)
 }
 
 // ---------------------------------------------------------------------------
-// Deterministic per-image reduction: every thread holds VW partial values for
-// images (lane % CPB) * VW + c.  Values are summed in FP32 inside a warp and
-// in FP64 across warps and blocks, always in the same order.  The block that
-// finishes last writes the grid total per image to out[] and returns true
-// (in every thread of that block); `counter` is reset for the next launch.
-// smem must hold (blockDim.x / 32) * NB doubles.
+// Deterministic per-image reduction of K quantities at once: every thread
+// holds K vectors of VW partial values for images (lane % CPB) * VW + c.
+// Values are summed in FP32 inside a warp and in FP64 across warps and
+// blocks, always in the same order.  The block that finishes last writes the
+// grid totals to out[k][img] and returns true (in every thread of that
+// block); `counter` is reset for the next launch.  Blocks have 256 threads;
+// smem must hold K * max(8, 256 / NB) * NB doubles; part holds
+// K * gridDim.x * NB doubles.
 // ---------------------------------------------------------------------------
-template <int NB>
-__device__ __forceinline__ bool reduce_images(Vec<Batch<NB>::VW> v, double *__restrict__ part,
+template <int NB, int K>
+__device__ __forceinline__ bool reduce_images(Vec<Batch<NB>::VW> (&v)[K], double *__restrict__ part,
                                               double *__restrict__ out, unsigned *counter,
                                               double *smem)
 {
     constexpr int VW = Batch<NB>::VW, CPB = Batch<NB>::CPB;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const size_t pstride = (size_t)gridDim.x * NB;
 #pragma unroll
-    for (int off = CPB; off < 32; off <<= 1)
+    for (int q = 0; q < K; ++q)
 #pragma unroll
-        for (int c = 0; c < VW; ++c) v.v[c] += __shfl_xor_sync(0xffffffffu, v.v[c], off);
+        for (int off = CPB; off < 32; off <<= 1)
+#pragma unroll
+            for (int c = 0; c < VW; ++c) v[q].v[c] += __shfl_xor_sync(0xffffffffu, v[q].v[c], off);
     if (lane < CPB)
 #pragma unroll
-        for (int c = 0; c < VW; ++c) smem[warp * NB + lane * VW + c] = (double)v.v[c];
+        for (int q = 0; q < K; ++q)
+#pragma unroll
+            for (int c = 0; c < VW; ++c) smem[(q * nw + warp) * NB + lane * VW + c] = (double)v[q].v[c];
     __syncthreads();
-    if (threadIdx.x < NB) {
+    if (threadIdx.x < K * NB) {
+        const int q = threadIdx.x / NB, img = threadIdx.x % NB;
         double s = 0.0;
-        for (int w = 0; w < nw; ++w) s += smem[w * NB + threadIdx.x];
-        part[(size_t)blockIdx.x * NB + threadIdx.x] = s;
+        for (int w = 0; w < nw; ++w) s += smem[(q * nw + w) * NB + img];
+        part[q * pstride + (size_t)blockIdx.x * NB + img] = s;
     }
     __threadfence();
     __syncthreads();
@@ -117,23 +125,50 @@ __device__ __forceinline__ bool reduce_images(Vec<Batch<NB>::VW> v, double *__re
     __syncthreads();
     if (!last) return false;
     __threadfence();
-    if (threadIdx.x < NB) {
-        double s = 0.0;
-        for (unsigned b = 0; b < gridDim.x; ++b) s += __ldcg(&part[(size_t)b * NB + threadIdx.x]);
-        out[threadIdx.x] = s;
+    // grid total: SPLIT threads per image each sum a fixed stride of the block
+    // partials, then one thread per image adds the SPLIT sub-sums in order
+    constexpr int SPLIT = 256 / NB;
+    static_assert(SPLIT * NB == 256, "reduce_images needs 256-thread blocks");
+    const int img = threadIdx.x % NB, sub = threadIdx.x / NB;
+    double s[K];
+#pragma unroll
+    for (int q = 0; q < K; ++q) {
+        s[q] = 0.0;
+#pragma unroll 4
+        for (unsigned b = sub; b < gridDim.x; b += SPLIT) s[q] += __ldcg(&part[q * pstride + (size_t)b * NB + img]);
+    }
+    __syncthreads();  // smem is reused below
+#pragma unroll
+    for (int q = 0; q < K; ++q) smem[(q * SPLIT + sub) * NB + img] = s[q];
+    __syncthreads();
+    if (threadIdx.x < K * NB) {
+        const int q = threadIdx.x / NB, im = threadIdx.x % NB;
+        double t = 0.0;
+        for (int u = 0; u < SPLIT; ++u) t += smem[(q * SPLIT + u) * NB + im];
+        out[q * NB + im] = t;
     }
     if (threadIdx.x == 0) *counter = 0u;
     __syncthreads();
     return true;
 }
 
+template <int NB>
+__host__ __device__ constexpr int reduce_smem_doubles(int K)
+{
+    return K * (8 > 256 / NB ? 8 : 256 / NB) * NB;
+}
+
 // ---------------------------------------------------------------------------
 // Row kernel core: one row (a ray of the ray-major table or a pixel of the
-// pixel-major table) is handled by G lanes.  With LPE = CPB lanes per entry
-// (one vector each), a row's entries are split over EG = G / LPE groups,
-// visited in order k = begin + group, + EG, ...; the groups are summed by a
-// fixed xor-butterfly, so the result is bitwise reproducible.
-// After the call, the lanes with group == 0 hold the row's VW sums.
+// pixel-major table) is handled by G lanes.  The G lanes load the row's
+// entries cooperatively, G at a time (coalesced, streamed past L1), one batch
+// ahead of use, so a table entry's DRAM latency overlaps the gathers of the
+// previous batch.  Inside a batch, entry j is broadcast by shuffle to the
+// LPE = CPB lanes that gather its VW-wide vectors of the NB images; the
+// batch's EG = G / LPE entry groups give every lane LPE independent gathers.
+// Groups are summed by a fixed xor-butterfly: the result is bitwise
+// reproducible.  After the call, the lanes with group == 0 hold the row's sums.
+// Every lane of the warp must call it (rows past the end pass b = e).
 // ---------------------------------------------------------------------------
 template <int NB, int G, bool IL>
 __device__ __forceinline__ Vec<Batch<NB>::VW> row_dot(const Entry *__restrict__ ent, int64_t b,
@@ -141,26 +176,53 @@ __device__ __forceinline__ Vec<Batch<NB>::VW> row_dot(const Entry *__restrict__ 
                                                       int64_t src_stride, int lr, int nimg = NB)
 {
     constexpr int VW = Batch<NB>::VW, LPE = Batch<NB>::CPB, EG = G / LPE;
+    constexpr int U = LPE >= 4 ? 1 : 4 / LPE;  // batches in flight per step
     static_assert(G % LPE == 0 && G <= 32, "bad row split");
     const int grp = lr / LPE, vl = lr % LPE;
+    const unsigned lane = threadIdx.x & 31;
+    const unsigned gbase = lane & ~(unsigned)(G - 1);  // first lane of this row group
     Vec<VW> acc;
     acc.zero();
-#pragma unroll 4
-    for (int64_t k = b + grp; k < e; k += EG) {
-        Entry t = ld_entry(ent + k);
-        float w = __int_as_float(t.y);
-        Vec<VW> xv;
-        if constexpr (IL) {
-            xv = ld_il<VW>(src + (int64_t)t.x * NB + vl * VW);
-        } else {
+    Entry cur[U];
 #pragma unroll
-            for (int c = 0; c < VW; ++c) {
-                const int img = vl * VW + c;
-                xv.v[c] = img < nimg ? __ldg(src + (int64_t)img * src_stride + t.x) : 0.f;
+    for (int u = 0; u < U; ++u) {
+        const int64_t k = b + u * G + lr;
+        cur[u] = k < e ? ld_entry(ent + k) : make_int2(0, 0);
+    }
+    // the loop runs in lockstep over the warp (its shuffles need every lane):
+    // rows shorter than the warp's longest see padded entries
+    const unsigned maxlen = __reduce_max_sync(0xffffffffu, (unsigned)(e - b));
+    for (int64_t base = b; base < b + (int64_t)maxlen; base += U * G) {
+        Entry nxt[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int64_t k = base + (U + u) * G + lr;
+            nxt[u] = k < e ? ld_entry(ent + k) : make_int2(0, 0);
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+#pragma unroll
+            for (int j = 0; j < G / EG; ++j) {
+                const unsigned srcl = gbase + j * EG + grp;
+                const int pix = __shfl_sync(0xffffffffu, cur[u].x, srcl);
+                const float w = __int_as_float(__shfl_sync(0xffffffffu, cur[u].y, srcl));
+                // padded entries carry w = 0 and index 0: a valid address, no contribution
+                Vec<VW> xv;
+                if constexpr (IL) {
+                    xv = ld_il<VW>(src + (int64_t)pix * NB + vl * VW);
+                } else {
+#pragma unroll
+                    for (int c = 0; c < VW; ++c) {
+                        const int img = vl * VW + c;
+                        xv.v[c] = img < nimg ? __ldg(src + (int64_t)img * src_stride + pix) : 0.f;
+                    }
+                }
+#pragma unroll
+                for (int c = 0; c < VW; ++c) acc.v[c] = fmaf(w, xv.v[c], acc.v[c]);
             }
         }
 #pragma unroll
-        for (int c = 0; c < VW; ++c) acc.v[c] = fmaf(w, xv.v[c], acc.v[c]);
+        for (int u = 0; u < U; ++u) cur[u] = nxt[u];
     }
 #pragma unroll
     for (int off = LPE; off < G; off <<= 1)

@@ -78,9 +78,16 @@ __device__ bool reduce_planar(const float (&v)[K], double *part, double *out, un
     __threadfence();
     for (unsigned t = threadIdx.x; t < gy * K; t += blockDim.x) {
         const unsigned y = t / K, k = t % K;
-        double s = 0.0;
-        for (unsigned b = 0; b < gx; ++b) s += __ldcg(&part[((size_t)y * gx + b) * K + k]);
-        out[t] = s;
+        double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+        unsigned b = 0;
+        for (; b + 4 <= gx; b += 4) {
+            s0 += __ldcg(&part[((size_t)y * gx + b) * K + k]);
+            s1 += __ldcg(&part[((size_t)y * gx + b + 1) * K + k]);
+            s2 += __ldcg(&part[((size_t)y * gx + b + 2) * K + k]);
+            s3 += __ldcg(&part[((size_t)y * gx + b + 3) * K + k]);
+        }
+        for (; b < gx; ++b) s0 += __ldcg(&part[((size_t)y * gx + b) * K + k]);
+        out[t] = (s0 + s1) + (s2 + s3);
     }
     if (threadIdx.x == 0) *counter = 0u;
     __syncthreads();
