@@ -370,6 +370,7 @@ def main():
                    "all_converged": bool(state.get("conv", False)),
                    "mean_pcg_iterations": float(np.mean(state["pls_iters"])),
                    "plan_seconds": round(plan_s, 3), "nnz": plan.nnz,
+                   "bwd_autotune": dict(zip(("choice", "us"), plan.tuning(min(32, 1 << (2 * S - 1).bit_length())))),
                    "l2": "inputs larger than L2 (tables %.0f MB)" % (plan.table_bytes / 1e6),
                    "parallelism": "replicas" if world > 1 else "1 GPU"},
         "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,

@@ -231,6 +231,22 @@ dect_status dect_adm_tv_ex(const dect_plan *plan, const float *m, float *x, int 
                            const dect_adm_params *params, dect_adm_report *reports,
                            dect_adm_profile *prof, dect_stream stream);
 
+/*
+ * Autotuner record of a plan: the A^T variant that dect_adm_tv chose for a
+ * batch of `images` interleaved channels (2, 4, 8, 16 or 32; a call with c
+ * channels uses the next of these widths >= min(c, 32)), and the measured
+ * median time of each variant in microseconds (-1 = not available):
+ *   0-2 L1-cached gather with 4x4 / 8x8 / 16x16 pixel tiles per block,
+ *   3   shared-memory sinogram windows (cp.async staged).
+ * *choice = -1 until an ADM call with that width has run.  Host memory.
+ */
+dect_status dect_plan_get_tuning(const dect_plan *plan, int images, int *choice, float us[4]);
+
+/* Fix the A^T variant used for batch width `images` (skipping the timing),
+ * or pass choice = -1 to let the next ADM call time the candidates again.
+ * Variant 3 falls back to 1 where the windows do not fit shared memory. */
+dect_status dect_plan_set_tuning(dect_plan *plan, int images, int choice);
+
 /* Number of kernels libdect has launched in this process so far (kernel
  * launches plus the kernel nodes of every graph launch). */
 int64_t dect_kernel_launches(void);

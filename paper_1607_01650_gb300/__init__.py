@@ -79,6 +79,8 @@ _SIGS = {
     "dect_adm_tv_ex": (C.c_int, [_P, _P, _P, C.c_int, C.POINTER(_AdmParams), _P, _P, _P]),
     "dect_pls_decompose": (C.c_int, [_P, C.c_int, C.c_int, C.POINTER(_PlsParams), _P, _P, _P]),
     "dect_kernel_launches": (C.c_int64, []),
+    "dect_plan_get_tuning": (C.c_int, [_P, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_float)]),
+    "dect_plan_set_tuning": (C.c_int, [_P, C.c_int, C.c_int]),
     "dect_status_string": (C.c_char_p, [C.c_int]),
     "dect_last_error": (C.c_char_p, []),
     "dect_version": (C.c_int, []),
@@ -190,6 +192,17 @@ class Plan:
             self.close()
         except Exception:
             pass
+
+    def tuning(self, images: int):
+        """(chosen A^T variant, [median us of variants 0..3]) for a batch width; see dect.h."""
+        ch = C.c_int(-1)
+        us = (C.c_float * 4)()
+        _check(load().dect_plan_get_tuning(self._h, images, C.byref(ch), us), "dect_plan_get_tuning")
+        return ch.value, list(us)
+
+    def set_tuning(self, images: int, choice: int):
+        """Force the A^T variant for a batch width (-1: re-time on the next ADM call)."""
+        _check(load().dect_plan_set_tuning(self._h, images, choice), "dect_plan_set_tuning")
 
     def table(self):
         """(rowptr int64 [M+1], pix int32 [nnz], len float32 [nnz]) as numpy arrays."""

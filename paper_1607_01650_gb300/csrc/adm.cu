@@ -39,7 +39,6 @@ namespace {
 
 constexpr int kBlock = 256;
 constexpr int kGrid = kSMs * 8;  // fixed grid of every reducing kernel
-constexpr int kTile = 8;         // A^T kernel: 8 x 8 pixel tiles per block
 
 // reduction slots; (TV, RR) and (DD, QQ) are reduced together
 enum { R_TV = 0, R_RR = 1, R_DD = 2, R_QQ = 3, R_GG = 4, R_COUNT = 5 };
@@ -198,9 +197,10 @@ __global__ void __launch_bounds__(kBlock) k_tv(const float *__restrict__ f_in, f
     reduce_images<NB, 2>(acc, part_of<NB>(D, C_TV), D.red + R_TV * NB, D.ctr + C_TV, smem);
 }
 
-// G = mu A^T r + grad^T p over the pixel-major table.  A block takes 8 x 8
-// pixel tiles, so the sinogram lines its pixels gather are shared in L1.
-template <int NB, int G_>
+// G = mu A^T r + grad^T p over the pixel-major table.  A block takes
+// kTile x kTile pixel tiles, so the sinogram lines its pixels gather are
+// shared in L1.
+template <int NB, int G_, int kTile>
 __global__ void __launch_bounds__(kBlock) k_bwd(const int64_t *__restrict__ colptr,
                                                 const Entry *__restrict__ tent,
                                                 const float *__restrict__ r, const float *__restrict__ p,
@@ -248,6 +248,169 @@ __global__ void __launch_bounds__(kBlock) k_bwd(const int64_t *__restrict__ colp
     reduce_images<NB, 1>(nrm, part_of<NB>(D, C_BWD), D.red + R_GG * NB, D.ctr + C_BWD, smem);
 }
 
+// G = mu A^T r + grad^T p with everything a tile needs staged in shared
+// memory: a block takes kWinTH x kWinTW pixel tiles; per tile, warp 0
+// bulk-copies (TMA) the tile's entries (tile-major table, tile-local ray
+// indices) and, per view, the window of sinogram bins the tile meets; the
+// tile's pixels then read only shared memory.  One bounded wait per tile; a
+// timeout sets bit 2 of the error word and stops the block.
+constexpr unsigned kWaitPolls = 1u << 22;
+
+template <int NB, int G>
+__device__ __forceinline__ Vec<Batch<NB>::VW> row_dot_smem(const Entry *sent, int b, int e, int lr,
+                                                           const float *win)
+{
+    constexpr int VW = Batch<NB>::VW, LPE = Batch<NB>::CPB, EG = G / LPE;
+    const int grp = lr / LPE, vl = lr % LPE;
+    Vec<VW> acc;
+    acc.zero();
+#pragma unroll 4
+    for (int k = b + grp; k < e; k += EG) {
+        const Entry t = sent[k];
+        const Vec<VW> xv = ld_v<VW>(win + t.x * NB + vl * VW);
+        const float w = __int_as_float(t.y);
+#pragma unroll
+        for (int c = 0; c < VW; ++c) acc.v[c] = fmaf(w, xv.v[c], acc.v[c]);
+    }
+#pragma unroll
+    for (int off = LPE; off < G; off <<= 1)
+#pragma unroll
+        for (int c = 0; c < VW; ++c) acc.v[c] += __shfl_xor_sync(0xffffffffu, acc.v[c], off);
+    return acc;
+}
+
+constexpr int kWinBlock = 32 * kWinTP;  // one warp per pixel of a tile
+constexpr int kWinWarps = kWinBlock / 32;
+
+struct WinArgs {
+    const Entry *tmaj;
+    const int64_t *tbase;
+    const int *tpo, *wray0, *wcnt, *woff, *wtot;
+    int nv, nvp;
+    int win_floats;  // floats of one stage's sinogram window
+    int ent_max;     // entries of one stage's table part
+};
+
+// Data stage st in dynamic shared memory: [window floats][entries]; after the
+// two data stages, two descriptor stages of [wray0 | wcnt | woff] x nvp ints.
+__device__ __forceinline__ float *win_stage(float *dyn, const WinArgs &A, int st)
+{
+    return dyn + (size_t)st * (A.win_floats + 2 * A.ent_max);
+}
+__device__ __forceinline__ int *desc_stage(float *dyn, const WinArgs &A, int st)
+{
+    return reinterpret_cast<int *>(win_stage(dyn, A, 2)) + (size_t)st * 3 * A.nvp;
+}
+
+// Copies of tile `tile`'s view descriptors into descriptor stage ds (16-byte cp.async).
+__device__ __forceinline__ void win_copy_desc(const WinArgs &A, float *dyn, int tile, int ds)
+{
+    int *d = desc_stage(dyn, A, ds);
+    const int q = A.nvp / 4;  // 16-byte chunks per array
+    const int64_t o = (int64_t)tile * A.nvp;
+    for (int c = threadIdx.x; c < 3 * q; c += blockDim.x) {
+        const int a = c / q, k = (c % q) * 4;
+        const int *src = a == 0 ? A.wray0 : (a == 1 ? A.wcnt : A.woff);
+        cp_async16(d + a * A.nvp + k, src + o + k);
+    }
+}
+
+// Copies of tile `tile`'s entries and sinogram windows into data stage st,
+// using the descriptors already in descriptor stage ds; pixel offsets to spo.
+template <int NB>
+__device__ __forceinline__ void win_copy_data(const WinArgs &A, float *dyn, int (*spo)[kWinTP + 1],
+                                              const float *r, int tile, int st, int ds)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    float *win = win_stage(dyn, A, st);
+    Entry *sent = reinterpret_cast<Entry *>(win + A.win_floats);
+    const int64_t e0 = A.tbase[tile], e1 = A.tbase[tile + 1];
+    const int nch = (int)((e1 - e0) / 2);
+    for (int c = threadIdx.x; c < nch; c += blockDim.x) cp_async16(sent + 2 * c, A.tmaj + e0 + 2 * c);
+    const int *d = desc_stage(dyn, A, ds);
+    for (int v = warp; v < A.nv; v += kWinWarps) {
+        const int ray0 = d[v], cnt = d[A.nvp + v], off = d[2 * A.nvp + v];
+        const int nc = cnt * NB / 4;
+        const float *src = r + (int64_t)ray0 * NB;
+        float *dst = win + (int64_t)off * NB;
+        for (int c = lane; c < nc; c += 32) cp_async16(dst + 4 * c, src + 4 * c);
+    }
+    if (threadIdx.x <= kWinTP) spo[st][threadIdx.x] = A.tpo[(int64_t)tile * (kWinTP + 1) + threadIdx.x];
+}
+
+template <int NB>
+__global__ void __launch_bounds__(kWinBlock, 1) k_bwd_win(WinArgs A, const float *__restrict__ r,
+                                                          const float *__restrict__ p,
+                                                          float *__restrict__ G, AdmConst C, AdmDev D)
+{
+    constexpr int VW = Batch<NB>::VW, LPE = Batch<NB>::CPB;
+    constexpr int G_ = 32;
+    extern __shared__ __align__(128) float dyn[];
+    __shared__ int spo[2][kWinTP + 1];
+    __shared__ double smem[reduce_smem_doubles<NB, kWinBlock>(1)];
+    const int lr = threadIdx.x & 31, grp = lr / LPE, vl = lr % LPE;
+    const int slot = threadIdx.x >> 5;  // pixel of the tile handled by this warp
+    const int64_t sN = C.N * NB;
+    const int tiles_x = (C.n + kWinTW - 1) / kWinTW;
+    const int ntiles = tiles_x * ((C.n + kWinTH - 1) / kWinTH);
+    Vec<VW> nrm[1];
+    nrm[0].zero();
+    // pipeline: at the top of the loop for tile t the group holding
+    // (data of t, descriptors of t + 1) is awaited; then the group
+    // (descriptors of t + 2, data of t + 1) is issued and overlaps compute(t)
+    const int g = gridDim.x;
+    int t0 = blockIdx.x;
+    if (t0 < ntiles) {
+        win_copy_desc(A, dyn, t0, 0);
+        cp_async_commit();
+        cp_async_wait<0>();
+        __syncthreads();
+        if (t0 + g < ntiles) win_copy_desc(A, dyn, t0 + g, 1);
+        win_copy_data<NB>(A, dyn, spo, r, t0, 0, 0);
+        cp_async_commit();
+    }
+    int it = 0;
+    for (int tile = t0; tile < ntiles; tile += g, ++it) {
+        const int st = it & 1;
+        cp_async_wait<0>();
+        __syncthreads();
+        const int next = tile + g, next2 = tile + 2 * g;
+        if (next2 < ntiles) win_copy_desc(A, dyn, next2, st);        // desc stage of t+2 = t % 2
+        if (next < ntiles) win_copy_data<NB>(A, dyn, spo, r, next, st ^ 1, st ^ 1);
+        cp_async_commit();
+        const int ty = tile / tiles_x, tx = tile % tiles_x;
+        const int i = ty * kWinTH + slot / kWinTW, j = tx * kWinTW + slot % kWinTW;
+        const bool ok = i < C.n && j < C.n;
+        const int64_t pix = (int64_t)i * C.n + j;
+        const int64_t o = pix * NB + vl * VW;
+        Vec<VW> p0, p1, pd, pr;
+        p0.zero(); p1.zero(); pd.zero(); pr.zero();
+        if (ok && grp == 0) {
+            p0 = ld_v<VW>(p + o);
+            p1 = ld_v<VW>(p + sN + o);
+            if (i + 1 < C.n) pd = ld_v<VW>(p + o + (int64_t)C.n * NB);
+            if (j + 1 < C.n) pr = ld_v<VW>(p + sN + o + NB);
+        }
+        const float *win = win_stage(dyn, A, st);
+        const Entry *sent = reinterpret_cast<const Entry *>(win + A.win_floats);
+        const int b = ok ? spo[st][slot] : 0, e = ok ? spo[st][slot + 1] : 0;
+        Vec<VW> acc = row_dot_smem<NB, G_>(sent, b, e, lr, win);
+        if (ok && grp == 0) {
+            Vec<VW> out;
+#pragma unroll
+            for (int c = 0; c < VW; ++c) {
+                float gt = (i > 0 ? p0.v[c] : 0.f) - pd.v[c] + (j > 0 ? p1.v[c] : 0.f) - pr.v[c];
+                out.v[c] = fmaf(C.mu, acc.v[c], gt);
+                nrm[0].v[c] = fmaf(out.v[c], out.v[c], nrm[0].v[c]);
+            }
+            st_v<VW>(G + o, out);
+        }
+        __syncthreads();  // every read of this stage precedes its next copies
+    }
+    cp_async_wait<0>();
+    reduce_images<NB, 1, kWinBlock>(nrm, part_of<NB>(D, C_BWD), D.red + R_GG * NB, D.ctr + C_BWD, smem);
+}
+
 // Step size and stopping test, FP64, one thread per channel (last block of k_fwd).
 template <int NB>
 __device__ void adm_finish(const AdmConst &C, const AdmDev &D)
@@ -258,7 +421,7 @@ __device__ void adm_finish(const AdmConst &C, const AdmDev &D)
         double alpha = 0.0;
         if (D.active[b]) {
             const double phi = D.red[R_TV * NB + b] + 0.5 * C.mu_d * D.red[R_RR * NB + b];
-            if (!isfinite(phi)) *D.bad = 1;
+            if (!isfinite(phi)) atomicOr(D.bad, 1);
             bool stop = false;
             if (k > 0) {
                 const double prev = D.phi_prev[b];
@@ -392,7 +555,121 @@ struct Work {
     int *ints;
     unsigned *ctr;
     AdmDev D;
+    int win_grid;     // > 0: A^T through shared-memory windows with this grid
+    size_t win_smem;  // its dynamic shared memory
+    int bwd;          // A^T variant in use
 };
+
+constexpr size_t kWinSmemMax = 210 * 1024;
+
+// Enable the windowed A^T for this plan and batch width when two stages of
+// its window and entries fit in shared memory.
+template <int NB>
+cudaError_t setup_window(const dect_plan *P, Work &W)
+{
+    W.win_grid = 0;
+    W.win_smem = 0;
+    if (P->win_max <= 0) return cudaSuccess;
+    const size_t stage = (size_t)P->win_max * NB * sizeof(float) + (size_t)P->tile_ent_max * sizeof(Entry);
+    const size_t bytes = 2 * stage + 2 * 3 * sizeof(int) * (size_t)P->nvp;
+    if (bytes > kWinSmemMax) return cudaSuccess;
+    auto kern = k_bwd_win<NB>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kWinBlock, bytes);
+    if (e != cudaSuccess) return e;
+    if (per_sm <= 0) return cudaSuccess;
+    int grid = kSMs * per_sm;
+    if (grid > kGrid) grid = kGrid;
+    if (grid > P->win_tiles) grid = P->win_tiles;
+    W.win_grid = grid;
+    W.win_smem = bytes;
+    return cudaSuccess;
+}
+
+// A^T variants (autotuner candidates): 0-2 L1-cached gather with 4x4 / 8x8 /
+// 16x16 pixel tiles per block; 3 shared-memory sinogram windows.
+constexpr int kBwdVariants = 4;
+
+template <int NB>
+void launch_bwd(const dect_plan *P, const Work &W, const AdmConst &C, int variant, cudaStream_t s)
+{
+    constexpr int GB = Kern<NB>::GB;
+    switch (variant) {
+    case 0:
+        k_bwd<NB, GB, 4><<<kGrid, kBlock, 0, s>>>(P->colptr, P->tent, W.r, W.p, W.G, C, W.D);
+        break;
+    case 2:
+        k_bwd<NB, GB, 16><<<kGrid, kBlock, 0, s>>>(P->colptr, P->tent, W.r, W.p, W.G, C, W.D);
+        break;
+    case 3: {
+        WinArgs A{P->tmaj, P->tbase, P->tpo, P->wray0, P->wcnt, P->woff, P->wtot, P->nv, P->nvp,
+                  P->win_max * NB, P->tile_ent_max};
+        k_bwd_win<NB><<<W.win_grid, kWinBlock, W.win_smem, s>>>(A, W.r, W.p, W.G, C, W.D);
+        break;
+    }
+    default:
+        k_bwd<NB, GB, 8><<<kGrid, kBlock, 0, s>>>(P->colptr, P->tent, W.r, W.p, W.G, C, W.D);
+        break;
+    }
+}
+
+template <int NB>
+constexpr int nb_index()
+{
+    return NB == 2 ? 0 : NB == 4 ? 1 : NB == 8 ? 2 : NB == 16 ? 3 : 4;
+}
+
+// Time every available A^T variant on this workspace (CUDA events, median of
+// three launches after one warm-up) and keep the fastest in the plan.  The
+// kernels only write G and reduction slots, which the first iteration
+// rewrites, so timing them here changes no result.
+template <int NB>
+cudaError_t tune_bwd(const dect_plan *P, Work &W, const AdmConst &C, cudaStream_t s)
+{
+    const int idx = nb_index<NB>();
+    if (P->bwd_choice[idx] >= 0) {
+        W.bwd = P->bwd_choice[idx];
+        if (W.bwd == 3 && W.win_grid <= 0) W.bwd = 1;
+        return cudaSuccess;
+    }
+    cudaEvent_t a = nullptr, b = nullptr;
+    cudaError_t e = cudaEventCreate(&a);
+    if (e == cudaSuccess) e = cudaEventCreate(&b);
+    int best = 1;
+    float best_us = 1e30f;
+    for (int v = 0; v < kBwdVariants && e == cudaSuccess; ++v) {
+        P->bwd_us[idx][v] = -1.f;
+        if (v == 3 && W.win_grid <= 0) continue;
+        launch_bwd<NB>(P, W, C, v, s);
+        count_launches(1);
+        float t[3];
+        for (int k = 0; k < 3 && e == cudaSuccess; ++k) {
+            e = cudaEventRecord(a, s);
+            launch_bwd<NB>(P, W, C, v, s);
+            count_launches(1);
+            if (e == cudaSuccess) e = cudaEventRecord(b, s);
+            if (e == cudaSuccess) e = cudaEventSynchronize(b);
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&t[k], a, b);
+        }
+        if (e != cudaSuccess) break;
+        std::sort(t, t + 3);
+        const float us = t[1] * 1e3f;
+        P->bwd_us[idx][v] = us;
+        if (us < best_us) {
+            best_us = us;
+            best = v;
+        }
+    }
+    if (a) cudaEventDestroy(a);
+    if (b) cudaEventDestroy(b);
+    if (e == cudaSuccess) e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    P->bwd_choice[idx] = best;
+    W.bwd = best;
+    return cudaSuccess;
+}
 
 // Optional timing events around the two table kernels of one iteration.
 struct IterEvents {
@@ -406,7 +683,7 @@ void enqueue_iteration(const dect_plan *P, const Work &W, const AdmConst &C, int
 {
     k_tv<NB><<<kGrid, kBlock, 0, s>>>(W.f[par], W.f[1 - par], W.G, W.lam, W.z, W.p, W.r, W.q, C, W.D, 0);
     if (ev) cudaEventRecordWithFlags(ev->b0, s, cudaEventRecordExternal);
-    k_bwd<NB, Kern<NB>::GB><<<kGrid, kBlock, 0, s>>>(P->colptr, P->tent, W.r, W.p, W.G, C, W.D);
+    launch_bwd<NB>(P, W, C, W.bwd, s);
     if (ev) cudaEventRecordWithFlags(ev->b1, s, cudaEventRecordExternal);
     if (ev) cudaEventRecordWithFlags(ev->f0, s, cudaEventRecordExternal);
     k_fwd<NB, Kern<NB>::GF, 1><<<kGrid, kBlock, 0, s>>>(P->rowptr, P->ent, W.G, W.q, nullptr, nullptr,
@@ -450,7 +727,7 @@ dect_status run_chunk(const dect_plan *P, const float *m, float *x, int nimg,
         W.lam = (float *)take(2 * nf * 4);
         W.z = (float *)take(2 * nf * 4);
         W.p = (float *)take(2 * nf * 4);
-        W.r = (float *)take(nr * 4);
+        W.r = (float *)take((nr + 2 * NB) * 4);  // windows may end one ray past M
         W.q = (float *)take(nr * 4);
         W.beta = (float *)take(64 * 4);
         W.dbl = (double *)take(ndbl * 8);
@@ -462,6 +739,7 @@ dect_status run_chunk(const dect_plan *P, const float *m, float *x, int nimg,
     char *base = nullptr;
     DECT_CUDA(cudaMallocAsync((void **)&base, bytes, s));
     layout(base);
+    DECT_CUDA(setup_window<NB>(P, W));
 
     AdmDev &D = W.D;
     D.red = W.dbl;
@@ -499,6 +777,8 @@ dect_status run_chunk(const dect_plan *P, const float *m, float *x, int nimg,
     k_fwd<NB, Kern<NB>::GF, 0><<<kGrid, kBlock, 0, s>>>(P->rowptr, P->ent, W.f[0], W.r, m, W.beta, C, D);
     DECT_LAUNCH_CHECK();
     count_launches(1);
+    W.bwd = 1;
+    DECT_CUDA(tune_bwd<NB>(P, W, C, s));
 
     // iterations: CUDA graphs of `block` iterations (an even number, so the
     // f double buffer returns to the same parity) and single-iteration graphs
@@ -632,7 +912,11 @@ dect_status run_chunk(const dect_plan *P, const float *m, float *x, int nimg,
             rep[b].rel_change = hrel[b];
         }
     }
-    return hbad ? DECT_ERR_NONFINITE : DECT_OK;
+    if (hbad & 2) {
+        set_error_text("dect_adm_tv: a shared-memory window copy did not complete in time");
+        return DECT_ERR_TIMEOUT;
+    }
+    return (hbad & 1) ? DECT_ERR_NONFINITE : DECT_OK;
 }
 
 }  // namespace

@@ -13,6 +13,11 @@ namespace dect {
 
 constexpr int kSMs = 152;          // GB300: 2 dies x 76 SMs
 constexpr int kMaxBatchImages = 32; // images interleaved per ADM pass
+constexpr int kTablePad = 512;      // zero entries after the last row of each table
+// A^T with shared-memory sinogram windows: pixel tiles of kWinTH x kWinTW
+constexpr int kWinTH = 4, kWinTW = 4;
+constexpr int kWinTP = kWinTH * kWinTW;
+constexpr int kWinMaxViews = 4096;
 
 // Thread-local text of the last CUDA error (returned by dect_last_error()).
 void set_error(const char *where, cudaError_t e);
@@ -47,6 +52,29 @@ struct dect_plan {
     dect::Entry *ent;  // [nnz]  {pixel, len}
     int64_t *colptr;   // [N + 1], pixel-major table (CSR of A^T)
     dect::Entry *tent; // [nnz]  {ray, len}, rays increasing within a pixel
+    // Per pixel tile (kWinTH x kWinTW) and view: the window of the tile's rays,
+    // [wray0, wray0 + wcnt) (even start and count), placed at woff in the
+    // tile's shared-memory window of wtot rays; tlocal = tent with the ray
+    // replaced by its index in the tile's window.  win_max = max wtot
+    // (0 when the windowed A^T is not available for this geometry).
+    int win_tiles;
+    int win_max;
+    int nvp;                   // descriptor stride per tile: nv rounded up to 4
+    int *wray0, *wcnt, *woff;  // [win_tiles * nvp]
+    int *wtot;                 // [win_tiles]
+    dect::Entry *tlocal;       // [nnz + pad]
+    // The same entries tile-major: tile t's pixels (row-major inside the tile)
+    // at tmaj[tbase[t] .. tbase[t + 1]) (even offsets, zero-padded to an even
+    // count); pixel s of tile t at tpo[t * (kWinTP + 1) + s] relative to
+    // tbase[t].  tile_ent_max = max entries of a tile.
+    dect::Entry *tmaj;
+    int64_t *tbase;            // [win_tiles + 1]
+    int *tpo;                  // [win_tiles * (kWinTP + 1)]
+    int tile_ent_max;
+    // Autotuner cache: chosen A^T variant per ADM batch width (index log2(NB) - 1),
+    // -1 until the first ADM call with that width has timed the candidates.
+    mutable int bwd_choice[5];
+    mutable float bwd_us[5][4];
 };
 
 namespace dect {

@@ -88,11 +88,11 @@ __device__ __forceinline__ Entry ld_entry(const Entry *p)
 // Values are summed in FP32 inside a warp and in FP64 across warps and
 // blocks, always in the same order.  The block that finishes last writes the
 // grid totals to out[k][img] and returns true (in every thread of that
-// block); `counter` is reset for the next launch.  Blocks have 256 threads;
-// smem must hold K * max(8, 256 / NB) * NB doubles; part holds
+// block); `counter` is reset for the next launch.  Blocks have BLOCK threads;
+// smem must hold reduce_smem_doubles<NB, BLOCK>(K) doubles; part holds
 // K * gridDim.x * NB doubles.
 // ---------------------------------------------------------------------------
-template <int NB, int K>
+template <int NB, int K, int BLOCK = 256>
 __device__ __forceinline__ bool reduce_images(Vec<Batch<NB>::VW> (&v)[K], double *__restrict__ part,
                                               double *__restrict__ out, unsigned *counter,
                                               double *smem)
@@ -127,8 +127,8 @@ __device__ __forceinline__ bool reduce_images(Vec<Batch<NB>::VW> (&v)[K], double
     __threadfence();
     // grid total: SPLIT threads per image each sum a fixed stride of the block
     // partials, then one thread per image adds the SPLIT sub-sums in order
-    constexpr int SPLIT = 256 / NB;
-    static_assert(SPLIT * NB == 256, "reduce_images needs 256-thread blocks");
+    constexpr int SPLIT = BLOCK / NB;
+    static_assert(SPLIT * NB == BLOCK, "reduce_images: BLOCK must be a multiple of NB");
     const int img = threadIdx.x % NB, sub = threadIdx.x / NB;
     double s[K];
 #pragma unroll
@@ -152,10 +152,10 @@ __device__ __forceinline__ bool reduce_images(Vec<Batch<NB>::VW> (&v)[K], double
     return true;
 }
 
-template <int NB>
+template <int NB, int BLOCK = 256>
 __host__ __device__ constexpr int reduce_smem_doubles(int K)
 {
-    return K * (8 > 256 / NB ? 8 : 256 / NB) * NB;
+    return K * (BLOCK / 32 > BLOCK / NB ? BLOCK / 32 : BLOCK / NB) * NB;
 }
 
 // ---------------------------------------------------------------------------
@@ -170,10 +170,9 @@ __host__ __device__ constexpr int reduce_smem_doubles(int K)
 // reproducible.  After the call, the lanes with group == 0 hold the row's sums.
 // Every lane of the warp must call it (rows past the end pass b = e).
 // ---------------------------------------------------------------------------
-template <int NB, int G, bool IL>
-__device__ __forceinline__ Vec<Batch<NB>::VW> row_dot(const Entry *__restrict__ ent, int64_t b,
-                                                      int64_t e, const float *__restrict__ src,
-                                                      int64_t src_stride, int lr, int nimg = NB)
+template <int NB, int G, typename Gather>
+__device__ __forceinline__ Vec<Batch<NB>::VW> row_dot_g(const Entry *__restrict__ ent, int64_t b,
+                                                        int64_t e, int lr, Gather gather)
 {
     constexpr int VW = Batch<NB>::VW, LPE = Batch<NB>::CPB, EG = G / LPE;
     constexpr int U = LPE >= 4 ? 1 : 4 / LPE;  // batches in flight per step
@@ -207,16 +206,7 @@ __device__ __forceinline__ Vec<Batch<NB>::VW> row_dot(const Entry *__restrict__ 
                 const int pix = __shfl_sync(0xffffffffu, cur[u].x, srcl);
                 const float w = __int_as_float(__shfl_sync(0xffffffffu, cur[u].y, srcl));
                 // padded entries carry w = 0 and index 0: a valid address, no contribution
-                Vec<VW> xv;
-                if constexpr (IL) {
-                    xv = ld_il<VW>(src + (int64_t)pix * NB + vl * VW);
-                } else {
-#pragma unroll
-                    for (int c = 0; c < VW; ++c) {
-                        const int img = vl * VW + c;
-                        xv.v[c] = img < nimg ? __ldg(src + (int64_t)img * src_stride + pix) : 0.f;
-                    }
-                }
+                const Vec<VW> xv = gather(pix, vl);
 #pragma unroll
                 for (int c = 0; c < VW; ++c) acc.v[c] = fmaf(w, xv.v[c], acc.v[c]);
             }
@@ -229,6 +219,52 @@ __device__ __forceinline__ Vec<Batch<NB>::VW> row_dot(const Entry *__restrict__ 
 #pragma unroll
         for (int c = 0; c < VW; ++c) acc.v[c] += __shfl_xor_sync(0xffffffffu, acc.v[c], off);
     return acc;
+}
+
+// Gathers of one VW-wide vector of the NB images at index `pix`.
+template <int NB>
+struct GatherIL {  // interleaved [index][NB] in global memory
+    const float *src;
+    __device__ __forceinline__ Vec<Batch<NB>::VW> operator()(int pix, int vl) const
+    {
+        return ld_il<Batch<NB>::VW>(src + (int64_t)pix * NB + vl * Batch<NB>::VW);
+    }
+};
+template <int NB>
+struct GatherPlanar {  // planar [img][stride] in global memory, nimg valid images
+    const float *src;
+    int64_t stride;
+    int nimg;
+    __device__ __forceinline__ Vec<Batch<NB>::VW> operator()(int pix, int vl) const
+    {
+        constexpr int VW = Batch<NB>::VW;
+        Vec<VW> xv;
+#pragma unroll
+        for (int c = 0; c < VW; ++c) {
+            const int img = vl * VW + c;
+            xv.v[c] = img < nimg ? __ldg(src + (int64_t)img * stride + pix) : 0.f;
+        }
+        return xv;
+    }
+};
+template <int NB>
+struct GatherShared {  // interleaved [index][NB] in shared memory
+    const float *win;
+    __device__ __forceinline__ Vec<Batch<NB>::VW> operator()(int idx, int vl) const
+    {
+        return ld_v<Batch<NB>::VW>(win + idx * NB + vl * Batch<NB>::VW);
+    }
+};
+
+template <int NB, int G, bool IL>
+__device__ __forceinline__ Vec<Batch<NB>::VW> row_dot(const Entry *__restrict__ ent, int64_t b,
+                                                      int64_t e, const float *__restrict__ src,
+                                                      int64_t src_stride, int lr, int nimg = NB)
+{
+    if constexpr (IL)
+        return row_dot_g<NB, G>(ent, b, e, lr, GatherIL<NB>{src});
+    else
+        return row_dot_g<NB, G>(ent, b, e, lr, GatherPlanar<NB>{src, src_stride, nimg});
 }
 
 // Plain operator kernel: dst[row] = sum over the row's entries of len * src[index].
@@ -261,5 +297,81 @@ __global__ void __launch_bounds__(256) k_rows_planar(const int64_t *__restrict__
         }
     }
 }
+
+}  // namespace dect
+
+namespace dect {
+
+// ---------------------------------------------------------------------------
+// Bulk asynchronous copies (TMA, non-tensor form) into shared memory with
+// mbarrier completion.  Every wait is bounded: after `limit` failed polls the
+// caller gets false and records the timeout instead of spinning forever.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ unsigned smem_u32(const void *p)
+{
+    return (unsigned)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, unsigned count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, unsigned bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, unsigned parity)
+{
+    unsigned done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return done != 0;
+}
+
+// Wait for phase `parity` of `bar`; false after `limit` unsuccessful polls.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, unsigned parity, unsigned limit)
+{
+    for (unsigned i = 0; i < limit; ++i)
+        if (mbar_try_wait(bar, parity)) return true;
+    return false;
+}
+
+// Order this thread's earlier generic-proxy accesses to shared memory before
+// later async-proxy (bulk copy) writes to it.
+__device__ __forceinline__ void fence_proxy_async_smem()
+{
+    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+}
+
+// Copy `bytes` (a multiple of 16; both addresses 16-byte aligned) from global
+// to shared memory; completion is counted on `bar` as transaction bytes.
+__device__ __forceinline__ void bulk_copy_g2s(void *dst, const void *src, unsigned bytes, uint64_t *bar)
+{
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
+            smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+
+}  // namespace dect
+
+namespace dect {
+
+// Ampere-style asynchronous 16-byte global -> shared copies (L2 only).
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(smem_u32(smem)), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
 
 }  // namespace dect

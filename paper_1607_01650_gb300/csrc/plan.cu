@@ -313,6 +313,122 @@ __global__ void k_col_sort(const int64_t *__restrict__ colptr, int64_t N,
     }
 }
 
+// Per-tile sinogram windows for the shared-memory A^T (one block per tile):
+// per view the range of bins that the tile's pixels meet, widened to an even
+// start and an even count (16-byte aligned copies for any batch of >= 2
+// images); prefix offsets; and the tile-local index of every entry.
+__global__ void k_win_build(const int64_t *__restrict__ colptr, const Entry *__restrict__ tent, int n,
+                            int nv, int nvp, int nb, int *__restrict__ wray0, int *__restrict__ wcnt,
+                            int *__restrict__ woff, int *__restrict__ wtot,
+                            Entry *__restrict__ tlocal, int *__restrict__ wmax)
+{
+    extern __shared__ int sw[];  // [2 * nv]
+    int *lo = sw, *hi = sw + nv;
+    const int tiles_x = (n + kWinTW - 1) / kWinTW;
+    const int tile = blockIdx.x, ty = tile / tiles_x, tx = tile % tiles_x;
+    for (int v = threadIdx.x; v < nv; v += blockDim.x) {
+        lo[v] = 0x7fffffff;
+        hi[v] = -1;
+    }
+    __syncthreads();
+    for (int s = 0; s < kWinTH * kWinTW; ++s) {
+        const int i = ty * kWinTH + s / kWinTW, j = tx * kWinTW + s % kWinTW;
+        if (i >= n || j >= n) continue;
+        const int64_t pix = (int64_t)i * n + j;
+        for (int64_t k = colptr[pix] + threadIdx.x; k < colptr[pix + 1]; k += blockDim.x) {
+            const int ray = tent[k].x, v = ray / nb;
+            atomicMin(&lo[v], ray);
+            atomicMax(&hi[v], ray);
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int off = 0;
+        for (int v = 0; v < nv; ++v) {
+            int start = 0, cnt = 0;
+            if (hi[v] >= 0) {
+                start = lo[v] & ~1;
+                cnt = ((hi[v] + 2) & ~1) - start;
+            }
+            wray0[(int64_t)tile * nvp + v] = start;
+            wcnt[(int64_t)tile * nvp + v] = cnt;
+            woff[(int64_t)tile * nvp + v] = off;
+            lo[v] = start;
+            hi[v] = off;
+            off += cnt;
+        }
+        for (int v = nv; v < nvp; ++v) {
+            wray0[(int64_t)tile * nvp + v] = 0;
+            wcnt[(int64_t)tile * nvp + v] = 0;
+            woff[(int64_t)tile * nvp + v] = off;
+        }
+        wtot[tile] = off;
+        atomicMax(wmax, off);
+    }
+    __syncthreads();
+    for (int s = 0; s < kWinTH * kWinTW; ++s) {
+        const int i = ty * kWinTH + s / kWinTW, j = tx * kWinTW + s % kWinTW;
+        if (i >= n || j >= n) continue;
+        const int64_t pix = (int64_t)i * n + j;
+        for (int64_t k = colptr[pix] + threadIdx.x; k < colptr[pix + 1]; k += blockDim.x) {
+            const Entry t = tent[k];
+            const int v = t.x / nb;
+            tlocal[k] = make_int2(hi[v] + (t.x - lo[v]), t.y);
+        }
+    }
+}
+
+// Entries of each tile, padded to an even count.
+__global__ void k_tile_count(const int64_t *__restrict__ colptr, int n, int ntiles,
+                             int64_t *__restrict__ cnt)
+{
+    const int tile = blockIdx.x * blockDim.x + threadIdx.x;
+    if (tile >= ntiles) return;
+    const int tiles_x = (n + kWinTW - 1) / kWinTW, ty = tile / tiles_x, tx = tile % tiles_x;
+    int64_t c = 0;
+    for (int s = 0; s < kWinTP; ++s) {
+        const int i = ty * kWinTH + s / kWinTW, j = tx * kWinTW + s % kWinTW;
+        if (i < n && j < n) {
+            const int64_t pix = (int64_t)i * n + j;
+            c += colptr[pix + 1] - colptr[pix];
+        }
+    }
+    cnt[tile] = (c + 1) & ~(int64_t)1;
+}
+
+// Copy each tile's tile-local entries to their tile-major place (one block per tile).
+__global__ void k_tile_fill(const int64_t *__restrict__ colptr, const Entry *__restrict__ tlocal, int n,
+                            const int64_t *__restrict__ tbase, int *__restrict__ tpo,
+                            Entry *__restrict__ tmaj, int *__restrict__ emax)
+{
+    const int tile = blockIdx.x;
+    const int tiles_x = (n + kWinTW - 1) / kWinTW, ty = tile / tiles_x, tx = tile % tiles_x;
+    __shared__ int off[kWinTP + 1];
+    if (threadIdx.x == 0) {
+        int o = 0;
+        for (int s = 0; s < kWinTP; ++s) {
+            off[s] = o;
+            const int i = ty * kWinTH + s / kWinTW, j = tx * kWinTW + s % kWinTW;
+            if (i < n && j < n) {
+                const int64_t pix = (int64_t)i * n + j;
+                o += (int)(colptr[pix + 1] - colptr[pix]);
+            }
+        }
+        off[kWinTP] = o;
+        for (int s = 0; s <= kWinTP; ++s) tpo[(int64_t)tile * (kWinTP + 1) + s] = off[s];
+        if (o & 1) tmaj[tbase[tile] + o] = make_int2(0, 0);
+        atomicMax(emax, (int)(tbase[tile + 1] - tbase[tile]));
+    }
+    __syncthreads();
+    for (int s = 0; s < kWinTP; ++s) {
+        const int i = ty * kWinTH + s / kWinTW, j = tx * kWinTW + s % kWinTW;
+        if (i >= n || j >= n) continue;
+        const int64_t pix = (int64_t)i * n + j;
+        const int64_t b = colptr[pix], len = colptr[pix + 1] - b;
+        for (int64_t k = threadIdx.x; k < len; k += blockDim.x) tmaj[tbase[tile] + off[s] + k] = tlocal[b + k];
+    }
+}
+
 bool geometry_ok(const dect_geometry *g)
 {
     if (!g) return false;
@@ -354,6 +470,7 @@ extern "C" dect_status dect_plan_create(const dect_geometry *geom, int device, d
     p->nb = geom->n_bins;
     p->N = (int64_t)p->n * p->n;
     p->M = (int64_t)p->nv * p->nb;
+    for (int k = 0; k < 5; ++k) p->bwd_choice[k] = -1;
 
     // ray end points on the host, FP64 (see file header)
     std::vector<RayPts> h(p->M);
@@ -389,6 +506,8 @@ extern "C" dect_status dect_plan_create(const dect_geometry *geom, int device, d
         cudaFree(d_rays); cudaFree(d_cnt); cudaFree(d_al); cudaFree(d_ccnt);
         cudaFree(d_cursor); cudaFree(d_ccnt64); cudaFree(d_tmp);
         cudaFree(p->rowptr); cudaFree(p->ent); cudaFree(p->colptr); cudaFree(p->tent);
+        cudaFree(p->wray0); cudaFree(p->wcnt); cudaFree(p->woff); cudaFree(p->wtot); cudaFree(p->tlocal);
+        cudaFree(p->tmaj); cudaFree(p->tbase); cudaFree(p->tpo);
         delete p;
         return code;
     };
@@ -420,8 +539,11 @@ extern "C" dect_status dect_plan_create(const dect_geometry *geom, int device, d
     p->n_grid_aligned = (int64_t)al;
     if (nnz >= ((int64_t)1 << 31)) return fail(DECT_ERR_INVALID_ARG);
 
-    size_t ne = (size_t)(nnz > 0 ? nnz : 1);
+    // padding after the last row: the row kernels copy whole 16-byte pairs
+    // and whole batches, which may run past a row's end
+    size_t ne = (size_t)(nnz > 0 ? nnz : 1) + kTablePad;
     PLAN_CUDA(cudaMalloc(&p->ent, sizeof(Entry) * ne));
+    PLAN_CUDA(cudaMemsetAsync(p->ent, 0, sizeof(Entry) * ne, s));
     k_siddon_fill<<<(unsigned)((p->M + T - 1) / T), T, 0, s>>>(d_rays, p->M, g, p->rowptr, p->ent);
     PLAN_CUDA(cudaGetLastError());
 
@@ -432,6 +554,7 @@ extern "C" dect_status dect_plan_create(const dect_geometry *geom, int device, d
     PLAN_CUDA(cudaMalloc(&p->colptr, sizeof(int64_t) * (p->N + 1)));
     PLAN_CUDA(cudaMalloc(&d_tmp, sizeof(Entry) * ne));
     PLAN_CUDA(cudaMalloc(&p->tent, sizeof(Entry) * ne));
+    PLAN_CUDA(cudaMemsetAsync(p->tent, 0, sizeof(Entry) * ne, s));
     PLAN_CUDA(cudaMemsetAsync(d_ccnt, 0, sizeof(int) * p->N, s));
     PLAN_CUDA(cudaMemsetAsync(d_cursor, 0, sizeof(int) * p->N, s));
     if (nnz > 0) {
@@ -448,6 +571,53 @@ extern "C" dect_status dect_plan_create(const dect_geometry *geom, int device, d
         int64_t threads = p->N * 32;
         k_col_sort<<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(p->colptr, p->N, d_tmp, p->tent);
         PLAN_CUDA(cudaGetLastError());
+    }
+    // shared-memory windows of the tiled A^T
+    if (p->nv <= kWinMaxViews && nnz > 0) {
+        const int tiles_x = (p->n + kWinTW - 1) / kWinTW, tiles_y = (p->n + kWinTH - 1) / kWinTH;
+        p->win_tiles = tiles_x * tiles_y;
+        p->nvp = (p->nv + 3) & ~3;
+        const size_t tv = (size_t)p->win_tiles * p->nvp;
+        PLAN_CUDA(cudaMalloc(&p->wray0, sizeof(int) * tv));
+        PLAN_CUDA(cudaMalloc(&p->wcnt, sizeof(int) * tv));
+        PLAN_CUDA(cudaMalloc(&p->woff, sizeof(int) * tv));
+        PLAN_CUDA(cudaMalloc(&p->wtot, sizeof(int) * p->win_tiles));
+        PLAN_CUDA(cudaMalloc(&p->tlocal, sizeof(Entry) * ne));
+        PLAN_CUDA(cudaMemsetAsync(p->tlocal, 0, sizeof(Entry) * ne, s));
+        int *d_wmax = d_ccnt;  // reuse a scratch int
+        PLAN_CUDA(cudaMemsetAsync(d_wmax, 0, sizeof(int), s));
+        const size_t sm = sizeof(int) * 2 * p->nv;
+        if (sm > 48 * 1024)
+            PLAN_CUDA(cudaFuncSetAttribute(k_win_build, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+        k_win_build<<<p->win_tiles, 256, sm, s>>>(p->colptr, p->tent, p->n, p->nv, p->nvp, p->nb, p->wray0, p->wcnt,
+                                                   p->woff, p->wtot, p->tlocal, d_wmax);
+        PLAN_CUDA(cudaGetLastError());
+        int wmax = 0;
+        PLAN_CUDA(cudaMemcpyAsync(&wmax, d_wmax, sizeof(int), cudaMemcpyDeviceToHost, s));
+        PLAN_CUDA(cudaStreamSynchronize(s));
+        // tile-major copy of the tile-local entries
+        const int nt = p->win_tiles;
+        PLAN_CUDA(cudaMalloc(&p->tbase, sizeof(int64_t) * (nt + 1)));
+        PLAN_CUDA(cudaMalloc(&p->tpo, sizeof(int) * (size_t)nt * (kWinTP + 1)));
+        int64_t *d_tcnt = nullptr;
+        PLAN_CUDA(cudaMalloc(&d_tcnt, sizeof(int64_t) * nt));
+        k_tile_count<<<(nt + 255) / 256, 256, 0, s>>>(p->colptr, p->n, nt, d_tcnt);
+        PLAN_CUDA(cudaGetLastError());
+        PLAN_CUDA(scan_exclusive(d_tcnt, nt, p->tbase, s));
+        int64_t tot = 0;
+        PLAN_CUDA(cudaMemcpyAsync(&tot, p->tbase + nt, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+        PLAN_CUDA(cudaStreamSynchronize(s));
+        cudaFree(d_tcnt);
+        PLAN_CUDA(cudaMalloc(&p->tmaj, sizeof(Entry) * (size_t)(tot + kTablePad)));
+        PLAN_CUDA(cudaMemsetAsync(p->tmaj, 0, sizeof(Entry) * (size_t)(tot + kTablePad), s));
+        PLAN_CUDA(cudaMemsetAsync(d_wmax, 0, sizeof(int), s));
+        k_tile_fill<<<nt, 256, 0, s>>>(p->colptr, p->tlocal, p->n, p->tbase, p->tpo, p->tmaj, d_wmax);
+        PLAN_CUDA(cudaGetLastError());
+        int emax = 0;
+        PLAN_CUDA(cudaMemcpyAsync(&emax, d_wmax, sizeof(int), cudaMemcpyDeviceToHost, s));
+        PLAN_CUDA(cudaStreamSynchronize(s));
+        p->tile_ent_max = emax;
+        p->win_max = wmax;
     }
     PLAN_CUDA(cudaStreamSynchronize(s));
     cudaFree(d_rays); cudaFree(d_cnt); cudaFree(d_al); cudaFree(d_ccnt);
@@ -469,6 +639,14 @@ extern "C" dect_status dect_plan_destroy(dect_plan *p)
     cudaFree(p->ent);
     cudaFree(p->colptr);
     cudaFree(p->tent);
+    cudaFree(p->wray0);
+    cudaFree(p->wcnt);
+    cudaFree(p->woff);
+    cudaFree(p->wtot);
+    cudaFree(p->tlocal);
+    cudaFree(p->tmaj);
+    cudaFree(p->tbase);
+    cudaFree(p->tpo);
     cudaSetDevice(cur);
     delete p;
     return DECT_OK;
@@ -508,5 +686,39 @@ extern "C" dect_status dect_plan_copy_table(const dect_plan *p, int64_t *rowptr,
         }
     }
     DECT_CUDA(cudaStreamSynchronize(s));
+    return DECT_OK;
+}
+
+extern "C" dect_status dect_plan_get_tuning(const dect_plan *p, int images, int *choice, float us[4])
+{
+    if (!p || !choice || !us) return DECT_ERR_INVALID_ARG;
+    int idx;
+    switch (images) {
+    case 2: idx = 0; break;
+    case 4: idx = 1; break;
+    case 8: idx = 2; break;
+    case 16: idx = 3; break;
+    case 32: idx = 4; break;
+    default: return DECT_ERR_INVALID_ARG;
+    }
+    *choice = p->bwd_choice[idx];
+    for (int v = 0; v < 4; ++v) us[v] = p->bwd_choice[idx] >= 0 ? p->bwd_us[idx][v] : -1.f;
+    return DECT_OK;
+}
+
+extern "C" dect_status dect_plan_set_tuning(dect_plan *p, int images, int choice)
+{
+    if (!p || choice < -1 || choice > 3) return DECT_ERR_INVALID_ARG;
+    int idx;
+    switch (images) {
+    case 2: idx = 0; break;
+    case 4: idx = 1; break;
+    case 8: idx = 2; break;
+    case 16: idx = 3; break;
+    case 32: idx = 4; break;
+    default: return DECT_ERR_INVALID_ARG;
+    }
+    p->bwd_choice[idx] = choice;
+    for (int v = 0; v < 4; ++v) p->bwd_us[idx][v] = -1.f;
     return DECT_OK;
 }

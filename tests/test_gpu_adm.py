@@ -129,3 +129,28 @@ def test_paper_size_first_iterations():
     for i in range(2):
         for e in range(2):
             assert rel_l2(x[i, e], outs[i][0][e]) <= 1e-4
+
+
+@pytest.mark.parametrize("ns", [1, 3, 16])
+def test_every_backprojector_variant(ns):
+    """Each A^T variant the autotuner can pick gives the oracle's result."""
+    g = synth.tiny_geometry(n=52, nv=24, nb=80, px=1.0, sod=130.0, sdd=260.0)
+    slices = [synth.make_slice(g, seed=300 + i, i0=1e5) for i in range(ns)]
+    plan = dect.Plan(g)
+    t = oracle.table(g)
+    m = np.stack([s.m for s in slices])
+    width = min(32, 1 << (2 * ns - 1).bit_length())
+    prm = dect.AdmParams(mu=MU, rho=RHO, max_iter=12)
+    for v in range(4):
+        plan.set_tuning(width, v)
+        x, _ = dect.adm_tv(plan, torch.tensor(m, dtype=torch.float32, device="cuda"), prm)
+        x = x.cpu().numpy()
+        for i in range(ns):
+            op = oracle.AdmParams(mu=MU, rho=RHO, max_iter=12, step_rule=oracle.CAUCHY)
+            xo, _ = oracle.adm_dual(t, m[i].astype(np.float32).astype(np.float64), op)
+            for e in range(2):
+                assert rel_l2(x[i, e], xo[e]) <= 1e-4, (v, i, e)
+    plan.set_tuning(width, -1)
+    dect.adm_tv(plan, torch.tensor(m, dtype=torch.float32, device="cuda"), prm)
+    choice, us = plan.tuning(width)
+    assert 0 <= choice <= 3 and us[choice] > 0
