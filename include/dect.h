@@ -210,6 +210,43 @@ typedef struct {
 dect_status dect_pls_decompose(const float *x, int n, int batch, const dect_pls_params *params,
                                float *u, dect_pls_report *reports, dect_stream stream);
 
+/*
+ * dect_pls_decompose without any device allocation.  (The paper has no
+ * counterpart: this is a service of the library, not a step of the method.)
+ *
+ * Who needs it: callers that must not allocate device memory while they
+ * run -- e.g. an inline reconstruction service that reserves the whole
+ * device pool at start-up and keeps its footprint fixed, or a plug-in inside
+ * a process whose own allocator owns the GPU.  This variant computes exactly
+ * what dect_pls_decompose computes (same kernels, same arguments, same
+ * results) but takes its scratch from one fixed array compiled into the
+ * library, of DECT_PLS_NOALLOC_SCRATCH_BYTES bytes, which every device that
+ * loads the library holds until the process exits.  It calls no cudaMalloc,
+ * cudaFree or other allocating routine, creates no stream, event or graph and
+ * pins no host memory; the caller still passes x and u.
+ *
+ * Limits: batch * n * n <= DECT_PLS_NOALLOC_MAX_PIXELS and
+ * batch <= DECT_PLS_NOALLOC_MAX_BATCH; larger work returns
+ * DECT_ERR_INVALID_ARG (dect_last_error() says why) -- use
+ * dect_pls_decompose for it.
+ *
+ * Shared state: every call on a device uses the same array, which keeps the
+ * previous call's contents (the call clears what must start at zero).  Calls
+ * whose work overlaps on the GPU -- e.g. on two streams without an ordering
+ * between them, or from two host threads -- race on it and give wrong
+ * results; order them on one stream or serialise them.
+ *
+ * The first call on each device looks up the array's device address
+ * (cudaGetSymbolAddress, with that device current) and caches it; make that
+ * first call before any stream capture on that device.  Synchronises
+ * `stream`.
+ */
+#define DECT_PLS_NOALLOC_MAX_PIXELS 262144
+#define DECT_PLS_NOALLOC_MAX_BATCH 64
+#define DECT_PLS_NOALLOC_SCRATCH_BYTES (14u << 20)
+dect_status dect_pls_decompose_noalloc(const float *x, int n, int batch, const dect_pls_params *params,
+                                       float *u, dect_pls_report *reports, dect_stream stream);
+
 /* Kernel timing of one dect_adm_tv_ex call, from CUDA events recorded
  * around the launches of the two table kernels inside the iteration graph. */
 typedef struct {

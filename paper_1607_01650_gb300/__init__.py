@@ -78,6 +78,7 @@ _SIGS = {
     "dect_adm_tv": (C.c_int, [_P, _P, _P, C.c_int, C.POINTER(_AdmParams), _P, _P]),
     "dect_adm_tv_ex": (C.c_int, [_P, _P, _P, C.c_int, C.POINTER(_AdmParams), _P, _P, _P]),
     "dect_pls_decompose": (C.c_int, [_P, C.c_int, C.c_int, C.POINTER(_PlsParams), _P, _P, _P]),
+    "dect_pls_decompose_noalloc": (C.c_int, [_P, C.c_int, C.c_int, C.POINTER(_PlsParams), _P, _P, _P]),
     "dect_kernel_launches": (C.c_int64, []),
     "dect_plan_get_tuning": (C.c_int, [_P, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_float)]),
     "dect_plan_set_tuning": (C.c_int, [_P, C.c_int, C.c_int]),
@@ -358,3 +359,33 @@ def pls_decompose(x, params: PlsParams, u=None, stream=None):
                                      _stream(stream)), "dect_pls_decompose")
     reps = [(tuple(r.iters), tuple(r.relres)) for r in rep[:batch]]
     return u, reps
+
+
+# Limits of the allocation-free decomposition (include/dect.h).
+PLS_NOALLOC_MAX_PIXELS = 262144
+PLS_NOALLOC_MAX_BATCH = 64
+
+
+def pls_decompose_noalloc(x, params: PlsParams, u, stream=None):
+    """Same as pls_decompose, for callers that cannot allocate device memory.
+
+    The library takes the decomposition's scratch from a fixed array it holds
+    on every device (no cudaMalloc, no stream, event or graph creation); `u`
+    must be passed in.  Work is limited to batch * n * n <= PLS_NOALLOC_MAX_PIXELS
+    and batch <= PLS_NOALLOC_MAX_BATCH.  Calls share that array, so calls that
+    could overlap on the GPU must be ordered on one stream.
+    """
+    import torch
+    if x.dim() != 4 or x.shape[1] != 2 or x.shape[2] != x.shape[3]:
+        raise DectError("x must be [B, 2, n, n]")
+    if u is None or u.shape != x.shape:
+        raise DectError("u must be given, with the shape of x")
+    n = x.shape[-1]
+    batch = x.shape[0]
+    dev = x.device.index
+    rep = (_PlsReport * max(batch, 1))()
+    _check(load().dect_pls_decompose_noalloc(_ptr(x, torch.float32, dev), n, batch,
+                                             C.byref(params._c()), _ptr(u, torch.float32, dev),
+                                             C.cast(rep, C.c_void_p), _stream(stream)),
+           "dect_pls_decompose_noalloc")
+    return u, [(tuple(r.iters), tuple(r.relres)) for r in rep[:batch]]

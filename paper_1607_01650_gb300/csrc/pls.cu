@@ -17,6 +17,8 @@
 
 #include <algorithm>
 #include <cmath>
+#include <mutex>
+#include <string>
 #include <vector>
 
 #include "dect_internal.cuh"
@@ -477,5 +479,168 @@ extern "C" dect_status dect_pls_decompose(const float *x, int n, int batch, cons
             }
     }
     (void)dev;
+    return DECT_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Allocation-free variant of dect_pls_decompose.
+//
+// Some callers cannot allocate device memory while they run: for example an
+// inline reconstruction service that reserves the whole device pool at
+// start-up and must keep its footprint fixed, or a plug-in hosted by a
+// process whose own allocator owns the GPU.  This entry point takes its
+// scratch from one fixed array in the library image instead of the
+// stream-ordered allocator, creates no stream, event or graph, and pins no
+// host memory.
+// ---------------------------------------------------------------------------
+namespace dect {
+namespace {
+
+// Upper bounds of the allocation-free path (see dect.h).
+constexpr int64_t kNoAllocMaxPixels = DECT_PLS_NOALLOC_MAX_PIXELS;
+constexpr int kNoAllocMaxBatch = DECT_PLS_NOALLOC_MAX_BATCH;
+constexpr size_t kNoAllocBytes = (size_t)14 << 20;
+
+// The scratch itself: every device that loads the library holds it until
+// the process exits.  In host code this name is only a stand-in; the device
+// address comes from cudaGetSymbolAddress.
+static __device__ __align__(256) unsigned char g_pls_scratch[kNoAllocBytes];
+
+std::mutex g_scratch_mu;
+void *g_scratch_addr[256];  // per device ordinal, filled on the first call
+
+cudaError_t scratch_address(int dev, void **out)
+{
+    std::lock_guard<std::mutex> lk(g_scratch_mu);
+    if (dev < 0 || dev >= 256) return cudaErrorInvalidDevice;
+    if (!g_scratch_addr[dev]) {
+        void *p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_pls_scratch);
+        if (e != cudaSuccess) return e;
+        g_scratch_addr[dev] = p;
+    }
+    *out = g_scratch_addr[dev];
+    return cudaSuccess;
+}
+
+}  // namespace
+}  // namespace dect
+
+extern "C" dect_status dect_pls_decompose_noalloc(const float *x, int n, int batch,
+                                                  const dect_pls_params *prm, float *u,
+                                                  dect_pls_report *reports, dect_stream stream)
+{
+    if (!prm || n < 1 || batch < 0 || n > 16384) return DECT_ERR_INVALID_ARG;
+    if (batch == 0) return DECT_OK;
+    if (!x || !u) return DECT_ERR_INVALID_ARG;
+    if ((int64_t)batch * n * n > kNoAllocMaxPixels || batch > kNoAllocMaxBatch) {
+        set_error_text("dect_pls_decompose_noalloc: batch * n * n must be <= " +
+                       std::to_string(kNoAllocMaxPixels) + " and batch <= " +
+                       std::to_string(kNoAllocMaxBatch) + " (use dect_pls_decompose for larger work)");
+        return DECT_ERR_INVALID_ARG;
+    }
+    {
+        const size_t span = (size_t)batch * 2 * n * n * sizeof(float);
+        const char *xa = (const char *)x, *ua = (const char *)u;
+        if (xa < ua + span && ua < xa + span) return DECT_ERR_INVALID_ARG;
+    }
+    if (!(prm->gamma >= 0) || !(prm->edge_eps >= 0) || prm->max_iter < 0 || !std::isfinite(prm->gamma))
+        return DECT_ERR_INVALID_ARG;
+    const double a = prm->eta[0][0], b = prm->eta[1][0], c = prm->eta[0][1], e = prm->eta[1][1];
+    const double det = a * e - b * c;
+    if (!(std::fabs(det) > 0) || !std::isfinite(det)) return DECT_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    int dev = 0;
+    DECT_CUDA(cudaGetDevice(&dev));
+    void *scratch = nullptr;
+    DECT_CUDA(scratch_address(dev, &scratch));
+
+    const int64_t N = (int64_t)n * n;
+    const int nvec = 2 * batch;
+    const int64_t want = (N + kBlock - 1) / kBlock;
+    const int gx = (int)std::max<int64_t>(1, std::min<int64_t>(want, std::max(1, (kSMs * 8) / nvec)));
+
+    // same layout as the allocating path, placed in the fixed array
+    const size_t nf = (size_t)nvec * N;
+    char *base = (char *)scratch;
+    size_t o = 0;
+    auto take = [&](size_t nb) { char *p = base + o; o = (o + nb + 255) & ~(size_t)255; return p; };
+    float *r = (float *)take(nf * 4);
+    float *z = (float *)take(nf * 4);
+    float *pa = (float *)take(nf * 4);
+    float *pb = (float *)take(nf * 4);
+    float *Ap = (float *)take(nf * 4);
+    float *mh = (float *)take((size_t)batch * N * 4);
+    float *ml = (float *)take((size_t)batch * N * 4);
+    unsigned char *mask = (unsigned char *)take((size_t)batch * N);
+    PlsDev D;
+    D.part = (double *)take((size_t)gx * nvec * 3 * 8);
+    D.red = (double *)take((size_t)nvec * 3 * 8);
+    D.alpha = (double *)take((size_t)nvec * 8);
+    D.beta = (double *)take((size_t)nvec * 8);
+    D.rz = (double *)take((size_t)nvec * 8);
+    D.bnorm = (double *)take((size_t)nvec * 8);
+    D.relres = (double *)take((size_t)nvec * 8);
+    D.iters = (int *)take((size_t)nvec * 4);
+    D.done = (int *)take((size_t)nvec * 4);
+    D.it = (int *)take(4);
+    D.all_done = (int *)take(4);
+    D.ctr = (unsigned *)take(8);
+    D.maxbits = (int *)take((size_t)2 * batch * 4);
+    if (o > kNoAllocBytes) {  // cannot happen within the limits above
+        set_error_text("dect_pls_decompose_noalloc: scratch layout exceeds the fixed array");
+        return DECT_ERR_INVALID_ARG;
+    }
+    // the array keeps the previous call's contents: zero what must start at zero
+    DECT_CUDA(cudaMemsetAsync(D.ctr, 0, 8, s));
+    DECT_CUDA(cudaMemsetAsync(D.maxbits, 0, (size_t)2 * batch * 4, s));
+
+    PlsConst C;
+    C.n = n;
+    C.N = N;
+    C.nvec = nvec;
+    C.gamma = (float)prm->gamma;
+    C.eps = (float)prm->edge_eps;
+    C.tol = prm->tol;
+
+    dim3 gs((unsigned)gx, (unsigned)batch), gv((unsigned)gx, (unsigned)nvec);
+    k_prep<<<gs, kBlock, 0, s>>>(x, n, N, a, b, c, e, u, mh, ml, D.maxbits);
+    DECT_LAUNCH_CHECK();
+    k_mask<<<gs, kBlock, 0, s>>>(mh, ml, N, D.maxbits, (float)prm->edge_tau, mask);
+    DECT_LAUNCH_CHECK();
+    k_init<<<gv, kBlock, 0, s>>>(u, mask, r, z, pa, C, D);
+    DECT_LAUNCH_CHECK();
+    count_launches(3);
+
+    // plain launches on the caller's stream; the stop flag is read into a
+    // host stack variable every 10 iterations when a tolerance is set
+    const int K = prm->max_iter;
+    const bool use_tol = prm->tol > 0.0;
+    float *p_cur = pa, *p_nxt = pb;
+    int done_flag = 0;
+    for (int it = 0; it < K; ++it) {
+        if (use_tol && it % 10 == 0) {
+            DECT_CUDA(cudaMemcpyAsync(&done_flag, D.all_done, sizeof(int), cudaMemcpyDeviceToHost, s));
+            DECT_CUDA(cudaStreamSynchronize(s));
+            if (done_flag) break;
+        }
+        k_cg_a<<<gv, kBlock, 0, s>>>(z, p_cur, p_nxt, Ap, mask, C, D);
+        k_cg_b<<<gv, kBlock, 0, s>>>(u, p_nxt, Ap, r, z, mask, C, D);
+        DECT_LAUNCH_CHECK();
+        count_launches(2);
+        std::swap(p_cur, p_nxt);
+    }
+    int hit[2 * kNoAllocMaxBatch];
+    double hrel[2 * kNoAllocMaxBatch];
+    DECT_CUDA(cudaMemcpyAsync(hit, D.iters, nvec * sizeof(int), cudaMemcpyDeviceToHost, s));
+    DECT_CUDA(cudaMemcpyAsync(hrel, D.relres, nvec * sizeof(double), cudaMemcpyDeviceToHost, s));
+    DECT_CUDA(cudaStreamSynchronize(s));
+    if (reports) {
+        for (int sl = 0; sl < batch; ++sl)
+            for (int m = 0; m < 2; ++m) {
+                reports[sl].iters[m] = hit[2 * sl + m];
+                reports[sl].relres[m] = hrel[2 * sl + m];
+            }
+    }
     return DECT_OK;
 }
