@@ -101,7 +101,7 @@ __device__ __forceinline__ void shrink2(float w0, float w1, float t, float &z0, 
 // final_pass: only the f / r step and the two norms (the result's objective).
 // ---------------------------------------------------------------------------
 template <int NB>
-__global__ void __launch_bounds__(kBlock) k_tv(const float *__restrict__ f_in, float *__restrict__ f_out,
+__global__ void __launch_bounds__(kBlock, 4) k_tv(const float *__restrict__ f_in, float *__restrict__ f_out,
                                                const float *__restrict__ G, float *__restrict__ lam,
                                                float *__restrict__ z, float *__restrict__ p,
                                                float *__restrict__ r, const float *__restrict__ q,

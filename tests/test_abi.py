@@ -1,0 +1,77 @@
+"""C ABI checks that need no GPU: the library builds for sm_103a, loads, and
+exports every entry point that include/dect.h declares; argument checks run
+on the host before any CUDA call."""
+import ctypes as C
+import os
+import re
+import shutil
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "dect.h")
+
+nvcc_missing = shutil.which("nvcc") is None and not os.path.exists("/usr/local/cuda/bin/nvcc")
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(dect_[a-z0-9_]+)\s*\(", text)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    if nvcc_missing:
+        pytest.skip("no CUDA toolkit to build libdect")
+    from paper_1607_01650_gb300 import _build
+    path = _build.build()
+    return C.CDLL(path), path
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ("dect_plan_create", "dect_plan_destroy", "dect_project", "dect_backproject",
+                     "dect_adm_tv", "dect_pls_decompose", "dect_status_string"):
+        assert required in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    cdll, path = lib
+    missing = [n for n in declared_functions() if not hasattr(cdll, n)]
+    assert not missing, missing
+    out = subprocess.run(["nm", "-D", "--defined-only", path], capture_output=True, text=True).stdout
+    exported = set(re.findall(r"\bT (dect_[a-z0-9_]+)", out))
+    assert set(declared_functions()) <= exported
+
+
+def test_binding_covers_the_header(lib):
+    import paper_1607_01650_gb300 as dect
+    assert set(declared_functions()) <= set(dect._SIGS)
+
+
+def test_built_for_sm_103a_only():
+    from paper_1607_01650_gb300 import _build
+    assert _build.ARCH == ["-gencode", "arch=compute_103a,code=sm_103a"]
+
+
+def test_host_side_argument_checks(lib):
+    import paper_1607_01650_gb300 as dect
+    L = dect.load()
+    assert L.dect_status_string(0) == b"ok"
+    assert L.dect_status_string(1) == b"invalid argument"
+    assert L.dect_version() >= 100
+    # NULL plan / pointers and bad geometry are refused before any CUDA call
+    assert L.dect_project(None, None, None, 1, None) == 1
+    assert L.dect_backproject(None, None, None, 1, None) == 1
+    assert L.dect_pls_decompose(None, 4, 1, None, None, None, None) == 1
+    out = C.c_void_p()
+    bad = dect._Geometry(0, 1.0, 10, 10, 1.0, 100.0, 200.0, 0.0, 6.28, 0.0)   # n = 0
+    assert L.dect_plan_create(C.byref(bad), 0, None, C.byref(out)) == 1
+    bad = dect._Geometry(64, 1.0, 10, 10, 1.0, 20.0, 200.0, 0.0, 6.28, 0.0)   # source inside the image
+    assert L.dect_plan_create(C.byref(bad), 0, None, C.byref(out)) == 1
+    bad = dect._Geometry(64, 1.0, 10, 10, 1.0, 100.0, 50.0, 0.0, 6.28, 0.0)   # SDD < SOD
+    assert L.dect_plan_create(C.byref(bad), 0, None, C.byref(out)) == 1
+    assert L.dect_plan_destroy(None) == 0
+    assert L.dect_plan_get_tuning(None, 2, None, None) == 1
