@@ -335,10 +335,13 @@ def main():
     fwd_n = sum(p.fwd_launches for p in state["prof"])
     bwd_n = sum(p.bwd_launches for p in state["prof"])
     p0 = state["prof"][-1]
+    width = min(32, 1 << (2 * S - 1).bit_length())
+    choice, _ = plan.tuning(width)
+    bwd_name = ["k_bwd<tile4>", "k_bwd<tile8>", "k_bwd<tile16>", "k_bwd_win"][choice] if choice >= 0 else "k_bwd"
     if fwd_ms >= bwd_ms:
         kname, avg_ms, bytes_ = "k_fwd", fwd_ms / max(fwd_n, 1), p0.table_bytes_fwd
     else:
-        kname, avg_ms, bytes_ = "k_bwd", bwd_ms / max(bwd_n, 1), p0.table_bytes_bwd
+        kname, avg_ms, bytes_ = bwd_name, bwd_ms / max(bwd_n, 1), p0.table_bytes_bwd
     peak, peak_src = measured_peaks()
     achieved = bytes_ / (avg_ms / 1e3) / 1e9
     traffic = committed_traffic(kname)
