@@ -176,6 +176,26 @@ dect_status dect_adm_tv(const dect_plan *plan, const float *m, float *x, int n_s
                         const dect_adm_params *params, dect_adm_report *reports,
                         dect_stream stream);
 
+/* One group of a mixed-geometry batch: slices that share `plan`. */
+typedef struct {
+    const dect_plan *plan;
+    const float *m;            /* [n_slices][2][n_views][n_bins], device           */
+    float *x;                  /* [n_slices][2][n][n], device (in: warm start)     */
+    int n_slices;
+    dect_adm_report *reports;  /* HOST [n_slices * 2] or NULL                       */
+} dect_adm_group;
+
+/*
+ * ADM-TV of a batch of slices of uneven size and view count, Eq. (3)-(10):
+ * each group is reconstructed as dect_adm_tv would (all its slices'
+ * channels interleaved per table pass), and the groups run concurrently,
+ * each on its own stream ordered after `stream`, from up to `workers` host
+ * threads (0 = min(n_groups, 8)).  Plans must differ between groups.
+ * Synchronises `stream`.  Returns the first error of any group.
+ */
+dect_status dect_adm_tv_groups(const dect_adm_group *groups, int n_groups,
+                               const dect_adm_params *params, int workers, dect_stream stream);
+
 typedef struct {
     double eta[2][2];   /* eta[material][energy]: attenuation (1/mm) of basis material
                            1 / 2 at energy 0 (high) / 1 (low); D of Eq. (12)            */
@@ -287,6 +307,14 @@ dect_status dect_plan_set_tuning(dect_plan *plan, int images, int choice);
 /* Number of kernels libdect has launched in this process so far (kernel
  * launches plus the kernel nodes of every graph launch). */
 int64_t dect_kernel_launches(void);
+
+/*
+ * Self-test of the bounded device waits (failure detection without a GPU
+ * fault): a kernel waits on a barrier that nothing completes, for at most
+ * `polls` polls, and returns.  Returns DECT_ERR_TIMEOUT when the wait ran out
+ * (the expected result), DECT_OK otherwise.  Synchronises `stream`.
+ */
+dect_status dect_selftest_bounded_wait(unsigned polls, dect_stream stream);
 
 /* Text of a status code (static storage). */
 const char *dect_status_string(dect_status s);

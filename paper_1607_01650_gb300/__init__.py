@@ -55,6 +55,11 @@ class _AdmProfile(C.Structure):
                 ("table_bytes_fwd", C.c_int64), ("table_bytes_bwd", C.c_int64)]
 
 
+class _AdmGroup(C.Structure):
+    _fields_ = [("plan", C.c_void_p), ("m", C.c_void_p), ("x", C.c_void_p), ("n_slices", C.c_int),
+                ("reports", C.c_void_p)]
+
+
 class _PlsParams(C.Structure):
     _fields_ = [("eta", (C.c_double * 2) * 2), ("gamma", C.c_double), ("edge_tau", C.c_double),
                 ("edge_eps", C.c_double), ("max_iter", C.c_int), ("tol", C.c_double)]
@@ -78,8 +83,10 @@ _SIGS = {
     "dect_adm_tv": (C.c_int, [_P, _P, _P, C.c_int, C.POINTER(_AdmParams), _P, _P]),
     "dect_adm_tv_ex": (C.c_int, [_P, _P, _P, C.c_int, C.POINTER(_AdmParams), _P, _P, _P]),
     "dect_pls_decompose": (C.c_int, [_P, C.c_int, C.c_int, C.POINTER(_PlsParams), _P, _P, _P]),
+    "dect_adm_tv_groups": (C.c_int, [C.POINTER(_AdmGroup), C.c_int, C.POINTER(_AdmParams), C.c_int, _P]),
     "dect_pls_decompose_noalloc": (C.c_int, [_P, C.c_int, C.c_int, C.POINTER(_PlsParams), _P, _P, _P]),
     "dect_kernel_launches": (C.c_int64, []),
+    "dect_selftest_bounded_wait": (C.c_int, [C.c_uint, _P]),
     "dect_plan_get_tuning": (C.c_int, [_P, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_float)]),
     "dect_plan_set_tuning": (C.c_int, [_P, C.c_int, C.c_int]),
     "dect_status_string": (C.c_char_p, [C.c_int]),
@@ -315,6 +322,35 @@ def adm_tv(plan: Plan, m, params: AdmParams, x=None, stream=None, profile: bool 
         return x, reps, AdmProfile(prof.fwd_ms_total, prof.bwd_ms_total, prof.fwd_launches,
                                    prof.bwd_launches, prof.table_bytes_fwd, prof.table_bytes_bwd)
     return x, reps
+
+
+def adm_tv_groups(groups, params: AdmParams, workers: int = 0, stream=None):
+    """ADM-TV of slices of uneven geometry (Eq. (3)-(10)) in one call.
+
+    groups: list of (plan, m [S, 2, nv, nb], x [S, 2, n, n] or None); plans must
+    differ.  Groups run concurrently on their own streams.  Returns
+    [(x, reports)] in the order given.
+    """
+    import torch
+    cg = (_AdmGroup * max(len(groups), 1))()
+    keep = []
+    out = []
+    for i, (plan, m, x) in enumerate(groups):
+        g = plan.geom
+        if m.dim() != 4 or m.shape[1:] != (2, g.nv, g.nb):
+            raise DectError("group %d: m must be [S, 2, nv, nb]" % i)
+        S = m.shape[0]
+        if x is None:
+            x = torch.zeros((S, 2, g.n, g.n), device=m.device, dtype=torch.float32)
+        rep = (_AdmReport * max(2 * S, 1))()
+        keep.append(rep)
+        cg[i] = _AdmGroup(plan.handle.value, _ptr(m, torch.float32, plan.device).value,
+                          _ptr(x, torch.float32, plan.device).value, S, C.cast(rep, C.c_void_p).value)
+        out.append((x, rep, S))
+    _check(load().dect_adm_tv_groups(cg, len(groups), C.byref(params._c()), workers, _stream(stream)),
+           "dect_adm_tv_groups")
+    return [(x, [AdmReport(r.iters, bool(r.converged), r.objective, r.rel_change) for r in rep[:2 * S]])
+            for x, rep, S in out]
 
 
 def kernel_launches() -> int:

@@ -28,7 +28,9 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
+#include <thread>
 #include <vector>
 
 #include "dect_internal.cuh"
@@ -574,7 +576,9 @@ cudaError_t setup_window(const dect_plan *P, Work &W)
     const size_t bytes = 2 * stage + 2 * 3 * sizeof(int) * (size_t)P->nvp;
     if (bytes > kWinSmemMax) return cudaSuccess;
     auto kern = k_bwd_win<NB>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    // the attribute is per kernel and process-wide: always the same cap, so
+    // concurrent calls on plans with different windows cannot race on it
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kWinSmemMax);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kWinBlock, bytes);
@@ -973,4 +977,65 @@ extern "C" dect_status dect_adm_tv(const dect_plan *plan, const float *m, float 
                                    dect_stream stream)
 {
     return dect_adm_tv_ex(plan, m, x, n_slices, prm, reports, nullptr, stream);
+}
+
+extern "C" dect_status dect_adm_tv_groups(const dect_adm_group *groups, int n_groups,
+                                          const dect_adm_params *prm, int workers, dect_stream stream)
+{
+    if (!groups || n_groups < 0 || !prm || workers < 0) return DECT_ERR_INVALID_ARG;
+    if (n_groups == 0) return DECT_OK;
+    for (int i = 0; i < n_groups; ++i) {
+        if (!groups[i].plan || groups[i].n_slices < 0) return DECT_ERR_INVALID_ARG;
+        for (int j = 0; j < i; ++j)
+            if (groups[j].plan == groups[i].plan) return DECT_ERR_INVALID_ARG;  // plans must differ
+    }
+    const int device = groups[0].plan->device;
+    for (int i = 1; i < n_groups; ++i)
+        if (groups[i].plan->device != device) return DECT_ERR_INVALID_ARG;
+    DECT_CUDA(cudaSetDevice(device));
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaEvent_t start = nullptr;
+    DECT_CUDA(cudaEventCreateWithFlags(&start, cudaEventDisableTiming));
+    DECT_CUDA(cudaEventRecord(start, s));
+    const int nw = workers > 0 ? std::min(workers, n_groups) : std::min(n_groups, 8);
+    std::vector<dect_status> status(n_groups, DECT_OK);
+    std::vector<cudaEvent_t> done(n_groups, nullptr);
+    std::atomic<int> next{0};
+    auto work = [&]() {
+        cudaSetDevice(device);
+        cudaStream_t ws = nullptr;
+        if (cudaStreamCreateWithFlags(&ws, cudaStreamNonBlocking) != cudaSuccess) {
+            for (int g; (g = next.fetch_add(1)) < n_groups;) status[g] = DECT_ERR_CUDA;
+            return;
+        }
+        for (int g; (g = next.fetch_add(1)) < n_groups;) {
+            if (cudaStreamWaitEvent(ws, start, 0) != cudaSuccess) {
+                status[g] = DECT_ERR_CUDA;
+                continue;
+            }
+            const dect_adm_group &G = groups[g];
+            status[g] = dect_adm_tv(G.plan, G.m, G.x, G.n_slices, prm, G.reports, (dect_stream)ws);
+            cudaEvent_t e = nullptr;
+            if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) == cudaSuccess &&
+                cudaEventRecord(e, ws) == cudaSuccess)
+                done[g] = e;
+        }
+        cudaStreamSynchronize(ws);
+        cudaStreamDestroy(ws);
+    };
+    std::vector<std::thread> pool;
+    for (int w = 1; w < nw; ++w) pool.emplace_back(work);
+    work();
+    for (auto &t : pool) t.join();
+    dect_status first = DECT_OK;
+    for (int g = 0; g < n_groups; ++g) {
+        if (done[g]) {
+            cudaStreamWaitEvent(s, done[g], 0);
+            cudaEventDestroy(done[g]);
+        }
+        if (first == DECT_OK && status[g] != DECT_OK) first = status[g];
+    }
+    cudaEventDestroy(start);
+    DECT_CUDA(cudaStreamSynchronize(s));
+    return first;
 }

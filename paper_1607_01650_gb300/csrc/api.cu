@@ -46,3 +46,47 @@ extern "C" const char *dect_last_error(void) { return dect::g_err; }
 extern "C" int dect_version(void) { return 100; }
 
 extern "C" int64_t dect_kernel_launches(void) { return dect::g_launches.load(); }
+
+// ---------------------------------------------------------------------------
+// Self-test of the bounded device wait used by the staged kernels: one block
+// waits on an mbarrier that nothing arrives on, for at most `polls` polls,
+// and reports whether the wait ran out.  Nothing faults, traps or hangs.
+// ---------------------------------------------------------------------------
+#include "kernels.cuh"
+
+namespace dect {
+namespace {
+__global__ void k_wait_selftest(unsigned polls, int *timed_out)
+{
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x == 0) mbar_init(&bar, 1);
+    __syncthreads();
+    const bool got = mbar_wait_bounded(&bar, 0u, polls);
+    if (__syncthreads_or(!got) && threadIdx.x == 0) *timed_out = 1;
+    // complete the phase so the barrier is left balanced
+    if (threadIdx.x == 0) mbar_arrive_expect_tx(&bar, 0u);
+    __syncthreads();
+    mbar_wait_bounded(&bar, 0u, 1u << 20);
+}
+}  // namespace
+}  // namespace dect
+
+extern "C" dect_status dect_selftest_bounded_wait(unsigned polls, dect_stream stream)
+{
+    cudaStream_t s = (cudaStream_t)stream;
+    int *d = nullptr;
+    int h = 0;
+    DECT_CUDA(cudaMallocAsync((void **)&d, sizeof(int), s));
+    DECT_CUDA(cudaMemsetAsync(d, 0, sizeof(int), s));
+    dect::k_wait_selftest<<<1, 64, 0, s>>>(polls, d);
+    DECT_LAUNCH_CHECK();
+    dect::count_launches(1);
+    DECT_CUDA(cudaMemcpyAsync(&h, d, sizeof(int), cudaMemcpyDeviceToHost, s));
+    DECT_CUDA(cudaFreeAsync(d, s));
+    DECT_CUDA(cudaStreamSynchronize(s));
+    if (h) {
+        dect::set_error_text("dect_selftest_bounded_wait: the wait ran out after the poll limit");
+        return DECT_ERR_TIMEOUT;
+    }
+    return DECT_OK;
+}
