@@ -94,6 +94,8 @@ def _load():
             "orc_pls_diag": (None, [C.c_int, u8, C.c_double, C.c_double, d]),
             "orc_pls_pcg": (C.c_int, [C.c_int, u8, C.c_double, C.c_double, d, d,
                                       C.c_int, C.c_double, d]),
+            "orc_cnn_num_params": (C.c_int64, []),
+            "orc_cnn_run": (None, [d, C.c_double, d, C.c_int, C.c_int, d, d, d, d]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(_lib, name)
@@ -399,3 +401,49 @@ def pls_decompose(xh, xl, prm: PlsParams):
     u1, i1, _ = pls_pcg(mask, prm.gamma, prm.eps, d1, prm.max_iter, prm.tol)
     u2, i2, _ = pls_pcg(mask, prm.gamma, prm.eps, d2, prm.max_iter, prm.tol)
     return u1, u2, mask, (i1, i2)
+
+
+# ---------------------------------------------------------------------------
+# CNN warm start (not in the paper; the learned part of the workload)
+# ---------------------------------------------------------------------------
+
+def cnn_num_params() -> int:
+    return int(_load().orc_cnn_num_params())
+
+
+def cnn_forward(params, x, scale: float) -> np.ndarray:
+    """Encoder-decoder output x + s * net(x / s) for one image x [H][W] (H, W multiples of 4)."""
+    params = _f64(params)
+    x = _f64(x)
+    out = np.zeros_like(x)
+    _load().orc_cnn_run(_d(params), scale, _d(x), x.shape[0], x.shape[1], _d(out), None, None, None)
+    return out
+
+
+def cnn_loss_grad(params, x, target, scale: float):
+    """(loss, dloss/dparams) for L = mean (out - target)^2 on one image."""
+    params = _f64(params)
+    x = _f64(x)
+    target = _f64(target)
+    grad = np.zeros_like(params)
+    loss = C.c_double(0.0)
+    _load().orc_cnn_run(_d(params), scale, _d(x), x.shape[0], x.shape[1], None, _d(target), _d(grad),
+                        C.byref(loss))
+    return float(loss.value), grad
+
+
+CNN_LAYERS = [(1, 32), (32, 32), (32, 64), (64, 64), (64, 128), (128, 128), (192, 64), (64, 64),
+              (96, 32), (32, 32)]
+
+
+def cnn_init(seed: int) -> np.ndarray:
+    """He-normal weights, zero biases, zero head (so the untrained net is the identity)."""
+    rng = np.random.default_rng(seed)
+    parts = []
+    for cin, cout in CNN_LAYERS:
+        parts.append(rng.standard_normal(cout * cin * 9) * np.sqrt(2.0 / (cin * 9)))
+        parts.append(np.zeros(cout))
+    parts.append(np.zeros(33))
+    p = np.concatenate(parts)
+    assert p.size == cnn_num_params()
+    return p

@@ -559,3 +559,241 @@ int orc_pls_pcg(int n, const uint8_t *mask, double gamma, double eps, const doub
     free(r); free(z); free(p); free(Ap); free(M);
     return it;
 }
+
+/* ======================================================================== */
+/* CNN warm start (not in the paper): the encoder-decoder that maps a short */
+/* ADM reconstruction to a converged one.  FP64 definition by direct loops; */
+/* layout NCHW, one image per batch element, weights [Cout][Cin][3][3].     */
+/*                                                                          */
+/*   a1 = relu(conv(x/s, W1)),  e1 = relu(conv(a1, W2))           H  x 32   */
+/*   p1 = avgpool2(e1); a3 = relu(conv(p1,W3)); e2 = relu(conv(a3,W4)) 64   */
+/*   p2 = avgpool2(e2); a5 = relu(conv(p2,W5)); bt = relu(conv(a5,W6)) 128  */
+/*   c2 = [up2(bt), e2]; a7 = relu(conv(c2,W7)); d2 = relu(conv(a7,W8)) 64  */
+/*   c1 = [up2(d2), e1]; a9 = relu(conv(c1,W9)); d1 = relu(conv(a9,W10)) 32 */
+/*   out = x + s (Wh . d1 + bh)     (1x1 head, residual)                     */
+/* every conv has a bias; s is the input scale.                              */
+/* ======================================================================== */
+
+#define CNN_LAYERS 10
+static const int cnn_cin[CNN_LAYERS] = {1, 32, 32, 64, 64, 128, 192, 64, 96, 32};
+static const int cnn_cout[CNN_LAYERS] = {32, 32, 64, 64, 128, 128, 64, 64, 32, 32};
+
+/* Parameter vector: for each conv layer W[Cout][Cin][3][3] then b[Cout];
+   then the head Wh[32], bh[1]. */
+int64_t orc_cnn_num_params(void)
+{
+    int64_t n = 0;
+    for (int l = 0; l < CNN_LAYERS; ++l) n += (int64_t)cnn_cout[l] * cnn_cin[l] * 9 + cnn_cout[l];
+    return n + 32 + 1;
+}
+
+static void cnn_offsets(int64_t *wo, int64_t *bo, int64_t *ho)
+{
+    int64_t o = 0;
+    for (int l = 0; l < CNN_LAYERS; ++l) {
+        wo[l] = o;
+        o += (int64_t)cnn_cout[l] * cnn_cin[l] * 9;
+        bo[l] = o;
+        o += cnn_cout[l];
+    }
+    *ho = o;
+}
+
+/* y[co][h][w] = b[co] + sum_ci sum_kh sum_kw W[co][ci][kh][kw] x[ci][h+kh-1][w+kw-1] (zero padding) */
+static void conv3(const double *x, int cin, int H, int W, const double *Wt, const double *b, int cout,
+                  double *y)
+{
+    for (int co = 0; co < cout; ++co)
+        for (int h = 0; h < H; ++h)
+            for (int w = 0; w < W; ++w) {
+                double s = b[co];
+                for (int ci = 0; ci < cin; ++ci)
+                    for (int kh = 0; kh < 3; ++kh)
+                        for (int kw = 0; kw < 3; ++kw) {
+                            int hh = h + kh - 1, ww = w + kw - 1;
+                            if (hh < 0 || hh >= H || ww < 0 || ww >= W) continue;
+                            s += Wt[((int64_t)(co * cin + ci) * 3 + kh) * 3 + kw] *
+                                 x[((int64_t)ci * H + hh) * W + ww];
+                        }
+                y[((int64_t)co * H + h) * W + w] = s;
+            }
+}
+
+/* gradients of conv3: given dy, accumulate dW, db and (if dx) write dx */
+static void conv3_back(const double *x, int cin, int H, int W, const double *Wt, int cout,
+                       const double *dy, double *dW, double *db, double *dx)
+{
+    if (dx)
+        for (int64_t i = 0; i < (int64_t)cin * H * W; ++i) dx[i] = 0.0;
+    for (int co = 0; co < cout; ++co)
+        for (int h = 0; h < H; ++h)
+            for (int w = 0; w < W; ++w) {
+                double g = dy[((int64_t)co * H + h) * W + w];
+                db[co] += g;
+                for (int ci = 0; ci < cin; ++ci)
+                    for (int kh = 0; kh < 3; ++kh)
+                        for (int kw = 0; kw < 3; ++kw) {
+                            int hh = h + kh - 1, ww = w + kw - 1;
+                            if (hh < 0 || hh >= H || ww < 0 || ww >= W) continue;
+                            int64_t wi = ((int64_t)(co * cin + ci) * 3 + kh) * 3 + kw;
+                            int64_t xi = ((int64_t)ci * H + hh) * W + ww;
+                            dW[wi] += g * x[xi];
+                            if (dx) dx[xi] += g * Wt[wi];
+                        }
+            }
+}
+
+static void relu(double *a, int64_t n)
+{
+    for (int64_t i = 0; i < n; ++i)
+        if (a[i] < 0.0) a[i] = 0.0;
+}
+
+static void relu_mask(const double *y, double *d, int64_t n)
+{
+    for (int64_t i = 0; i < n; ++i)
+        if (!(y[i] > 0.0)) d[i] = 0.0;
+}
+
+static void pool2(const double *x, int C, int H, int W, double *y)
+{
+    int H2 = H / 2, W2 = W / 2;
+    for (int c = 0; c < C; ++c)
+        for (int h = 0; h < H2; ++h)
+            for (int w = 0; w < W2; ++w) {
+                const double *p = x + ((int64_t)c * H + 2 * h) * W + 2 * w;
+                y[((int64_t)c * H2 + h) * W2 + w] = 0.25 * (p[0] + p[1] + p[W] + p[W + 1]);
+            }
+}
+
+static void pool2_back(const double *dy, int C, int H, int W, double *dx_acc)
+{
+    int H2 = H / 2, W2 = W / 2;
+    for (int c = 0; c < C; ++c)
+        for (int h = 0; h < H; ++h)
+            for (int w = 0; w < W; ++w)
+                dx_acc[((int64_t)c * H + h) * W + w] += 0.25 * dy[((int64_t)c * H2 + h / 2) * W2 + w / 2];
+}
+
+/* nearest up-sampling by 2 into channels [coff, coff + C) of y (Ctot channels) */
+static void up2(const double *x, int C, int H, int W, double *y, int coff)
+{
+    for (int c = 0; c < C; ++c)
+        for (int h = 0; h < 2 * H; ++h)
+            for (int w = 0; w < 2 * W; ++w)
+                y[((int64_t)(coff + c) * 2 * H + h) * 2 * W + w] = x[((int64_t)c * H + h / 2) * W + w / 2];
+}
+
+static void up2_back(const double *dy, int coff, int C, int H, int W, double *dx)
+{
+    for (int c = 0; c < C; ++c)
+        for (int h = 0; h < H; ++h)
+            for (int w = 0; w < W; ++w) {
+                const double *p = dy + ((int64_t)(coff + c) * 2 * H + 2 * h) * 2 * W + 2 * w;
+                dx[((int64_t)c * H + h) * W + w] = p[0] + p[1] + p[2 * W] + p[2 * W + 1];
+            }
+}
+
+/*
+ * Forward, and backward of the loss L = mean over pixels of (out - target)^2
+ * when target != NULL (grad receives dL/dparams, *loss the value).  One image
+ * x [H][W] (H, W multiples of 4) per call; out [H][W] may be NULL.
+ */
+void orc_cnn_run(const double *prm, double s, const double *x, int H, int W, double *out,
+                 const double *target, double *grad, double *loss)
+{
+    int64_t wo[CNN_LAYERS], bo[CNN_LAYERS], ho;
+    cnn_offsets(wo, bo, &ho);
+    const int H2 = H / 2, W2 = W / 2, H4 = H / 4, W4 = W / 4;
+    const int64_t P = (int64_t)H * W, P2 = (int64_t)H2 * W2, P4 = (int64_t)H4 * W4;
+    double *xin = malloc(sizeof(double) * P), *a1 = malloc(sizeof(double) * 32 * P),
+           *e1 = malloc(sizeof(double) * 32 * P), *p1 = malloc(sizeof(double) * 32 * P2),
+           *a3 = malloc(sizeof(double) * 64 * P2), *e2 = malloc(sizeof(double) * 64 * P2),
+           *p2 = malloc(sizeof(double) * 64 * P4), *a5 = malloc(sizeof(double) * 128 * P4),
+           *bt = malloc(sizeof(double) * 128 * P4), *c2 = malloc(sizeof(double) * 192 * P2),
+           *a7 = malloc(sizeof(double) * 64 * P2), *d2 = malloc(sizeof(double) * 64 * P2),
+           *c1 = malloc(sizeof(double) * 96 * P), *a9 = malloc(sizeof(double) * 32 * P),
+           *d1 = malloc(sizeof(double) * 32 * P), *o = malloc(sizeof(double) * P);
+    for (int64_t i = 0; i < P; ++i) xin[i] = x[i] / s;
+    conv3(xin, 1, H, W, prm + wo[0], prm + bo[0], 32, a1); relu(a1, 32 * P);
+    conv3(a1, 32, H, W, prm + wo[1], prm + bo[1], 32, e1); relu(e1, 32 * P);
+    pool2(e1, 32, H, W, p1);
+    conv3(p1, 32, H2, W2, prm + wo[2], prm + bo[2], 64, a3); relu(a3, 64 * P2);
+    conv3(a3, 64, H2, W2, prm + wo[3], prm + bo[3], 64, e2); relu(e2, 64 * P2);
+    pool2(e2, 64, H2, W2, p2);
+    conv3(p2, 64, H4, W4, prm + wo[4], prm + bo[4], 128, a5); relu(a5, 128 * P4);
+    conv3(a5, 128, H4, W4, prm + wo[5], prm + bo[5], 128, bt); relu(bt, 128 * P4);
+    up2(bt, 128, H4, W4, c2, 0);
+    memcpy(c2 + 128 * P2, e2, sizeof(double) * 64 * P2);
+    conv3(c2, 192, H2, W2, prm + wo[6], prm + bo[6], 64, a7); relu(a7, 64 * P2);
+    conv3(a7, 64, H2, W2, prm + wo[7], prm + bo[7], 64, d2); relu(d2, 64 * P2);
+    up2(d2, 64, H2, W2, c1, 0);
+    memcpy(c1 + 64 * P, e1, sizeof(double) * 32 * P);
+    conv3(c1, 96, H, W, prm + wo[8], prm + bo[8], 32, a9); relu(a9, 32 * P);
+    conv3(a9, 32, H, W, prm + wo[9], prm + bo[9], 32, d1); relu(d1, 32 * P);
+    const double *Wh = prm + ho, bh = prm[ho + 32];
+    for (int64_t i = 0; i < P; ++i) {
+        double h = bh;
+        for (int c = 0; c < 32; ++c) h += Wh[c] * d1[c * P + i];
+        o[i] = x[i] + s * h;
+    }
+    if (out) memcpy(out, o, sizeof(double) * P);
+    if (target) {
+        int64_t np = orc_cnn_num_params();
+        for (int64_t i = 0; i < np; ++i) grad[i] = 0.0;
+        double L = 0.0;
+        double *dh = malloc(sizeof(double) * P);
+        for (int64_t i = 0; i < P; ++i) {
+            double e = o[i] - target[i];
+            L += e * e;
+            dh[i] = s * 2.0 * e / (double)P;
+        }
+        *loss = L / (double)P;
+        double *dd1 = malloc(sizeof(double) * 32 * P);
+        for (int c = 0; c < 32; ++c)
+            for (int64_t i = 0; i < P; ++i) {
+                grad[ho + c] += dh[i] * d1[c * P + i];
+                dd1[c * P + i] = dh[i] * Wh[c];
+            }
+        for (int64_t i = 0; i < P; ++i) grad[ho + 32] += dh[i];
+        relu_mask(d1, dd1, 32 * P);
+        double *da9 = malloc(sizeof(double) * 32 * P), *dc1 = malloc(sizeof(double) * 96 * P);
+        conv3_back(a9, 32, H, W, prm + wo[9], 32, dd1, grad + wo[9], grad + bo[9], da9);
+        relu_mask(a9, da9, 32 * P);
+        conv3_back(c1, 96, H, W, prm + wo[8], 32, da9, grad + wo[8], grad + bo[8], dc1);
+        double *dd2 = malloc(sizeof(double) * 64 * P2);
+        up2_back(dc1, 0, 64, H2, W2, dd2);
+        relu_mask(d2, dd2, 64 * P2);
+        double *da7 = malloc(sizeof(double) * 64 * P2), *dc2 = malloc(sizeof(double) * 192 * P2);
+        conv3_back(a7, 64, H2, W2, prm + wo[7], 64, dd2, grad + wo[7], grad + bo[7], da7);
+        relu_mask(a7, da7, 64 * P2);
+        conv3_back(c2, 192, H2, W2, prm + wo[6], 64, da7, grad + wo[6], grad + bo[6], dc2);
+        double *dbt = malloc(sizeof(double) * 128 * P4);
+        up2_back(dc2, 0, 128, H4, W4, dbt);
+        relu_mask(bt, dbt, 128 * P4);
+        double *da5 = malloc(sizeof(double) * 128 * P4), *dp2 = malloc(sizeof(double) * 64 * P4);
+        conv3_back(a5, 128, H4, W4, prm + wo[5], 128, dbt, grad + wo[5], grad + bo[5], da5);
+        relu_mask(a5, da5, 128 * P4);
+        conv3_back(p2, 64, H4, W4, prm + wo[4], 128, da5, grad + wo[4], grad + bo[4], dp2);
+        double *de2 = malloc(sizeof(double) * 64 * P2);
+        memcpy(de2, dc2 + 128 * P2, sizeof(double) * 64 * P2);   /* skip path */
+        pool2_back(dp2, 64, H2, W2, de2);
+        relu_mask(e2, de2, 64 * P2);
+        double *da3 = malloc(sizeof(double) * 64 * P2), *dp1 = malloc(sizeof(double) * 32 * P2);
+        conv3_back(a3, 64, H2, W2, prm + wo[3], 64, de2, grad + wo[3], grad + bo[3], da3);
+        relu_mask(a3, da3, 64 * P2);
+        conv3_back(p1, 32, H2, W2, prm + wo[2], 64, da3, grad + wo[2], grad + bo[2], dp1);
+        double *de1 = malloc(sizeof(double) * 32 * P);
+        memcpy(de1, dc1 + 64 * P, sizeof(double) * 32 * P);      /* skip path */
+        pool2_back(dp1, 32, H, W, de1);
+        relu_mask(e1, de1, 32 * P);
+        double *da1 = malloc(sizeof(double) * 32 * P);
+        conv3_back(a1, 32, H, W, prm + wo[1], 32, de1, grad + wo[1], grad + bo[1], da1);
+        relu_mask(a1, da1, 32 * P);
+        conv3_back(xin, 1, H, W, prm + wo[0], 32, da1, grad + wo[0], grad + bo[0], NULL);
+        free(dh); free(dd1); free(da9); free(dc1); free(dd2); free(da7); free(dc2); free(dbt);
+        free(da5); free(dp2); free(de2); free(da3); free(dp1); free(de1); free(da1);
+    }
+    free(xin); free(a1); free(e1); free(p1); free(a3); free(e2); free(p2); free(a5); free(bt);
+    free(c2); free(a7); free(d2); free(c1); free(a9); free(d1); free(o);
+}
