@@ -316,6 +316,40 @@ int64_t dect_kernel_launches(void);
  */
 dect_status dect_selftest_bounded_wait(unsigned polls, dect_stream stream);
 
+/* ------------------------------------------------------------------------ */
+/* CNN warm start (not part of the paper's method: the learned part of the   */
+/* workload).  A 3-level encoder-decoder (32/64/128 channels, 3x3            */
+/* convolutions + ReLU, 2x2 average pooling, nearest up-sampling, skip       */
+/* concatenation, 1x1 head) maps a short ADM reconstruction x to             */
+/* x + s * net(x / s), an estimate of the converged image from which ADM     */
+/* continues.  BF16 activations and weights on the tensor cores, FP32        */
+/* accumulation, FP32 master weights, gradients and Adam state.  Parameter   */
+/* vector (host FP32): per layer W[Cout][Cin][3][3] then b[Cout], layers     */
+/* (Cin, Cout) = (1,32) (32,32) (32,64) (64,64) (64,128) (128,128) (192,64)  */
+/* (64,64) (96,32) (32,32); then the head Wh[32] and bh.                     */
+/* Images: FP32 [batch][h][w] device arrays, h and w multiples of 4,         */
+/* batch * h * w <= the max_pixels given at creation.                        */
+/* ------------------------------------------------------------------------ */
+typedef struct dect_cnn dect_cnn;
+
+int64_t dect_cnn_num_params(void);
+dect_status dect_cnn_create(int device, int max_pixels, dect_cnn **out);
+dect_status dect_cnn_destroy(dect_cnn *net);
+/* Copy the parameter vector in (host FP32); resets the Adam state. */
+dect_status dect_cnn_set_params(dect_cnn *net, const float *params);
+dect_status dect_cnn_get_params(const dect_cnn *net, float *params);
+/* out = x + s * net(x / s). */
+dect_status dect_cnn_forward(dect_cnn *net, const float *x, float *out, int batch, int h, int w,
+                             float scale, dect_stream stream);
+/* Loss L = mean over all pixels of (out - target)^2 and its gradient with
+ * respect to the parameters (kept on the device for dect_cnn_adam_step;
+ * copied to grad if grad != NULL, host FP32).  Synchronises `stream`. */
+dect_status dect_cnn_loss_grad(dect_cnn *net, const float *x, const float *target, int batch, int h,
+                               int w, float scale, float *loss, float *grad, dect_stream stream);
+/* One Adam step on the last gradient. */
+dect_status dect_cnn_adam_step(dect_cnn *net, float lr, float beta1, float beta2, float eps,
+                               dect_stream stream);
+
 /* Text of a status code (static storage). */
 const char *dect_status_string(dect_status s);
 

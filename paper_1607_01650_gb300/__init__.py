@@ -86,6 +86,15 @@ _SIGS = {
     "dect_adm_tv_groups": (C.c_int, [C.POINTER(_AdmGroup), C.c_int, C.POINTER(_AdmParams), C.c_int, _P]),
     "dect_pls_decompose_noalloc": (C.c_int, [_P, C.c_int, C.c_int, C.POINTER(_PlsParams), _P, _P, _P]),
     "dect_kernel_launches": (C.c_int64, []),
+    "dect_cnn_num_params": (C.c_int64, []),
+    "dect_cnn_create": (C.c_int, [C.c_int, C.c_int, C.POINTER(_P)]),
+    "dect_cnn_destroy": (C.c_int, [_P]),
+    "dect_cnn_set_params": (C.c_int, [_P, _P]),
+    "dect_cnn_get_params": (C.c_int, [_P, _P]),
+    "dect_cnn_forward": (C.c_int, [_P, _P, _P, C.c_int, C.c_int, C.c_int, C.c_float, _P]),
+    "dect_cnn_loss_grad": (C.c_int, [_P, _P, _P, C.c_int, C.c_int, C.c_int, C.c_float,
+                                     C.POINTER(C.c_float), _P, _P]),
+    "dect_cnn_adam_step": (C.c_int, [_P, C.c_float, C.c_float, C.c_float, C.c_float, _P]),
     "dect_selftest_bounded_wait": (C.c_int, [C.c_uint, _P]),
     "dect_plan_get_tuning": (C.c_int, [_P, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_float)]),
     "dect_plan_set_tuning": (C.c_int, [_P, C.c_int, C.c_int]),
@@ -425,3 +434,68 @@ def pls_decompose_noalloc(x, params: PlsParams, u, stream=None):
                                              C.cast(rep, C.c_void_p), _stream(stream)),
            "dect_pls_decompose_noalloc")
     return u, [(tuple(r.iters), tuple(r.relres)) for r in rep[:batch]]
+
+
+class Cnn:
+    """CNN warm start (see dect_cnn_* in include/dect.h): x -> x + s * net(x / s)."""
+
+    def __init__(self, device: int = 0, max_pixels: int = 1 << 20):
+        import torch
+        self.device = device
+        h = C.c_void_p()
+        with torch.cuda.device(device):
+            _check(load().dect_cnn_create(device, max_pixels, C.byref(h)), "dect_cnn_create")
+        self._h = h
+        self.num_params = int(load().dect_cnn_num_params())
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().dect_cnn_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_params(self, params):
+        import numpy as np
+        p = np.ascontiguousarray(params, dtype=np.float32)
+        if p.size != self.num_params:
+            raise DectError("expected %d parameters" % self.num_params)
+        _check(load().dect_cnn_set_params(self._h, p.ctypes.data), "dect_cnn_set_params")
+
+    def get_params(self):
+        import numpy as np
+        p = np.zeros(self.num_params, np.float32)
+        _check(load().dect_cnn_get_params(self._h, p.ctypes.data), "dect_cnn_get_params")
+        return p
+
+    def forward(self, x, scale: float, out=None, stream=None):
+        """x: [B, H, W] float32 CUDA (H, W multiples of 4)."""
+        import torch
+        B, H, W = x.shape
+        if out is None:
+            out = torch.empty_like(x)
+        _check(load().dect_cnn_forward(self._h, _ptr(x, torch.float32, self.device),
+                                       _ptr(out, torch.float32, self.device), B, H, W, scale,
+                                       _stream(stream)), "dect_cnn_forward")
+        return out
+
+    def loss_grad(self, x, target, scale: float, want_grad: bool = False, stream=None):
+        import numpy as np
+        import torch
+        B, H, W = x.shape
+        loss = C.c_float(0.0)
+        g = np.zeros(self.num_params, np.float32) if want_grad else None
+        _check(load().dect_cnn_loss_grad(self._h, _ptr(x, torch.float32, self.device),
+                                         _ptr(target, torch.float32, self.device), B, H, W, scale,
+                                         C.byref(loss), g.ctypes.data if want_grad else None,
+                                         _stream(stream)), "dect_cnn_loss_grad")
+        return (float(loss.value), g) if want_grad else float(loss.value)
+
+    def adam_step(self, lr: float, beta1: float = 0.9, beta2: float = 0.999, eps: float = 1e-8,
+                  stream=None):
+        _check(load().dect_cnn_adam_step(self._h, lr, beta1, beta2, eps, _stream(stream)),
+               "dect_cnn_adam_step")
