@@ -52,9 +52,12 @@ def parse():
     ap.add_argument("--max-iter", type=int, default=2000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--workload", default="paper", choices=["paper", "batched"],
+    ap.add_argument("--train-slices", type=int, default=1024, help="learned workload: training slices")
+    ap.add_argument("--epochs", type=int, default=6, help="learned workload: training epochs")
+    ap.add_argument("--workload", default="paper", choices=["paper", "batched", "learned"],
                     help="paper: 16 slices of 512^2/60 views per step (the headline); batched: "
-                         "64 slices of uneven size (256^2-512^2) and view count (30-180) per step")
+                         "64 slices of uneven size (256^2-512^2) and view count (30-180) per step; "
+                         "learned: CNN warm start trained on 256^2 pairs, evaluated at 512^2")
     return ap.parse_args()
 
 
@@ -245,6 +248,81 @@ def run_reference(args, rank, world):
 # GPU side
 # ---------------------------------------------------------------------------
 
+def run_learned(args, rank, world, local):
+    """CNN warm start: pairs (20 -> 300 ADM iterations) on 256^2 / 0.5 mm / 60 views /
+    368 bins head phantoms (seeds 10000 + i), the network trained by libdect's
+    kernels, then 32 held-out 512^2 slices (seeds 90000 + i, 16 per step) run to
+    the 1e-4 stop from the network's output and, for comparison, from zero."""
+    import torch
+    import oracle
+    import paper_1607_01650_gb300 as dect
+    from paper_1607_01650_gb300 import warmstart as ws
+    torch.cuda.set_device(local)
+    gt = synth.batched_geometry(256, 60)
+    plan_t = dect.Plan(gt, device=local)
+    t0 = time.perf_counter()
+    m_train = torch.tensor(make_inputs(gt, [10000 + i for i in range(args.train_slices)]), device="cuda")
+    prm = dect.AdmParams(mu=MU, rho=RHO, beta=BETA, step_rule=dect.CAUCHY)
+    pairs = ws.make_pairs(plan_t, m_train, prm)
+    torch.cuda.synchronize()
+    t_pairs = time.perf_counter() - t0
+    net = dect.Cnn(device=local, max_pixels=32 * 512 * 512)
+    net.set_params(oracle.cnn_init(0).astype(np.float32))
+    t0 = time.perf_counter()
+    losses = ws.train(net, pairs, epochs=args.epochs, batch=16, lr=1e-3)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    ge = synth.paper_geometry()
+    plan = dect.Plan(ge, device=local)
+    S = 16
+    held = [torch.tensor(make_inputs(ge, [90000 + 16 * k + i for i in range(S)]), device="cuda") for k in range(2)]
+    stop = dect.AdmParams(mu=MU, rho=RHO, beta=BETA, step_rule=dect.CAUCHY, max_iter=args.max_iter,
+                          rel_obj_tol=TOL, check_every=10)
+    pp = dect.PlsParams(**PLS)
+    res = {}
+
+    def run(warm):
+        iters, objs = [], []
+        for m in held:
+            if warm:
+                x, reps, k0 = ws.warm_started_adm(net, plan, m, stop)
+            else:
+                x, reps = dect.adm_tv(plan, m, stop)
+                k0 = 0
+            dect.pls_decompose(x, pp)
+            iters += [r.iters + k0 for r in reps]
+            objs += [r.objective for r in reps]
+        return iters, objs
+
+    for warm in (False, True):
+        for _ in range(max(1, args.warmup)):
+            run(warm)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(args.steps):
+            iters, objs = run(warm)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        res["warm" if warm else "cold"] = {"slices_per_s": 2 * S * args.steps / (ms / 1e3),
+                                            "mean_iterations": float(np.mean(iters)),
+                                            "mean_objective": float(np.mean(objs))}
+    line = {"metric": "DECT slices/s to 1e-4 rel. objective at 512^2/60 views, CNN warm start (2 energies + PLS)",
+            "value": res["warm"]["slices_per_s"], "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * 2 * S / res["warm"]["slices_per_s"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+bf16",
+            "data": "synthetic",
+            "config": {"workload": "learned warm start: train 256^2/60 views/368 bins, evaluate 512^2/60 views/736 bins",
+                       "train_slices": args.train_slices, "train_images": 2 * args.train_slices,
+                       "epochs": args.epochs, "final_train_mse": losses[-1], "first_epoch_mse": losses[0],
+                       "pairs_seconds": round(t_pairs, 2), "train_seconds": round(t_train, 2),
+                       "cold": res["cold"], "warm": res["warm"],
+                       "speedup_vs_cold": res["warm"]["slices_per_s"] / res["cold"]["slices_per_s"]}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_batched(args, rank, world, local):
     """Uneven-slice workload: 64 slices, n in {256..512} at 0.5 mm, 30-180 views,
     bins 368 + round((n - 256) / 256 * 368) x 0.6 mm; one dect_adm_tv_groups
@@ -324,6 +402,8 @@ def main():
 
     if args.workload == "batched":
         return run_batched(args, rank, world, local)
+    if args.workload == "learned":
+        return run_learned(args, rank, world, local)
     torch.cuda.set_device(local)
     dist = None
     if world > 1:
