@@ -66,6 +66,7 @@ struct AdmDev {
 struct AdmConst {
     int n;
     int64_t N, M;
+    int xi_is_rho;       // multiplier rebuilt from p (see k_tv)
     float mu, rho, xi;   // FP32 copies for the bulk kernels
     double mu_d, rho_d;  // FP64 for the step and objective
     double tol;
@@ -127,33 +128,44 @@ __global__ void __launch_bounds__(kBlock, 4) k_tv(const float *__restrict__ f_in
         const int64_t pix = t / CPB;
         const int i = (int)(pix / C.n), j = (int)(pix % C.n);
         const int64_t o = pix * NB + vl * VW;
-        Vec<VW> fc = ld_v<VW>(f_in + o), gc = ld_v<VW>(G + o), fu, fl;
+        Vec<VW> fc = ld_v<VW>(f_in + o), gc = ld_v<VW>(G + o), fu, fl, gu_, gl_;
 #pragma unroll
         for (int c = 0; c < VW; ++c) fc.v[c] = fmaf(-a.v[c], gc.v[c], fc.v[c]);
         st_v<VW>(f_out + o, fc);
         if (i > 0) {
             fu = ld_v<VW>(f_in + o - row);
-            Vec<VW> gu = ld_v<VW>(G + o - row);
+            gu_ = ld_v<VW>(G + o - row);
 #pragma unroll
-            for (int c = 0; c < VW; ++c) fu.v[c] = fmaf(-a.v[c], gu.v[c], fu.v[c]);
+            for (int c = 0; c < VW; ++c) fu.v[c] = fmaf(-a.v[c], gu_.v[c], fu.v[c]);
         } else {
             fu = fc;
+            gu_ = gc;
         }
         if (j > 0) {
             fl = ld_v<VW>(f_in + o - NB);
-            Vec<VW> gl = ld_v<VW>(G + o - NB);
+            gl_ = ld_v<VW>(G + o - NB);
 #pragma unroll
-            for (int c = 0; c < VW; ++c) fl.v[c] = fmaf(-a.v[c], gl.v[c], fl.v[c]);
+            for (int c = 0; c < VW; ++c) fl.v[c] = fmaf(-a.v[c], gl_.v[c], fl.v[c]);
         } else {
             fl = fc;
+            gl_ = gc;
         }
         Vec<VW> l0, l1, z0, z1;
         if (!final_pass) {
-            l0 = ld_v<VW>(lam + o);
-            l1 = ld_v<VW>(lam + sN + o);
-            if (k > 0) {
-                z0 = ld_v<VW>(z + o);
-                z1 = ld_v<VW>(z + sN + o);
+            if (C.xi_is_rho) {
+                // With xi = rho the multiplier step of Eq. (7) and
+                // p^{k-1} = rho(grad f^{k-1} - z^k) - lambda^{k-1} give
+                // lambda^k = xi alpha^{k-1} grad G^{k-1} - p^{k-1}: neither
+                // lambda nor z has to be stored (l0, l1 carry p^{k-1} here).
+                l0 = ld_v<VW>(p + o);
+                l1 = ld_v<VW>(p + sN + o);
+            } else {
+                l0 = ld_v<VW>(lam + o);
+                l1 = ld_v<VW>(lam + sN + o);
+                if (k > 0) {
+                    z0 = ld_v<VW>(z + o);
+                    z1 = ld_v<VW>(z + sN + o);
+                }
             }
         }
         Vec<VW> p0, p1;
@@ -163,10 +175,23 @@ __global__ void __launch_bounds__(kBlock, 4) k_tv(const float *__restrict__ f_in
             float g1 = fc.v[c] - fl.v[c];   // Eq. (2), 0 on the first column
             acc[0].v[c] += sqrtf(g0 * g0 + g1 * g1);
             if (final_pass) continue;
-            float a0 = l0.v[c], a1 = l1.v[c];
-            if (k > 0) {  // lambda^k = lambda^{k-1} - xi (grad f^k - z^k), Eq. (7)
-                a0 -= C.xi * (g0 - z0.v[c]);
-                a1 -= C.xi * (g1 - z1.v[c]);
+            float a0, a1;
+            if (C.xi_is_rho) {
+                a0 = 0.f;
+                a1 = 0.f;
+                if (k > 0) {
+                    const float dg0 = i > 0 ? gc.v[c] - gu_.v[c] : 0.f;
+                    const float dg1 = j > 0 ? gc.v[c] - gl_.v[c] : 0.f;
+                    a0 = C.xi * a.v[c] * dg0 - l0.v[c];
+                    a1 = C.xi * a.v[c] * dg1 - l1.v[c];
+                }
+            } else {
+                a0 = l0.v[c];
+                a1 = l1.v[c];
+                if (k > 0) {  // lambda^k = lambda^{k-1} - xi (grad f^k - z^k), Eq. (7)
+                    a0 -= C.xi * (g0 - z0.v[c]);
+                    a1 -= C.xi * (g1 - z1.v[c]);
+                }
             }
             float s0, s1;
             shrink2(g0 - a0 * inv_rho, g1 - a1 * inv_rho, inv_rho, s0, s1);
@@ -178,10 +203,12 @@ __global__ void __launch_bounds__(kBlock, 4) k_tv(const float *__restrict__ f_in
             p1.v[c] = C.rho * (g1 - s1) - a1;
         }
         if (!final_pass) {
-            st_v<VW>(lam + o, l0);
-            st_v<VW>(lam + sN + o, l1);
-            st_v<VW>(z + o, z0);
-            st_v<VW>(z + sN + o, z1);
+            if (!C.xi_is_rho) {
+                st_v<VW>(lam + o, l0);
+                st_v<VW>(lam + sN + o, l1);
+                st_v<VW>(z + o, z0);
+                st_v<VW>(z + sN + o, z1);
+            }
             st_v<VW>(p + o, p0);
             st_v<VW>(p + sN + o, p1);
         }
@@ -711,6 +738,7 @@ dect_status run_chunk(const dect_plan *P, const float *m, float *x, int nimg,
     C.rho = (float)prm->rho;
     double xi = prm->xi > 0 ? prm->xi : prm->rho;
     C.xi = (float)xi;
+    C.xi_is_rho = xi == prm->rho ? 1 : 0;
     C.mu_d = prm->mu;
     C.rho_d = prm->rho;
     C.tol = prm->rel_obj_tol;
