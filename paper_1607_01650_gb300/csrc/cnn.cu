@@ -83,6 +83,33 @@ __device__ __forceinline__ void mma_bf16(float (&d)[4], const unsigned (&a)[4], 
         : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
 }
 
+// Elementwise pieces move 8 channels (16 bytes) per thread; channel counts,
+// row strides and view offsets are multiples of 8.
+struct B8 {
+    float v[8];
+};
+__device__ __forceinline__ B8 ld8(const bf16 *p)
+{
+    const uint4 u = *reinterpret_cast<const uint4 *>(p);
+    const __nv_bfloat162 *h = reinterpret_cast<const __nv_bfloat162 *>(&u);
+    B8 r;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const float2 f = __bfloat1622float2(h[i]);
+        r.v[2 * i] = f.x;
+        r.v[2 * i + 1] = f.y;
+    }
+    return r;
+}
+__device__ __forceinline__ void st8(bf16 *p, const B8 &r)
+{
+    uint4 u;
+    __nv_bfloat162 *h = reinterpret_cast<__nv_bfloat162 *>(&u);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) h[i] = __floats2bfloat162_rn(r.v[2 * i], r.v[2 * i + 1]);
+    *reinterpret_cast<uint4 *>(p) = u;
+}
+
 // ---------------------------------------------------------------------------
 // 3x3 convolution, implicit GEMM: Y[p][co] = sum over (tap, ci) of
 // X[p + off(tap)][ci] * Wt[co][tap][ci] (+ bias, ReLU, mask).  Block tile 64
@@ -116,21 +143,34 @@ __global__ void __launch_bounds__(128) k_conv(ConvArgs a)
     const int m0 = blockIdx.x * BM, n0 = blockIdx.y * BN;
     const int nk = 9 * a.Cin / BK;
 
+    // each thread always loads the same two A rows: decompose their pixels once
+    int rh[2], rw[2];
+    const bf16 *rbase[2];
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+        const int c = tid + u * 128, row = c >> 2, q = c & 3;
+        const int p = m0 + row;
+        if (p < P) {
+            const int b = p / (a.H * a.W), hw = p % (a.H * a.W);
+            rh[u] = hw / a.W;
+            rw[u] = hw % a.W;
+            rbase[u] = a.X + ((int64_t)(b * a.H + rh[u]) * a.W + rw[u]) * a.ldx + q * 8;
+        } else {
+            rh[u] = -100000;  // never inside the image
+            rw[u] = 0;
+            rbase[u] = a.X;
+        }
+    }
     auto load = [&](int kc, int st) {
         const int k = kc * BK, tap = k / a.Cin, ci0 = k % a.Cin;
-        const int kh = tap / 3, kw = tap % 3;
-        for (int c = tid; c < BM * 4; c += 128) {
-            const int row = c >> 2, q = c & 3;
-            const int p = m0 + row;
-            bool ok = p < P;
-            const bf16 *src = a.X;
-            if (ok) {
-                const int b = p / (a.H * a.W), hw = p % (a.H * a.W), h = hw / a.W, w = hw % a.W;
-                const int hh = h + kh - 1, ww = w + kw - 1;
-                ok = hh >= 0 && hh < a.H && ww >= 0 && ww < a.W;
-                if (ok) src = a.X + ((int64_t)(b * a.H + hh) * a.W + ww) * a.ldx + ci0 + q * 8;
-            }
-            cp16_zfill(&sA[st][row][q * 8], src, ok);
+        const int kh = tap / 3 - 1, kw = tap % 3 - 1;
+        const int64_t shift = ((int64_t)kh * a.W + kw) * a.ldx + ci0;
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            const int c = tid + u * 128, row = c >> 2, q = c & 3;
+            const int hh = rh[u] + kh, ww = rw[u] + kw;
+            const bool ok = hh >= 0 && hh < a.H && ww >= 0 && ww < a.W;
+            cp16_zfill(&sA[st][row][q * 8], ok ? rbase[u] + shift : a.X, ok);
         }
         for (int c = tid; c < BN * 4; c += 128) {
             const int row = c >> 2, q = c & 3;
@@ -316,15 +356,32 @@ __global__ void k_wgrad_reduce(const float *part, int splits, int Cout, int Cin_
     }
 }
 
-// Per-channel sums of a [P][ld] BF16 tensor over pixels: partials per block row.
+// Per-channel sums of a [P][ld] BF16 tensor over pixels: one block per range
+// of pps pixels; thread t sums channels 8 (t % (C/8)) .. +7 over the pixels
+// p0 + t / (C/8), + 256 / (C/8), ...; then a fixed-order reduction in shared
+// memory.  part[block][C].
 __global__ void k_chansum(const bf16 *Y, int ld, int C, int P, int pps, float *part)
 {
-    const int split = blockIdx.x, c = threadIdx.x;
-    if (c >= C) return;
-    const int p0 = split * pps, p1 = min(P, p0 + pps);
-    float s = 0.f;
-    for (int p = p0; p < p1; ++p) s += __bfloat162float(Y[(int64_t)p * ld + c]);
-    part[(int64_t)split * C + c] = s;
+    __shared__ float red[256][8];
+    const int C8 = C / 8, lanes = 256 / C8;  // C8 divides 256 for C in {32, 64, 128}
+    const int cg = threadIdx.x % C8, pr = threadIdx.x / C8;
+    const int p0 = blockIdx.x * pps, p1 = min(P, p0 + pps);
+    float acc[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    if (pr < lanes)
+        for (int p = p0 + pr; p < p1; p += lanes) {
+            const B8 v = ld8(Y + (int64_t)p * ld + cg * 8);
+#pragma unroll
+            for (int k = 0; k < 8; ++k) acc[k] += v.v[k];
+        }
+#pragma unroll
+    for (int k = 0; k < 8; ++k) red[threadIdx.x][k] = acc[k];
+    __syncthreads();
+    if (threadIdx.x < C) {
+        const int g = threadIdx.x / 8, k = threadIdx.x % 8;
+        float s = 0.f;
+        for (int r = 0; r < lanes; ++r) s += red[r * C8 + g][k];
+        part[(int64_t)blockIdx.x * C + threadIdx.x] = s;
+    }
 }
 
 __global__ void k_chansum_reduce(const float *part, int splits, int C, float *out)
@@ -350,29 +407,31 @@ __global__ void k_in_prep(const float *x, int P, float inv_s, bf16 *xin)
 // dst (H/2 x W/2) = 2x2 average of src (H x W), C channels
 __global__ void k_pool(const bf16 *src, int lds, bf16 *dst, int ldd, int C, int B, int H, int W)
 {
-    const int H2 = H / 2, W2 = W / 2;
-    const int64_t n = (int64_t)B * H2 * W2 * C;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        const int c = (int)(i % C);
-        const int64_t q = i / C;
-        const int b = (int)(q / (H2 * W2)), hw = (int)(q % (H2 * W2)), h = hw / W2, w = hw % W2;
+    const int H2 = H / 2, W2 = W / 2, C8 = C / 8;
+    const int n = B * H2 * W2 * C8;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const int c = (i % C8) * 8, q = i / C8;
+        const int b = q / (H2 * W2), hw = q % (H2 * W2), h = hw / W2, w = hw % W2;
         const int64_t s0 = ((int64_t)(b * H + 2 * h) * W + 2 * w) * lds + c;
-        const float v = __bfloat162float(src[s0]) + __bfloat162float(src[s0 + lds]) +
-                        __bfloat162float(src[s0 + (int64_t)W * lds]) + __bfloat162float(src[s0 + (int64_t)W * lds + lds]);
-        dst[q * ldd + c] = __float2bfloat16(0.25f * v);
+        const B8 x0 = ld8(src + s0), x1 = ld8(src + s0 + lds), x2 = ld8(src + s0 + (int64_t)W * lds),
+                 x3 = ld8(src + s0 + (int64_t)W * lds + lds);
+        B8 r;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) r.v[k] = 0.25f * (x0.v[k] + x1.v[k] + x2.v[k] + x3.v[k]);
+        st8(dst + (int64_t)q * ldd + c, r);
     }
 }
 
 // dst (2H x 2W) = nearest up-sampling of src (H x W)
 __global__ void k_up(const bf16 *src, int lds, bf16 *dst, int ldd, int C, int B, int H, int W)
 {
-    const int H2 = 2 * H, W2 = 2 * W;
-    const int64_t n = (int64_t)B * H2 * W2 * C;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        const int c = (int)(i % C);
-        const int64_t q = i / C;
-        const int b = (int)(q / (H2 * W2)), hw = (int)(q % (H2 * W2)), h = hw / W2, w = hw % W2;
-        dst[q * ldd + c] = src[((int64_t)(b * H + h / 2) * W + w / 2) * lds + c];
+    const int H2 = 2 * H, W2 = 2 * W, C8 = C / 8;
+    const int n = B * H2 * W2 * C8;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const int c = (i % C8) * 8, q = i / C8;
+        const int b = q / (H2 * W2), hw = q % (H2 * W2), h = hw / W2, w = hw % W2;
+        *reinterpret_cast<uint4 *>(dst + (int64_t)q * ldd + c) =
+            *reinterpret_cast<const uint4 *>(src + ((int64_t)(b * H + h / 2) * W + w / 2) * lds + c);
     }
 }
 
@@ -380,17 +439,17 @@ __global__ void k_up(const bf16 *src, int lds, bf16 *dst, int ldd, int C, int B,
 __global__ void k_up_back_mask(const bf16 *dy, int ldy, const bf16 *x, int ldx, bf16 *dx, int ldd, int C,
                                int B, int H, int W)
 {
-    const int64_t n = (int64_t)B * H * W * C;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        const int c = (int)(i % C);
-        const int64_t q = i / C;
-        const int b = (int)(q / (H * W)), hw = (int)(q % (H * W)), h = hw / W, w = hw % W;
-        const int W2 = 2 * W;
+    const int C8 = C / 8, n = B * H * W * C8, W2 = 2 * W;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const int c = (i % C8) * 8, q = i / C8;
+        const int b = q / (H * W), hw = q % (H * W), h = hw / W, w = hw % W;
         const int64_t s0 = ((int64_t)(b * 2 * H + 2 * h) * W2 + 2 * w) * ldy + c;
-        float v = __bfloat162float(dy[s0]) + __bfloat162float(dy[s0 + ldy]) +
-                  __bfloat162float(dy[s0 + (int64_t)W2 * ldy]) + __bfloat162float(dy[s0 + (int64_t)W2 * ldy + ldy]);
-        if (!(__bfloat162float(x[q * ldx + c]) > 0.f)) v = 0.f;
-        dx[q * ldd + c] = __float2bfloat16(v);
+        const B8 y0 = ld8(dy + s0), y1 = ld8(dy + s0 + ldy), y2 = ld8(dy + s0 + (int64_t)W2 * ldy),
+                 y3 = ld8(dy + s0 + (int64_t)W2 * ldy + ldy), xm = ld8(x + (int64_t)q * ldx + c);
+        B8 r;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) r.v[k] = xm.v[k] > 0.f ? y0.v[k] + y1.v[k] + y2.v[k] + y3.v[k] : 0.f;
+        st8(dx + (int64_t)q * ldd + c, r);
     }
 }
 
@@ -398,16 +457,16 @@ __global__ void k_up_back_mask(const bf16 *dy, int ldy, const bf16 *x, int ldx, 
 __global__ void k_pool_back_mask(const bf16 *dskip, int lds, const bf16 *dp, int ldp, const bf16 *e, int lde,
                                  bf16 *de, int ldd, int C, int B, int H, int W)
 {
-    const int64_t n = (int64_t)B * H * W * C;
-    const int H2 = H / 2, W2 = W / 2;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        const int c = (int)(i % C);
-        const int64_t q = i / C;
-        const int b = (int)(q / (H * W)), hw = (int)(q % (H * W)), h = hw / W, w = hw % W;
-        float v = __bfloat162float(dskip[q * lds + c]) +
-                  0.25f * __bfloat162float(dp[((int64_t)(b * H2 + h / 2) * W2 + w / 2) * ldp + c]);
-        if (!(__bfloat162float(e[q * lde + c]) > 0.f)) v = 0.f;
-        de[q * ldd + c] = __float2bfloat16(v);
+    const int C8 = C / 8, n = B * H * W * C8, H2 = H / 2, W2 = W / 2;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const int c = (i % C8) * 8, q = i / C8;
+        const int b = q / (H * W), hw = q % (H * W), h = hw / W, w = hw % W;
+        const B8 sk = ld8(dskip + (int64_t)q * lds + c),
+                 pp = ld8(dp + ((int64_t)(b * H2 + h / 2) * W2 + w / 2) * ldp + c), em = ld8(e + (int64_t)q * lde + c);
+        B8 r;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) r.v[k] = em.v[k] > 0.f ? sk.v[k] + 0.25f * pp.v[k] : 0.f;
+        st8(de + (int64_t)q * ldd + c, r);
     }
 }
 
@@ -569,7 +628,7 @@ dect_status wgrad(dect_cnn *n, int l, const bf16 *dY, int ldd, const bf16 *X, in
     k_wgrad_reduce<<<grid_for((int64_t)Cout * kCin[l] * 9), 256, 0, s>>>(n->wpart, splits, Cout, Cinp, kCin[l],
                                                                         n->grad + n->off_w[l]);
     const int cpps = 4096, csplits = (P + cpps - 1) / cpps;
-    k_chansum<<<csplits, 128, 0, s>>>(dY, ldd, Cout, P, cpps, n->cpart);
+    k_chansum<<<csplits, 256, 0, s>>>(dY, ldd, Cout, P, cpps, n->cpart);
     k_chansum_reduce<<<1, 128, 0, s>>>(n->cpart, csplits, Cout, n->grad + n->off_b[l]);
     count_launches(4);
     DECT_CUDA(cudaGetLastError());
@@ -592,16 +651,16 @@ dect_status forward(dect_cnn *n, const float *x, int B, int H, int W, float scal
 #define CONV(...) if ((st = conv(n, __VA_ARGS__)) != DECT_OK) return st
     CONV(n->xin, 32, 32, n->wf[0], b + n->off_b[0], n->a1, 32, 32, nullptr, 0, true, B, H, W, s);
     CONV(n->a1, 32, 32, n->wf[1], b + n->off_b[1], n->c1 + 64, 96, 32, nullptr, 0, true, B, H, W, s);  // e1
-    k_pool<<<grid_for((int64_t)P2 * 32), 256, 0, s>>>(n->c1 + 64, 96, n->p1, 32, 32, B, H, W);
+    k_pool<<<grid_for((int64_t)P2 * 4), 256, 0, s>>>(n->c1 + 64, 96, n->p1, 32, 32, B, H, W);
     CONV(n->p1, 32, 32, n->wf[2], b + n->off_b[2], n->a3, 64, 64, nullptr, 0, true, B, H2, W2, s);
     CONV(n->a3, 64, 64, n->wf[3], b + n->off_b[3], n->c2 + 128, 192, 64, nullptr, 0, true, B, H2, W2, s);  // e2
-    k_pool<<<grid_for((int64_t)P4 * 64), 256, 0, s>>>(n->c2 + 128, 192, n->p2, 64, 64, B, H2, W2);
+    k_pool<<<grid_for((int64_t)P4 * 8), 256, 0, s>>>(n->c2 + 128, 192, n->p2, 64, 64, B, H2, W2);
     CONV(n->p2, 64, 64, n->wf[4], b + n->off_b[4], n->a5, 128, 128, nullptr, 0, true, B, H4, W4, s);
     CONV(n->a5, 128, 128, n->wf[5], b + n->off_b[5], n->bt, 128, 128, nullptr, 0, true, B, H4, W4, s);
-    k_up<<<grid_for((int64_t)P2 * 128), 256, 0, s>>>(n->bt, 128, n->c2, 192, 128, B, H4, W4);
+    k_up<<<grid_for((int64_t)P2 * 16), 256, 0, s>>>(n->bt, 128, n->c2, 192, 128, B, H4, W4);
     CONV(n->c2, 192, 192, n->wf[6], b + n->off_b[6], n->a7, 64, 64, nullptr, 0, true, B, H2, W2, s);
     CONV(n->a7, 64, 64, n->wf[7], b + n->off_b[7], n->d2, 64, 64, nullptr, 0, true, B, H2, W2, s);
-    k_up<<<grid_for((int64_t)P * 64), 256, 0, s>>>(n->d2, 64, n->c1, 96, 64, B, H2, W2);
+    k_up<<<grid_for((int64_t)P * 8), 256, 0, s>>>(n->d2, 64, n->c1, 96, 64, B, H2, W2);
     CONV(n->c1, 96, 96, n->wf[8], b + n->off_b[8], n->a9, 32, 32, nullptr, 0, true, B, H, W, s);
     CONV(n->a9, 32, 32, n->wf[9], b + n->off_b[9], n->d1, 32, 32, nullptr, 0, true, B, H, W, s);
 #undef CONV
@@ -744,23 +803,23 @@ extern "C" dect_status dect_cnn_loss_grad(dect_cnn *n, const float *x, const flo
     if ((st = conv(n, n->g_full_a, 32, 32, n->wt[9], nullptr, n->g_full_b, 32, 32, n->a9, 32, false, B, H, W, s)) != DECT_OK) return st;  // da9
     if ((st = wgrad(n, 8, n->g_full_b, 32, n->c1, 96, B, H, W, s)) != DECT_OK) return st;
     if ((st = conv(n, n->g_full_b, 32, 32, n->wt[8], nullptr, n->g_c1, 96, 96, nullptr, 0, false, B, H, W, s)) != DECT_OK) return st;  // dc1
-    k_up_back_mask<<<grid_for((int64_t)P2 * 64), 256, 0, s>>>(n->g_c1, 96, n->d2, 64, n->g_half_a, 64, 64, B, H2, W2);  // dd2
+    k_up_back_mask<<<grid_for((int64_t)P2 * 8), 256, 0, s>>>(n->g_c1, 96, n->d2, 64, n->g_half_a, 64, 64, B, H2, W2);  // dd2
     if ((st = wgrad(n, 7, n->g_half_a, 64, n->a7, 64, B, H2, W2, s)) != DECT_OK) return st;
     if ((st = conv(n, n->g_half_a, 64, 64, n->wt[7], nullptr, n->g_half_b, 64, 64, n->a7, 64, false, B, H2, W2, s)) != DECT_OK) return st;  // da7
     if ((st = wgrad(n, 6, n->g_half_b, 64, n->c2, 192, B, H2, W2, s)) != DECT_OK) return st;
     if ((st = conv(n, n->g_half_b, 64, 64, n->wt[6], nullptr, n->g_c2, 192, 192, nullptr, 0, false, B, H2, W2, s)) != DECT_OK) return st;  // dc2
-    k_up_back_mask<<<grid_for((int64_t)P4 * 128), 256, 0, s>>>(n->g_c2, 192, n->bt, 128, n->g_q_a, 128, 128, B, H4, W4);  // dbt
+    k_up_back_mask<<<grid_for((int64_t)P4 * 16), 256, 0, s>>>(n->g_c2, 192, n->bt, 128, n->g_q_a, 128, 128, B, H4, W4);  // dbt
     if ((st = wgrad(n, 5, n->g_q_a, 128, n->a5, 128, B, H4, W4, s)) != DECT_OK) return st;
     if ((st = conv(n, n->g_q_a, 128, 128, n->wt[5], nullptr, n->g_q_b, 128, 128, n->a5, 128, false, B, H4, W4, s)) != DECT_OK) return st;  // da5
     if ((st = wgrad(n, 4, n->g_q_b, 128, n->p2, 64, B, H4, W4, s)) != DECT_OK) return st;
     if ((st = conv(n, n->g_q_b, 128, 128, n->wt[4], nullptr, n->g_q_a, 64, 64, nullptr, 0, false, B, H4, W4, s)) != DECT_OK) return st;  // dp2
-    k_pool_back_mask<<<grid_for((int64_t)P2 * 64), 256, 0, s>>>(n->g_c2 + 128, 192, n->g_q_a, 64, n->c2 + 128, 192,
+    k_pool_back_mask<<<grid_for((int64_t)P2 * 8), 256, 0, s>>>(n->g_c2 + 128, 192, n->g_q_a, 64, n->c2 + 128, 192,
                                                                n->g_half_a, 64, 64, B, H2, W2);  // de2
     if ((st = wgrad(n, 3, n->g_half_a, 64, n->a3, 64, B, H2, W2, s)) != DECT_OK) return st;
     if ((st = conv(n, n->g_half_a, 64, 64, n->wt[3], nullptr, n->g_half_b, 64, 64, n->a3, 64, false, B, H2, W2, s)) != DECT_OK) return st;  // da3
     if ((st = wgrad(n, 2, n->g_half_b, 64, n->p1, 32, B, H2, W2, s)) != DECT_OK) return st;
     if ((st = conv(n, n->g_half_b, 64, 64, n->wt[2], nullptr, n->g_half_a, 32, 32, nullptr, 0, false, B, H2, W2, s)) != DECT_OK) return st;  // dp1
-    k_pool_back_mask<<<grid_for((int64_t)P * 32), 256, 0, s>>>(n->g_c1 + 64, 96, n->g_half_a, 32, n->c1 + 64, 96,
+    k_pool_back_mask<<<grid_for((int64_t)P * 4), 256, 0, s>>>(n->g_c1 + 64, 96, n->g_half_a, 32, n->c1 + 64, 96,
                                                               n->g_full_a, 32, 32, B, H, W);  // de1
     if ((st = wgrad(n, 1, n->g_full_a, 32, n->a1, 32, B, H, W, s)) != DECT_OK) return st;
     if ((st = conv(n, n->g_full_a, 32, 32, n->wt[1], nullptr, n->g_full_b, 32, 32, n->a1, 32, false, B, H, W, s)) != DECT_OK) return st;  // da1
