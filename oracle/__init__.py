@@ -51,7 +51,8 @@ class _Geom(C.Structure):
 
 class _AdmParams(C.Structure):
     _fields_ = [("mu", C.c_double), ("rho", C.c_double), ("xi", C.c_double),
-                ("step_rule", C.c_int), ("max_iter", C.c_int), ("tol", C.c_double)]
+                ("step_rule", C.c_int), ("max_iter", C.c_int), ("tol", C.c_double),
+                ("nonneg", C.c_int)]
 
 
 class _AdmState(C.Structure):
@@ -252,10 +253,12 @@ class AdmParams:
     max_iter: int = 100
     tol: float = 0.0
     beta: Tuple[float, float] = (1.0, 0.6)   # (beta_1 for x_h, beta_2 for x_l), Eq. (3)
+    nonneg: bool = False                     # project f onto f >= 0 after each f-step
 
     def c(self) -> _AdmParams:
         xi = self.rho if self.xi is None else self.xi
-        return _AdmParams(self.mu, self.rho, xi, self.step_rule, self.max_iter, self.tol)
+        return _AdmParams(self.mu, self.rho, xi, self.step_rule, self.max_iter, self.tol,
+                          1 if self.nonneg else 0)
 
 
 class AdmState:

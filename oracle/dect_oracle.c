@@ -33,7 +33,8 @@
  *      the default of the callers; both rules are kept.
  *   R7 Eq. (2) differences with an index outside the image are 0.
  *      i = row (y), j = column (x).
- *   R8 no projection onto x >= 0 (Eq. (10) has none).
+ *   R8 no projection onto x >= 0 (Eq. (10) has none); optionally (nonneg = 1)
+ *      f is projected onto f >= 0 right after the f-step.
  *   R10 Siddon segments between consecutive sorted crossing parameters go to
  *      the pixel that holds the segment midpoint; zero-length ones are dropped;
  *      consecutive pieces given to the same pixel (a crossing within rounding
@@ -287,6 +288,7 @@ typedef struct {
     int step_rule;     /* 0 = BB1 (lagged exact step), 1 = CAUCHY (R6) */
     int max_iter;
     double tol;        /* stop when |Phi_{k+1} - Phi_k| / Phi_k < tol; 0 = run max_iter */
+    int nonneg;        /* 1: project f onto f >= 0 after the f-step (x in R_+^N, Eq. (1)) */
 } orc_adm_params;
 
 /* ADM state of one channel (sizes: f N, z 2N, lam 2N). */
@@ -348,8 +350,11 @@ double orc_adm_iterate(int n, int64_t m, const int64_t *rowptr, const int32_t *i
     else alpha = st->alpha_prev;
     st->alpha_prev = c;
 
-    /* f-step and multiplier step */
-    for (int64_t p = 0; p < N; ++p) st->f[p] -= alpha * G[p];
+    /* f-step (optionally projected onto f >= 0, since x >= 0 in Eq. (1)) and multiplier step */
+    for (int64_t p = 0; p < N; ++p) {
+        st->f[p] -= alpha * G[p];
+        if (prm->nonneg && st->f[p] < 0.0) st->f[p] = 0.0;
+    }
     orc_grad(n, st->f, gf);
     for (int64_t p = 0; p < 2 * N; ++p) st->lam[p] -= xi * (gf[p] - st->z[p]);
 

@@ -213,3 +213,24 @@ def test_dual_energy_wrapper_uses_beta():
     x, its = oracle.adm_dual(t, mm, prm)
     f1, _, _, _ = oracle.adm_channel(t, 0.5 * mm[1], prm)
     np.testing.assert_array_equal(x[1], f1 / 0.5)
+
+
+def test_nonnegative_variant():
+    """With the projection onto f >= 0 (x in R_+^N, Eq. (1)) every iterate is
+    nonnegative, and the limit satisfies the optimality conditions of the
+    constrained subproblem: G ~ 0 where f > 0 and G >= 0 where f = 0."""
+    g, t, A, m = _tiny_problem(seed=8, noise=0.05)
+    prm = oracle.AdmParams(mu=64.0, rho=16.0, step_rule=oracle.CAUCHY, nonneg=True)
+    st = oracle.AdmState(np.zeros((8, 8)))
+    _, G0, _ = oracle.adm_iterate(t, m, prm, st)
+    scale = np.abs(G0).max()
+    for k in range(6000):
+        _, G, _ = oracle.adm_iterate(t, m, prm, st)
+        assert st.f.min() >= 0.0
+    free = st.f > 1e-9
+    assert np.abs(G[free]).max() < 1e-4 * scale
+    assert G[~free].min() > -1e-4 * scale
+    assert (~free).sum() > 0   # the constraint is active somewhere
+    # the unconstrained run goes negative on this noisy problem
+    f_u, _, _, _ = oracle.adm_channel(t, m, oracle.AdmParams(mu=64.0, rho=16.0, max_iter=3000))
+    assert f_u.min() < -1e-3
