@@ -142,6 +142,9 @@ typedef struct {
     int check_every;    /* host checks "all channels stopped" every this many
                            iterations (>= 1; 0 = 10); only used when rel_obj_tol > 0    */
     int warm_start;     /* 0: start from x = 0; 1: start from the x passed in           */
+    int nonneg;         /* 1: project f onto f >= 0 after every f-step (x in R_+^N,
+                           Eq. (1)); costs one extra A per iteration to rebuild the
+                           residual.  0: the unconstrained steps of Eq. (7)-(10)        */
 } dect_adm_params;
 
 typedef struct {

@@ -41,7 +41,8 @@ class _PlanInfo(C.Structure):
 class _AdmParams(C.Structure):
     _fields_ = [("mu", C.c_double), ("rho", C.c_double), ("xi", C.c_double),
                 ("beta", C.c_double * 2), ("step_rule", C.c_int), ("max_iter", C.c_int),
-                ("rel_obj_tol", C.c_double), ("check_every", C.c_int), ("warm_start", C.c_int)]
+                ("rel_obj_tol", C.c_double), ("check_every", C.c_int), ("warm_start", C.c_int),
+                ("nonneg", C.c_int)]
 
 
 class _AdmReport(C.Structure):
@@ -278,11 +279,13 @@ class AdmParams:
     rel_obj_tol: float = 0.0
     check_every: int = 10
     warm_start: bool = False
+    nonneg: bool = False                # project f onto f >= 0 after each f-step
 
     def _c(self) -> _AdmParams:
         b = (C.c_double * 2)(*self.beta)
         return _AdmParams(self.mu, self.rho, self.xi, b, self.step_rule, self.max_iter,
-                          self.rel_obj_tol, self.check_every, 1 if self.warm_start else 0)
+                          self.rel_obj_tol, self.check_every, 1 if self.warm_start else 0,
+                          1 if self.nonneg else 0)
 
 
 @dataclasses.dataclass

@@ -25,6 +25,12 @@
 //   k_fwd    q = A G  (ray-major table)                  ; |grad G|^2, |q|^2,
 //            then the last block forms Phi^k, the stopping test and
 //            alpha^k in FP64.
+//
+// Optional projection onto f >= 0 (x in R_+^N, Eq. (1)): k_tv clamps each
+// updated pixel, f^{k+1} = max(f^k - alpha^k G^k, 0).  The residual is then
+// no longer r - alpha q, so a fourth kernel (k_fwd in mode 2) rebuilds
+// r = A f - g after k_tv and reduces |r|^2; and the lambda step needs the
+// stored lambda and z (the xi = rho shortcut below assumes the plain step).
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -44,7 +50,7 @@ constexpr int kGrid = kSMs * 8;  // fixed grid of every reducing kernel
 
 // reduction slots; (TV, RR) and (DD, QQ) are reduced together
 enum { R_TV = 0, R_RR = 1, R_DD = 2, R_QQ = 3, R_GG = 4, R_COUNT = 5 };
-enum { C_TV = 0, C_BWD = 1, C_FWD = 2, C_COUNT = 3 };
+enum { C_TV = 0, C_BWD = 1, C_FWD = 2, C_RES = 3, C_COUNT = 4 };
 
 struct AdmDev {
     // per-channel scalars
@@ -67,6 +73,7 @@ struct AdmConst {
     int n;
     int64_t N, M;
     int xi_is_rho;       // multiplier rebuilt from p (see k_tv)
+    int nonneg;          // f-step projected onto f >= 0
     float mu, rho, xi;   // FP32 copies for the bulk kernels
     double mu_d, rho_d;  // FP64 for the step and objective
     double tol;
@@ -95,6 +102,14 @@ __device__ __forceinline__ void shrink2(float w0, float w1, float t, float &z0, 
     }
 }
 
+// f - a g, projected onto [0, inf) when `clamp` (a NaN stays a NaN, so the
+// non-finite-objective check still sees it).
+__device__ __forceinline__ float nonneg_step(float f, float a, float g, bool clamp)
+{
+    const float v = fmaf(-a, g, f);
+    return clamp && v < 0.f ? 0.f : v;
+}
+
 // ---------------------------------------------------------------------------
 // Start of iteration k: apply the previous step (f^k = f^{k-1} - alpha G,
 // r^k = r^{k-1} - alpha q; alpha = 0 at k = 0), then the lambda step of the
@@ -102,6 +117,9 @@ __device__ __forceinline__ void shrink2(float w0, float w1, float t, float &z0, 
 // Reduces |grad f^k|_TV and |r^k|^2.  f is double-buffered (f_in -> f_out)
 // because the stencil reads neighbours of the updated image.
 // final_pass: only the f / r step and the two norms (the result's objective).
+// With C.nonneg the updated pixels are clamped at 0 (from k = 1 on: at k = 0
+// the step is empty and f^0 is used as given), and r and |r|^2 are left to
+// k_fwd in mode 2.
 // ---------------------------------------------------------------------------
 template <int NB>
 __global__ void __launch_bounds__(kBlock, 4) k_tv(const float *__restrict__ f_in, float *__restrict__ f_out,
@@ -114,6 +132,7 @@ __global__ void __launch_bounds__(kBlock, 4) k_tv(const float *__restrict__ f_in
     __shared__ double smem[reduce_smem_doubles<NB>(2)];
     const int k = *D.k;
     const float inv_rho = 1.0f / C.rho;
+    const bool clamp = C.nonneg && k > 0;
     const int vl = threadIdx.x % CPB;
     Vec<VW> a;
 #pragma unroll
@@ -130,13 +149,13 @@ __global__ void __launch_bounds__(kBlock, 4) k_tv(const float *__restrict__ f_in
         const int64_t o = pix * NB + vl * VW;
         Vec<VW> fc = ld_v<VW>(f_in + o), gc = ld_v<VW>(G + o), fu, fl, gu_, gl_;
 #pragma unroll
-        for (int c = 0; c < VW; ++c) fc.v[c] = fmaf(-a.v[c], gc.v[c], fc.v[c]);
+        for (int c = 0; c < VW; ++c) fc.v[c] = nonneg_step(fc.v[c], a.v[c], gc.v[c], clamp);
         st_v<VW>(f_out + o, fc);
         if (i > 0) {
             fu = ld_v<VW>(f_in + o - row);
             gu_ = ld_v<VW>(G + o - row);
 #pragma unroll
-            for (int c = 0; c < VW; ++c) fu.v[c] = fmaf(-a.v[c], gu_.v[c], fu.v[c]);
+            for (int c = 0; c < VW; ++c) fu.v[c] = nonneg_step(fu.v[c], a.v[c], gu_.v[c], clamp);
         } else {
             fu = fc;
             gu_ = gc;
@@ -145,7 +164,7 @@ __global__ void __launch_bounds__(kBlock, 4) k_tv(const float *__restrict__ f_in
             fl = ld_v<VW>(f_in + o - NB);
             gl_ = ld_v<VW>(G + o - NB);
 #pragma unroll
-            for (int c = 0; c < VW; ++c) fl.v[c] = fmaf(-a.v[c], gl_.v[c], fl.v[c]);
+            for (int c = 0; c < VW; ++c) fl.v[c] = nonneg_step(fl.v[c], a.v[c], gl_.v[c], clamp);
         } else {
             fl = fc;
             gl_ = gc;
@@ -213,7 +232,8 @@ __global__ void __launch_bounds__(kBlock, 4) k_tv(const float *__restrict__ f_in
             st_v<VW>(p + sN + o, p1);
         }
     }
-    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < C.M * CPB; t += stride) {
+    const int64_t rn = C.nonneg ? 0 : C.M * CPB;  // with the projection r is rebuilt by k_fwd
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < rn; t += stride) {
         float *rp = r + t * VW;
         Vec<VW> rv = ld_v<VW>(rp), qv = ld_v<VW>(q + t * VW);
 #pragma unroll
@@ -485,7 +505,9 @@ __device__ void adm_finish(const AdmConst &C, const AdmDev &D)
 }
 
 // MODE 1: |grad G|^2, then q = A G over the ray-major table and |q|^2; the
-// last block forms the step.  MODE 0: r = A f - beta m (set-up).
+// last block forms the step.  MODE 0: r = A f - beta m (set-up).  MODE 2:
+// r = A f - beta m and |r|^2 into the RR slot (residual of the projected
+// f-step, run after k_tv).
 template <int NB, int G_, int MODE>
 __global__ void __launch_bounds__(kBlock) k_fwd(const int64_t *__restrict__ rowptr,
                                                 const Entry *__restrict__ ent,
@@ -526,12 +548,13 @@ __global__ void __launch_bounds__(kBlock) k_fwd(const int64_t *__restrict__ rowp
         }
         Vec<VW> acc = row_dot<NB, G_, true>(ent, b, e, src, 0, lr);
         if (ray < C.M && grp == 0) {
-            if (MODE == 0) {
+            if (MODE != 1) {
 #pragma unroll
                 for (int c = 0; c < VW; ++c) {
                     const int img = vl * VW + c;
                     float g = img < C.nimg ? beta_img[img] * m_planar[(int64_t)img * C.M + ray] : 0.f;
                     acc.v[c] -= g;
+                    if (MODE == 2) nrm[0].v[c] = fmaf(acc.v[c], acc.v[c], nrm[0].v[c]);
                 }
             } else {
 #pragma unroll
@@ -543,6 +566,9 @@ __global__ void __launch_bounds__(kBlock) k_fwd(const int64_t *__restrict__ rowp
     if (MODE == 1) {
         if (reduce_images<NB, 2>(nrm, part_of<NB>(D, C_FWD), D.red + R_DD * NB, D.ctr + C_FWD, smem))
             adm_finish<NB>(C, D);
+    } else if (MODE == 2) {
+        Vec<VW> rr[1] = {nrm[0]};
+        reduce_images<NB, 1>(rr, part_of<NB>(D, C_RES), D.red + R_RR * NB, D.ctr + C_RES, smem);
     }
 }
 
@@ -580,6 +606,7 @@ struct Kern {
 
 struct Work {
     float *f[2], *G, *lam, *z, *p, *r, *q, *beta;
+    const float *m;  // measured sinograms, planar [nimg][M]
     double *dbl;
     int *ints;
     unsigned *ctr;
@@ -713,6 +740,9 @@ void enqueue_iteration(const dect_plan *P, const Work &W, const AdmConst &C, int
                        const IterEvents *ev)
 {
     k_tv<NB><<<kGrid, kBlock, 0, s>>>(W.f[par], W.f[1 - par], W.G, W.lam, W.z, W.p, W.r, W.q, C, W.D, 0);
+    if (C.nonneg)
+        k_fwd<NB, Kern<NB>::GF, 2><<<kGrid, kBlock, 0, s>>>(P->rowptr, P->ent, W.f[1 - par], W.r, W.m,
+                                                             W.beta, C, W.D);
     if (ev) cudaEventRecordWithFlags(ev->b0, s, cudaEventRecordExternal);
     launch_bwd<NB>(P, W, C, W.bwd, s);
     if (ev) cudaEventRecordWithFlags(ev->b1, s, cudaEventRecordExternal);
@@ -722,7 +752,7 @@ void enqueue_iteration(const dect_plan *P, const Work &W, const AdmConst &C, int
     if (ev) cudaEventRecordWithFlags(ev->f1, s, cudaEventRecordExternal);
 }
 
-constexpr int kKernelsPerIteration = 3;
+int kernels_per_iteration(const AdmConst &C) { return C.nonneg ? 4 : 3; }
 
 template <int NB>
 dect_status run_chunk(const dect_plan *P, const float *m, float *x, int nimg,
@@ -738,7 +768,8 @@ dect_status run_chunk(const dect_plan *P, const float *m, float *x, int nimg,
     C.rho = (float)prm->rho;
     double xi = prm->xi > 0 ? prm->xi : prm->rho;
     C.xi = (float)xi;
-    C.xi_is_rho = xi == prm->rho ? 1 : 0;
+    C.nonneg = prm->nonneg ? 1 : 0;
+    C.xi_is_rho = (xi == prm->rho && !C.nonneg) ? 1 : 0;
     C.mu_d = prm->mu;
     C.rho_d = prm->rho;
     C.tol = prm->rel_obj_tol;
@@ -771,6 +802,7 @@ dect_status run_chunk(const dect_plan *P, const float *m, float *x, int nimg,
     char *base = nullptr;
     DECT_CUDA(cudaMallocAsync((void **)&base, bytes, s));
     layout(base);
+    W.m = m;
     DECT_CUDA(setup_window<NB>(P, W));
 
     AdmDev &D = W.D;
@@ -883,7 +915,7 @@ dect_status run_chunk(const dect_plan *P, const float *m, float *x, int nimg,
     int done_iters = 0;
     while (err == cudaSuccess && done_iters + block <= K) {
         err = cudaGraphLaunch(gx_block, cs);
-        count_launches((int64_t)kKernelsPerIteration * block);
+        count_launches((int64_t)kernels_per_iteration(C) * block);
         done_iters += block;
         if (err == cudaSuccess) err = collect(block, 0);
         if (err == cudaSuccess && use_tol) {
@@ -896,7 +928,7 @@ dect_status run_chunk(const dect_plan *P, const float *m, float *x, int nimg,
     while (err == cudaSuccess && !finished && done_iters < K) {
         const int par = done_iters & 1;
         err = cudaGraphLaunch(gx_one[par], cs);
-        count_launches(kKernelsPerIteration);
+        count_launches(kernels_per_iteration(C));
         ++done_iters;
         if (err == cudaSuccess) err = collect(1, block + par);
     }
@@ -904,9 +936,12 @@ dect_status run_chunk(const dect_plan *P, const float *m, float *x, int nimg,
     const int par = done_iters & 1;
     if (err == cudaSuccess) {
         k_tv<NB><<<kGrid, kBlock, 0, cs>>>(W.f[par], W.f[1 - par], W.G, W.lam, W.z, W.p, W.r, W.q, C, D, 1);
+        if (C.nonneg)
+            k_fwd<NB, Kern<NB>::GF, 2><<<kGrid, kBlock, 0, cs>>>(P->rowptr, P->ent, W.f[1 - par], W.r, m,
+                                                                  W.beta, C, D);
         k_unpack<NB><<<(unsigned)((tn + 255) / 256), 256, 0, cs>>>(W.f[1 - par], x, N, nimg, W.beta);
         err = cudaGetLastError();
-        count_launches(2);
+        count_launches(C.nonneg ? 3 : 2);
     }
     if (err == cudaSuccess) err = cudaEventRecord(ev, cs);
     if (err == cudaSuccess) err = cudaStreamWaitEvent(s, ev, 0);
@@ -966,7 +1001,8 @@ extern "C" dect_status dect_adm_tv_ex(const dect_plan *plan, const float *m, flo
     if (!(prm->mu > 0) || !(prm->rho > 0) || !(prm->beta[0] > 0) || !(prm->beta[1] > 0) ||
         prm->max_iter < 0 || (prm->step_rule != DECT_STEP_BB1 && prm->step_rule != DECT_STEP_CAUCHY) ||
         !std::isfinite(prm->mu) || !std::isfinite(prm->rho) || !std::isfinite(prm->xi) ||
-        !std::isfinite(prm->beta[0]) || !std::isfinite(prm->beta[1]) || prm->check_every < 0)
+        !std::isfinite(prm->beta[0]) || !std::isfinite(prm->beta[1]) || prm->check_every < 0 ||
+        (prm->nonneg != 0 && prm->nonneg != 1))
         return DECT_ERR_INVALID_ARG;
     DECT_CUDA(cudaSetDevice(plan->device));
     cudaStream_t s = (cudaStream_t)stream;

@@ -75,3 +75,32 @@ def test_host_side_argument_checks(lib):
     assert L.dect_plan_create(C.byref(bad), 0, None, C.byref(out)) == 1
     assert L.dect_plan_destroy(None) == 0
     assert L.dect_plan_get_tuning(None, 2, None, None) == 1
+
+
+def test_struct_layouts_match_the_header(tmp_path):
+    """Every ctypes structure of the binding has the field offsets and size
+    that a C compiler gives the struct of the same name in include/dect.h."""
+    if shutil.which("gcc") is None:
+        pytest.skip("no C compiler")
+    import paper_1607_01650_gb300 as dect
+    pairs = {"dect_geometry": dect._Geometry, "dect_plan_info": dect._PlanInfo,
+             "dect_adm_params": dect._AdmParams, "dect_adm_report": dect._AdmReport,
+             "dect_adm_profile": dect._AdmProfile, "dect_adm_group": dect._AdmGroup,
+             "dect_pls_params": dect._PlsParams, "dect_pls_report": dect._PlsReport}
+    lines = ["#include <stdio.h>", '#include "dect.h"', "int main(void) {"]
+    for cname, py in pairs.items():
+        lines.append(f'printf("{cname} sizeof %zu\\n", sizeof({cname}));')
+        for fname, _ in py._fields_:
+            lines.append(f'printf("{cname} {fname} %zu\\n", offsetof({cname}, {fname}));')
+    lines += ["return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)],
+                   check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    got = {tuple(l.split()[:2]): int(l.split()[2]) for l in out if l.strip()}
+    for cname, py in pairs.items():
+        assert got[(cname, "sizeof")] == C.sizeof(py), cname
+        for fname, _ in py._fields_:
+            assert got[(cname, fname)] == getattr(py, fname).offset, (cname, fname)

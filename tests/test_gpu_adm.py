@@ -21,19 +21,20 @@ def rel_l2(a, b):
     return float(np.linalg.norm(np.asarray(a, np.float64) - b) / np.linalg.norm(b))
 
 
-def run_both(g, slices, K, rule=dect.CAUCHY, beta=(1.0, 0.6), xi=0.0, tol=0.0, x0=None):
+def run_both(g, slices, K, rule=dect.CAUCHY, beta=(1.0, 0.6), xi=0.0, tol=0.0, x0=None,
+             nonneg=False):
     plan = dect.Plan(g)
     t = oracle.table(g)
     m = np.stack([s.m for s in slices])
     prm = dect.AdmParams(mu=MU, rho=RHO, xi=xi, beta=beta, step_rule=rule, max_iter=K,
-                         rel_obj_tol=tol, warm_start=x0 is not None)
+                         rel_obj_tol=tol, warm_start=x0 is not None, nonneg=nonneg)
     xin = None if x0 is None else torch.tensor(x0, dtype=torch.float32, device="cuda")
     x, reps = dect.adm_tv(plan, torch.tensor(m, dtype=torch.float32, device="cuda"), prm, x=xin)
     x = x.cpu().numpy()
     outs = []
     for i, s in enumerate(slices):
         op = oracle.AdmParams(mu=MU, rho=RHO, xi=(xi if xi > 0 else None), beta=beta,
-                              step_rule=rule, max_iter=K, tol=tol)
+                              step_rule=rule, max_iter=K, tol=tol, nonneg=nonneg)
         # the oracle reads the same FP32 data the GPU reads
         xo, its = oracle.adm_dual(t, m[i].astype(np.float32).astype(np.float64), op,
                                   x0=None if x0 is None else x0[i].astype(np.float32).astype(np.float64))
@@ -80,6 +81,49 @@ def test_warm_start():
     x, reps, outs, t = run_both(g, [sl], 15, x0=x0)
     for e in range(2):
         assert rel_l2(x[0, e], outs[0][0][e]) <= 1e-4
+
+
+@pytest.mark.parametrize("ns", [1, 5])
+def test_nonnegative_projection(ns):
+    """f-step projected onto f >= 0 (x in R_+^N, Eq. (1)): parity with the
+    oracle's projected iteration, a nonnegative result, and the objective
+    reported at it.  Low-dose data makes the unconstrained result negative,
+    so the projection is active."""
+    g = synth.tiny_geometry(n=48, nv=24, nb=72, px=1.0, sod=120.0, sdd=240.0)
+    slices = [synth.make_slice(g, seed=40 + i, i0=2e2) for i in range(ns)]
+    x, reps, outs, t = run_both(g, slices, 40, nonneg=True)
+    xu, _, _, _ = run_both(g, slices[:1], 40)
+    assert xu.min() < 0.0
+    assert x.min() >= 0.0
+    for i in range(ns):
+        for e in range(2):
+            xo = outs[i][0][e]
+            assert xo.min() >= 0.0
+            assert rel_l2(x[i, e], xo) <= 1e-4
+    b = (1.0, 0.6)
+    for e in range(2):
+        phi = oracle.objective(t, b[e] * slices[0].m[e].astype(np.float32), MU,
+                               b[e] * x[0, e].astype(np.float64))
+        assert abs(reps[e].objective - phi) <= 1e-4 * phi
+
+
+def test_nonnegative_projection_warm_start_negative():
+    """A warm start with negative pixels is used as given by the first step
+    (the projection applies to the updated f only), in both implementations."""
+    g = synth.tiny_geometry(n=40, nv=20, nb=64, px=1.0, sod=120.0, sdd=240.0)
+    sl = synth.make_slice(g, seed=11, i0=1e5)
+    rng = np.random.default_rng(3)
+    x0 = (np.stack([sl.truth()[1]]) + rng.normal(0.0, 0.02, size=(1, 2, 40, 40))).astype(np.float32)
+    assert x0.min() < 0.0
+    x, reps, outs, t = run_both(g, [sl], 10, x0=x0, nonneg=True)
+    assert x.min() >= 0.0
+    for e in range(2):
+        assert rel_l2(x[0, e], outs[0][0][e]) <= 1e-4
+    # with no iterations the result is the warm start, negative pixels included
+    # (up to the FP32 rounding of x -> beta x -> x)
+    x1, _, _, _ = run_both(g, [sl], 0, x0=x0, nonneg=True)
+    np.testing.assert_allclose(x1, x0, rtol=1e-6, atol=0.0)
+    assert x1.min() < 0.0
 
 
 def test_relative_objective_stop():
