@@ -88,6 +88,13 @@ def _load():
             "orc_objective": (C.c_double, [C.c_int, C.c_int64, i64, i32, d, d, C.c_double, d]),
             "orc_adm_run": (C.c_int, [C.c_int, C.c_int64, i64, i32, d, d,
                                       C.POINTER(_AdmParams), d, d, d]),
+            "orc_shrink4": (None, [C.c_int64, d, d, C.c_double, d, d]),
+            "orc_tv_joint": (C.c_double, [C.c_int, d]),
+            "orc_objective_joint": (C.c_double, [C.c_int, C.c_int64, i64, i32, d, d, C.c_double, d]),
+            "orc_adm_joint_iterate": (C.c_double, [C.c_int, C.c_int64, i64, i32, d, d,
+                                                   C.POINTER(_AdmParams), C.POINTER(_AdmState), d, d]),
+            "orc_adm_joint_run": (C.c_int, [C.c_int, C.c_int64, i64, i32, d, d,
+                                            C.POINTER(_AdmParams), d, d, d]),
             "orc_direct_decompose": (None, [C.c_int64, d, d, d, d, d]),
             "orc_prewitt": (None, [C.c_int, d, d]),
             "orc_edge_mask": (None, [C.c_int, d, d, C.c_double, u8]),
@@ -254,6 +261,7 @@ class AdmParams:
     tol: float = 0.0
     beta: Tuple[float, float] = (1.0, 0.6)   # (beta_1 for x_h, beta_2 for x_l), Eq. (3)
     nonneg: bool = False                     # project f onto f >= 0 after each f-step
+    joint: bool = False                      # adm_dual: TV coupled over both channels
 
     def c(self) -> _AdmParams:
         xi = self.rho if self.xi is None else self.xi
@@ -318,6 +326,12 @@ def adm_dual(t: Table, m_he, prm: AdmParams, x0=None):
     against g_c = beta_c m_c; returns x[2][n][n] = f_c / beta_c and the
     per-channel iteration counts.
     """
+    if prm.joint:
+        b = np.array(prm.beta, np.float64).reshape(2, 1, 1)
+        f0 = None if x0 is None else b * _f64(x0)
+        g = b * _f64(m_he).reshape(2, t.geom.nv, t.geom.nb)
+        f, k, _, _ = adm_joint(t, g, prm, f0)
+        return f / b, [k, k]
     xs, its = [], []
     for c in range(2):
         b = prm.beta[c]
@@ -326,6 +340,75 @@ def adm_dual(t: Table, m_he, prm: AdmParams, x0=None):
         xs.append(f / b)
         its.append(k)
     return np.stack(xs), its
+
+
+# ---------------------------------------------------------------------------
+# Joint TV: Eq. (4) with the TV norm taken over both channels per pixel
+# ---------------------------------------------------------------------------
+
+def shrink4(wh, wl, t: float):
+    """Prox of the per-pixel 4-norm: z = max(|w| - t, 0) w / |w| on
+    w = (wh[0], wh[1], wl[0], wl[1]).  Returns (zh, zl), each [2][...]."""
+    wh, wl = _f64(wh), _f64(wl)
+    zh, zl = np.zeros_like(wh), np.zeros_like(wl)
+    _load().orc_shrink4(wh[0].size, _d(wh), _d(wl), t, _d(zh), _d(zl))
+    return zh, zl
+
+
+def tv_joint(f) -> float:
+    """sum_p |(grad f_h, grad f_l)_p|_2 for f = [2][n][n]."""
+    f = _f64(f)
+    return float(_load().orc_tv_joint(f.shape[-1], _d(f)))
+
+
+def objective_joint(t: Table, g, mu: float, f) -> float:
+    """Joint objective: tv_joint(f) + mu/2 sum_c |A f_c - g_c|^2; g = [2][M]."""
+    g = _f64(g).reshape(-1)
+    f = _f64(f)
+    m, rp, ix, ln = t._args()
+    return float(_load().orc_objective_joint(t.geom.n, m, rp, ix, ln, _d(g), mu, _d(f)))
+
+
+class AdmJointState:
+    """State of the joint ADM: f [2][n][n], z and lambda [2][2][n][n]."""
+
+    def __init__(self, f0):
+        f0 = _f64(f0)
+        n = f0.shape[-1]
+        self.f = f0.copy()
+        self.z = np.zeros((2, 2, n, n))
+        self.lam = np.zeros((2, 2, n, n))
+        self.alpha_prev = -1.0
+
+
+def adm_joint_iterate(t: Table, g, prm: AdmParams, st: AdmJointState):
+    """One joint iteration of Eq. (10).  g = [2][M].
+    Returns (alpha, G [2][n][n], (|G|^2, |AG|^2, |grad G|^2) over both channels)."""
+    g = _f64(g).reshape(-1)
+    n = t.geom.n
+    cst = _AdmState(_d(st.f), _d(st.z), _d(st.lam), st.alpha_prev)
+    G = np.zeros((2, n, n))
+    norms = np.zeros(3)
+    cp = prm.c()
+    m, rp, ix, ln = t._args()
+    a = _load().orc_adm_joint_iterate(n, m, rp, ix, ln, _d(g), C.byref(cp), C.byref(cst), _d(G),
+                                      _d(norms))
+    st.alpha_prev = cst.alpha_prev
+    return float(a), G, tuple(norms)
+
+
+def adm_joint(t: Table, g, prm: AdmParams, f0=None):
+    """Joint ADM from f0 ([2][n][n], default 0) against g = [2][M].
+    Returns (f, iterations, phi[0..iters], alpha[0..iters-1])."""
+    n = t.geom.n
+    g = _f64(g).reshape(-1)
+    f = np.zeros((2, n, n)) if f0 is None else _f64(f0).copy()
+    phi = np.zeros(prm.max_iter + 1)
+    alpha = np.zeros(max(prm.max_iter, 1))
+    cp = prm.c()
+    m, rp, ix, ln = t._args()
+    k = _load().orc_adm_joint_run(n, m, rp, ix, ln, _d(g), C.byref(cp), _d(f), _d(phi), _d(alpha))
+    return f, int(k), phi[:k + 1].copy(), alpha[:k].copy()
 
 
 # ---------------------------------------------------------------------------

@@ -22,7 +22,11 @@
  *      z = 0 where |w| = 0 (the exact minimiser of the z-line of Eq. (7)).
  *   R2 lambda and z have the shape of grad f: two components per pixel.
  *   R3 the TV of Eq. (4) acts on each energy channel separately, so the
- *      stacked problem of Eq. (3) splits into one ADM per channel.
+ *      stacked problem of Eq. (3) splits into one ADM per channel.  The
+ *      other reading, one TV over the stacked image f, is kept as a variant:
+ *      the norm at each pixel is taken over both channels' gradients
+ *      (orc_adm_joint_*), the z-step shrinks 4-vectors and one step alpha
+ *      serves the stacked f.
  *   R5 xi (multiplier step) is a parameter; the default elsewhere is xi = rho.
  *   R6 "BB-like" step: with c(G) = |G|^2 / (mu |A G|^2 + rho |grad G|^2)
  *      (the exact line-search step of the quadratic f-subproblem along -G),
@@ -399,6 +403,164 @@ int orc_adm_run(int n, int64_t m, const int64_t *rowptr, const int32_t *idx, con
         if (alpha) alpha[k] = a;
         ++k;
         double cur = orc_objective(n, m, rowptr, idx, len, g, prm->mu, f);
+        if (phi) phi[k] = cur;
+        if (prm->tol > 0.0 && prev > 0.0 && fabs(cur - prev) / prev < prm->tol) break;
+        prev = cur;
+    }
+    free(st.z);
+    free(st.lam);
+    return k;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Joint (channel-coupled) TV on the combined image f = (f_h, f_l), Eq. (4)  */
+/* read with the TV norm taken over both channels at every pixel:           */
+/*   Phi(f) = sum_p |(grad f_h, grad f_l)_p|_2 + mu/2 sum_c |A f_c - g_c|^2  */
+/* The ADM of Eq. (6)-(10) then has one z, lambda in R^{4N} (both channels'  */
+/* gradients), one G in R^{2N} and one step alpha for the stacked f.         */
+/* ------------------------------------------------------------------------ */
+
+/*
+ * Prox of the per-pixel 4-norm, Eq. (8) with the joint reading: for
+ * w_p = (wh0, wh1, wl0, wl1), z_p = max(|w_p| - t, 0) w_p / |w_p|.
+ * wh, wl, zh, zl: [2][npix] (the two gradient components of each channel).
+ */
+void orc_shrink4(int64_t npix, const double *wh, const double *wl, double t, double *zh, double *zl)
+{
+    for (int64_t p = 0; p < npix; ++p) {
+        double a = wh[p], b = wh[npix + p], c = wl[p], d = wl[npix + p];
+        double nrm = sqrt(a * a + b * b + c * c + d * d);
+        double s = nrm - t;
+        if (s > 0.0 && nrm > 0.0) {
+            zh[p] = s * a / nrm;
+            zh[npix + p] = s * b / nrm;
+            zl[p] = s * c / nrm;
+            zl[npix + p] = s * d / nrm;
+        } else {
+            zh[p] = zh[npix + p] = zl[p] = zl[npix + p] = 0.0;
+        }
+    }
+}
+
+/* sum_p |(grad f_h, grad f_l)_p|_2 for f = [2][N]. */
+double orc_tv_joint(int n, const double *f)
+{
+    const int64_t N = (int64_t)n * n;
+    double *gh = (double *)malloc(sizeof(double) * (size_t)(2 * N));
+    double *gl = (double *)malloc(sizeof(double) * (size_t)(2 * N));
+    orc_grad(n, f, gh);
+    orc_grad(n, f + N, gl);
+    double s = 0.0;
+    for (int64_t p = 0; p < N; ++p)
+        s += sqrt(gh[p] * gh[p] + gh[N + p] * gh[N + p] + gl[p] * gl[p] + gl[N + p] * gl[N + p]);
+    free(gh);
+    free(gl);
+    return s;
+}
+
+/* Joint objective; g = [2][m] (g_h then g_l), f = [2][N]. */
+double orc_objective_joint(int n, int64_t m, const int64_t *rowptr, const int32_t *idx,
+                           const double *len, const double *g, double mu, const double *f)
+{
+    const int64_t N = (int64_t)n * n;
+    double *r = (double *)malloc(sizeof(double) * (size_t)m);
+    double s = 0.0;
+    for (int c = 0; c < 2; ++c) {
+        orc_project(m, rowptr, idx, len, f + c * N, r);
+        for (int64_t i = 0; i < m; ++i) { double e = r[i] - g[c * m + i]; s += e * e; }
+    }
+    free(r);
+    return orc_tv_joint(n, f) + 0.5 * mu * s;
+}
+
+/*
+ * One ADM iteration, Eq. (10), for the joint problem.  State sizes: f 2N
+ * ([channel][N]), z and lam 4N ([channel][component][N]).  The steps are
+ * those of orc_adm_iterate with the 4-vector shrink in the z-step, and the
+ * step c(G) = |G|^2 / (mu |A G|^2 + rho |grad G|^2) taken over both
+ * channels (the exact line search of the stacked quadratic).
+ * G_out (2N) and norms (3) may be NULL.  Returns the step applied.
+ */
+double orc_adm_joint_iterate(int n, int64_t m, const int64_t *rowptr, const int32_t *idx,
+                             const double *len, const double *g, const orc_adm_params *prm,
+                             orc_adm_state *st, double *G_out, double *norms)
+{
+    const int64_t N = (int64_t)n * n;
+    const double mu = prm->mu, rho = prm->rho, xi = prm->xi;
+    double *gf = (double *)malloc(sizeof(double) * (size_t)(4 * N));
+    double *w = (double *)malloc(sizeof(double) * (size_t)(4 * N));
+    double *r = (double *)malloc(sizeof(double) * (size_t)m);
+    double *t1 = (double *)malloc(sizeof(double) * (size_t)N);
+    double *t2 = (double *)malloc(sizeof(double) * (size_t)N);
+    double *t3 = (double *)malloc(sizeof(double) * (size_t)N);
+    double *G = (double *)malloc(sizeof(double) * (size_t)(2 * N));
+    double *AG = (double *)malloc(sizeof(double) * (size_t)m);
+    double *gG = (double *)malloc(sizeof(double) * (size_t)(2 * N));
+
+    /* z-step, Eq. (8), on the 4-vectors of both channels */
+    for (int c = 0; c < 2; ++c) orc_grad(n, st->f + c * N, gf + c * 2 * N);
+    for (int64_t p = 0; p < 4 * N; ++p) w[p] = gf[p] - st->lam[p] / rho;
+    orc_shrink4(N, w, w + 2 * N, 1.0 / rho, st->z, st->z + 2 * N);
+
+    /* G_f, Eq. (9), per channel; norms summed over both channels */
+    double gg = 0.0, aa = 0.0, dd = 0.0;
+    for (int c = 0; c < 2; ++c) {
+        const double *f = st->f + c * N, *z = st->z + c * 2 * N, *lam = st->lam + c * 2 * N;
+        double *Gc = G + c * N;
+        orc_project(m, rowptr, idx, len, f, r);
+        for (int64_t i = 0; i < m; ++i) r[i] -= g[c * m + i];
+        orc_backproject(m, N, rowptr, idx, len, r, t1);
+        for (int64_t p = 0; p < 2 * N; ++p) w[p] = gf[c * 2 * N + p] - z[p];
+        orc_grad_t(n, w, t2);
+        orc_grad_t(n, lam, t3);
+        for (int64_t p = 0; p < N; ++p) Gc[p] = mu * t1[p] + rho * t2[p] - t3[p];
+        orc_project(m, rowptr, idx, len, Gc, AG);
+        orc_grad(n, Gc, gG);
+        gg += dot(N, Gc, Gc);
+        aa += dot(m, AG, AG);
+        dd += dot(2 * N, gG, gG);
+    }
+
+    /* one step for the stacked f (R6) */
+    double den = mu * aa + rho * dd;
+    double cst = (den > 0.0) ? gg / den : 0.0;
+    double alpha;
+    if (prm->step_rule == 1 || st->alpha_prev < 0.0) alpha = cst;
+    else alpha = st->alpha_prev;
+    st->alpha_prev = cst;
+
+    /* f-step and multiplier step, per channel */
+    for (int64_t p = 0; p < 2 * N; ++p) {
+        st->f[p] -= alpha * G[p];
+        if (prm->nonneg && st->f[p] < 0.0) st->f[p] = 0.0;
+    }
+    for (int c = 0; c < 2; ++c) orc_grad(n, st->f + c * N, gf + c * 2 * N);
+    for (int64_t p = 0; p < 4 * N; ++p) st->lam[p] -= xi * (gf[p] - st->z[p]);
+
+    if (G_out) memcpy(G_out, G, sizeof(double) * (size_t)(2 * N));
+    if (norms) { norms[0] = gg; norms[1] = aa; norms[2] = dd; }
+    free(gf); free(w); free(r); free(t1); free(t2); free(t3); free(G); free(AG); free(gG);
+    return alpha;
+}
+
+/* The joint ADM loop from f ([2][N], in/out) with z = lam = 0; as orc_adm_run. */
+int orc_adm_joint_run(int n, int64_t m, const int64_t *rowptr, const int32_t *idx, const double *len,
+                      const double *g, const orc_adm_params *prm, double *f, double *phi, double *alpha)
+{
+    const int64_t N = (int64_t)n * n;
+    orc_adm_state st;
+    st.f = f;
+    st.z = (double *)calloc((size_t)(4 * N), sizeof(double));
+    st.lam = (double *)calloc((size_t)(4 * N), sizeof(double));
+    st.alpha_prev = -1.0;
+    double prev = orc_objective_joint(n, m, rowptr, idx, len, g, prm->mu, f);
+    if (phi) phi[0] = prev;
+    int k = 0;
+    while (k < prm->max_iter) {
+        double a = orc_adm_joint_iterate(n, m, rowptr, idx, len, g, prm, &st, NULL, NULL);
+        if (alpha) alpha[k] = a;
+        ++k;
+        double cur = orc_objective_joint(n, m, rowptr, idx, len, g, prm->mu, f);
         if (phi) phi[k] = cur;
         if (prm->tol > 0.0 && prev > 0.0 && fabs(cur - prev) / prev < prm->tol) break;
         prev = cur;

@@ -12,6 +12,9 @@ quantity from its definition by a different route than the oracle does:
 * ``pls_matrix``: the Hessian of the PLS objective Eq. (13)-(14), assembled
   pair by pair from the definition of R(u).
 * ``chambolle_pock``: an independent primal-dual solver of Eq. (4).
+* ``tv_joint_np`` / ``aug_lagrangian_joint`` / ``chambolle_pock_joint``: the
+  same for the channel-coupled TV (the norm taken over both channels'
+  gradients at every pixel).
 """
 from __future__ import annotations
 
@@ -180,3 +183,59 @@ def pls_objective(u: np.ndarray, d: np.ndarray, mask: np.ndarray, gamma: float, 
                     e = eps if (mask[i, j] or mask[ii, jj]) else 1.0
                     r += 0.5 * e * (u[i, j] - u[ii, jj]) ** 2
     return float(((u - d) ** 2).sum() + gamma * r)
+
+
+def tv_joint_np(f: np.ndarray) -> float:
+    """sum_p |(grad f_0, grad f_1)_p|_2 for f = [2][n][n]."""
+    d0, d1 = grad_np(f[0]), grad_np(f[1])
+    return float(np.sqrt(d0[0] ** 2 + d0[1] ** 2 + d1[0] ** 2 + d1[1] ** 2).sum())
+
+
+def tv_ls_objective_joint(A, g, f, mu) -> float:
+    """Joint form of Eq. (4): tv_joint + mu/2 sum_c |A f_c - g_c|^2, g = [2][M]."""
+    s = 0.0
+    for c in range(2):
+        r = A @ f[c].reshape(-1) - g[c].reshape(-1)
+        s += float(r @ r)
+    return tv_joint_np(f) + 0.5 * mu * s
+
+
+def aug_lagrangian_joint(A, g, f, z, lam, mu, rho) -> float:
+    """Eq. (6) for the stacked f = [2][n][n]; z, lam = [2][2][n][n]; the
+    z-norm is the per-pixel 4-norm."""
+    zn = float(np.sqrt((z ** 2).sum(axis=(0, 1))).sum())
+    val = zn
+    for c in range(2):
+        e = grad_np(f[c]) - z[c]
+        r = A @ f[c].reshape(-1) - g[c].reshape(-1)
+        val += -float((lam[c] * e).sum()) + 0.5 * rho * float((e * e).sum()) + 0.5 * mu * float(r @ r)
+    return val
+
+
+def chambolle_pock_joint(A, g, n, mu, iters=20000):
+    """Chambolle-Pock for the joint problem: the dual variable of the TV term
+    is projected per pixel onto the unit ball of R^4 (both channels)."""
+    N = n * n
+    v = np.random.default_rng(0).random(N)
+    for _ in range(200):
+        v = _gradT_np(grad_np(v.reshape(n, n))).reshape(-1) + A.T @ (A @ v)
+        v /= np.linalg.norm(v)
+    Lk = math.sqrt(np.linalg.norm(_gradT_np(grad_np(v.reshape(n, n))).reshape(-1) + A.T @ (A @ v)))
+    tau = sigma = 0.99 / Lk
+    f = np.zeros((2, N))
+    fb = f.copy()
+    p = np.zeros((2, 2, n, n))
+    q = np.zeros((2, A.shape[0]))
+    gg = g.reshape(2, -1)
+    for _ in range(iters):
+        for c in range(2):
+            p[c] = p[c] + sigma * grad_np(fb[c].reshape(n, n))
+        nrm = np.maximum(1.0, np.sqrt((p ** 2).sum(axis=(0, 1))))
+        p = p / nrm
+        f_new = np.empty_like(f)
+        for c in range(2):
+            q[c] = (q[c] + sigma * (A @ fb[c] - gg[c])) / (1.0 + sigma / mu)
+            f_new[c] = f[c] - tau * (_gradT_np(p[c]).reshape(-1) + A.T @ q[c])
+        fb = 2.0 * f_new - f
+        f = f_new
+    return f.reshape(2, n, n)
