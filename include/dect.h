@@ -145,6 +145,11 @@ typedef struct {
     int nonneg;         /* 1: project f onto f >= 0 after every f-step (x in R_+^N,
                            Eq. (1)); costs one extra A per iteration to rebuild the
                            residual.  0: the unconstrained steps of Eq. (7)-(10)        */
+    int joint_tv;       /* 0: TV per energy channel (the stacked problem splits);
+                           1: one TV over the stacked image: at each pixel the norm of
+                           both energies' gradients (4-vector), one step and one
+                           stopping test per slice, reports carry the slice's joint
+                           objective on both channels                                  */
 } dect_adm_params;
 
 typedef struct {

@@ -42,7 +42,7 @@ class _AdmParams(C.Structure):
     _fields_ = [("mu", C.c_double), ("rho", C.c_double), ("xi", C.c_double),
                 ("beta", C.c_double * 2), ("step_rule", C.c_int), ("max_iter", C.c_int),
                 ("rel_obj_tol", C.c_double), ("check_every", C.c_int), ("warm_start", C.c_int),
-                ("nonneg", C.c_int)]
+                ("nonneg", C.c_int), ("joint_tv", C.c_int)]
 
 
 class _AdmReport(C.Structure):
@@ -280,12 +280,13 @@ class AdmParams:
     check_every: int = 10
     warm_start: bool = False
     nonneg: bool = False                # project f onto f >= 0 after each f-step
+    joint: bool = False                 # one TV over both energies of a slice
 
     def _c(self) -> _AdmParams:
         b = (C.c_double * 2)(*self.beta)
         return _AdmParams(self.mu, self.rho, self.xi, b, self.step_rule, self.max_iter,
                           self.rel_obj_tol, self.check_every, 1 if self.warm_start else 0,
-                          1 if self.nonneg else 0)
+                          1 if self.nonneg else 0, 1 if self.joint else 0)
 
 
 @dataclasses.dataclass

@@ -26,6 +26,12 @@
 //            then the last block forms Phi^k, the stopping test and
 //            alpha^k in FP64.
 //
+// Optional joint TV over the stacked image (both energies of a slice, channels
+// 2s and 2s + 1, which one thread always holds together): the TV norm and the
+// z-shrink take the 4-vector of both channels' gradients at a pixel, and the
+// last block of k_fwd forms one step and one stopping test per slice from
+// the sums of the two channels' norms.
+//
 // Optional projection onto f >= 0 (x in R_+^N, Eq. (1)): k_tv clamps each
 // updated pixel, f^{k+1} = max(f^k - alpha^k G^k, 0).  The residual is then
 // no longer r - alpha q, so a fourth kernel (k_fwd in mode 2) rebuilds
@@ -74,6 +80,7 @@ struct AdmConst {
     int64_t N, M;
     int xi_is_rho;       // multiplier rebuilt from p (see k_tv)
     int nonneg;          // f-step projected onto f >= 0
+    int joint;           // TV over both channels of a slice (channels 2s, 2s + 1)
     float mu, rho, xi;   // FP32 copies for the bulk kernels
     double mu_d, rho_d;  // FP64 for the step and objective
     double tol;
@@ -85,6 +92,24 @@ template <int NB>
 __device__ __forceinline__ double *part_of(const AdmDev &D, int kernel)
 {
     return D.part + (size_t)kernel * 2 * kGrid * NB;
+}
+
+// z-shrink of Eq. (8) per pixel on the 4-vector of both channels' gradients
+// (joint TV over the stacked image).
+__device__ __forceinline__ void shrink4(float w0, float w1, float w2, float w3, float t, float &z0,
+                                        float &z1, float &z2, float &z3)
+{
+    float nrm = sqrtf(w0 * w0 + w1 * w1 + w2 * w2 + w3 * w3);
+    float s = nrm - t;
+    if (s > 0.f && nrm > 0.f) {
+        float k = s / nrm;
+        z0 = k * w0;
+        z1 = k * w1;
+        z2 = k * w2;
+        z3 = k * w3;
+    } else {
+        z0 = z1 = z2 = z3 = 0.f;
+    }
 }
 
 // z-shrink of Eq. (8) per pixel on the 2-vector w (reading: w / |w| for sign).
@@ -121,7 +146,7 @@ __device__ __forceinline__ float nonneg_step(float f, float a, float g, bool cla
 // the step is empty and f^0 is used as given), and r and |r|^2 are left to
 // k_fwd in mode 2.
 // ---------------------------------------------------------------------------
-template <int NB>
+template <int NB, bool JOINT>
 __global__ void __launch_bounds__(kBlock, 4) k_tv(const float *__restrict__ f_in, float *__restrict__ f_out,
                                                const float *__restrict__ G, float *__restrict__ lam,
                                                float *__restrict__ z, float *__restrict__ p,
@@ -187,12 +212,24 @@ __global__ void __launch_bounds__(kBlock, 4) k_tv(const float *__restrict__ f_in
                 }
             }
         }
-        Vec<VW> p0, p1;
+        Vec<VW> p0, p1, d0, d1;
 #pragma unroll
         for (int c = 0; c < VW; ++c) {
-            float g0 = fc.v[c] - fu.v[c];   // Eq. (2), 0 on the first row
-            float g1 = fc.v[c] - fl.v[c];   // Eq. (2), 0 on the first column
-            acc[0].v[c] += sqrtf(g0 * g0 + g1 * g1);
+            d0.v[c] = fc.v[c] - fu.v[c];   // Eq. (2), 0 on the first row
+            d1.v[c] = fc.v[c] - fl.v[c];   // Eq. (2), 0 on the first column
+        }
+        if (JOINT) {  // one norm per slice over both channels (c, c + 1)
+#pragma unroll
+            for (int c = 0; c < VW; c += 2)
+                acc[0].v[c] += sqrtf(d0.v[c] * d0.v[c] + d1.v[c] * d1.v[c] + d0.v[c + 1] * d0.v[c + 1] +
+                                     d1.v[c + 1] * d1.v[c + 1]);
+        } else {
+#pragma unroll
+            for (int c = 0; c < VW; ++c) acc[0].v[c] += sqrtf(d0.v[c] * d0.v[c] + d1.v[c] * d1.v[c]);
+        }
+#pragma unroll
+        for (int c = 0; c < VW; ++c) {
+            const float g0 = d0.v[c], g1 = d1.v[c];
             if (final_pass) continue;
             float a0, a1;
             if (C.xi_is_rho) {
@@ -212,14 +249,28 @@ __global__ void __launch_bounds__(kBlock, 4) k_tv(const float *__restrict__ f_in
                     a1 -= C.xi * (g1 - z1.v[c]);
                 }
             }
-            float s0, s1;
-            shrink2(g0 - a0 * inv_rho, g1 - a1 * inv_rho, inv_rho, s0, s1);
-            l0.v[c] = a0;
+            l0.v[c] = a0;  // lambda^k
             l1.v[c] = a1;
-            z0.v[c] = s0;
-            z1.v[c] = s1;
-            p0.v[c] = C.rho * (g0 - s0) - a0;
-            p1.v[c] = C.rho * (g1 - s1) - a1;
+            if (!JOINT) {
+                float s0, s1;
+                shrink2(g0 - a0 * inv_rho, g1 - a1 * inv_rho, inv_rho, s0, s1);
+                z0.v[c] = s0;
+                z1.v[c] = s1;
+            }
+        }
+        if (JOINT && !final_pass) {
+#pragma unroll
+            for (int c = 0; c < VW; c += 2)
+                shrink4(d0.v[c] - l0.v[c] * inv_rho, d1.v[c] - l1.v[c] * inv_rho,
+                        d0.v[c + 1] - l0.v[c + 1] * inv_rho, d1.v[c + 1] - l1.v[c + 1] * inv_rho, inv_rho,
+                        z0.v[c], z1.v[c], z0.v[c + 1], z1.v[c + 1]);
+        }
+        if (!final_pass) {
+#pragma unroll
+            for (int c = 0; c < VW; ++c) {
+                p0.v[c] = C.rho * (d0.v[c] - z0.v[c]) - l0.v[c];
+                p1.v[c] = C.rho * (d1.v[c] - z1.v[c]) - l1.v[c];
+            }
         }
         if (!final_pass) {
             if (!C.xi_is_rho) {
@@ -465,11 +516,19 @@ template <int NB>
 __device__ void adm_finish(const AdmConst &C, const AdmDev &D)
 {
     const int k = *D.k;
-    if (threadIdx.x < NB) {
+    // joint TV: thread 2s decides for the slice (channels 2s, 2s + 1) from
+    // the sums of both channels' norms; the odd threads stay idle
+    const int span = C.joint ? 2 : 1;
+    if (threadIdx.x < NB && threadIdx.x % span == 0) {
         const int b = threadIdx.x;
+        auto sum = [&](int slot) {
+            double v = D.red[slot * NB + b];
+            if (span == 2) v += D.red[slot * NB + b + 1];
+            return v;
+        };
         double alpha = 0.0;
         if (D.active[b]) {
-            const double phi = D.red[R_TV * NB + b] + 0.5 * C.mu_d * D.red[R_RR * NB + b];
+            const double phi = sum(R_TV) + 0.5 * C.mu_d * sum(R_RR);
             if (!isfinite(phi)) atomicOr(D.bad, 1);
             bool stop = false;
             if (k > 0) {
@@ -484,8 +543,7 @@ __device__ void adm_finish(const AdmConst &C, const AdmDev &D)
                 D.iters[b] = k;
             } else {
                 D.phi_prev[b] = phi;
-                const double gg = D.red[R_GG * NB + b], qq = D.red[R_QQ * NB + b],
-                             dd = D.red[R_DD * NB + b];
+                const double gg = sum(R_GG), qq = sum(R_QQ), dd = sum(R_DD);
                 const double den = C.mu_d * qq + C.rho_d * dd;
                 const double c = den > 0.0 ? gg / den : 0.0;
                 alpha = (C.rule == DECT_STEP_CAUCHY || k == 0) ? c : D.c_prev[b];
@@ -494,6 +552,13 @@ __device__ void adm_finish(const AdmConst &C, const AdmDev &D)
             }
         }
         D.alpha[b] = alpha;
+        if (span == 2) {
+            D.alpha[b + 1] = alpha;
+            D.active[b + 1] = D.active[b];
+            D.conv[b + 1] = D.conv[b];
+            D.iters[b + 1] = D.iters[b];
+            D.rel[b + 1] = D.rel[b];
+        }
     }
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -729,6 +794,17 @@ cudaError_t tune_bwd(const dect_plan *P, Work &W, const AdmConst &C, cudaStream_
     return cudaSuccess;
 }
 
+template <int NB>
+void launch_tv(const Work &W, const AdmConst &C, int par, int final_pass, cudaStream_t s)
+{
+    if (C.joint)
+        k_tv<NB, true><<<kGrid, kBlock, 0, s>>>(W.f[par], W.f[1 - par], W.G, W.lam, W.z, W.p, W.r, W.q, C,
+                                                 W.D, final_pass);
+    else
+        k_tv<NB, false><<<kGrid, kBlock, 0, s>>>(W.f[par], W.f[1 - par], W.G, W.lam, W.z, W.p, W.r, W.q, C,
+                                                  W.D, final_pass);
+}
+
 // Optional timing events around the two table kernels of one iteration.
 struct IterEvents {
     cudaEvent_t b0, b1, f0, f1;
@@ -739,7 +815,7 @@ template <int NB>
 void enqueue_iteration(const dect_plan *P, const Work &W, const AdmConst &C, int par, cudaStream_t s,
                        const IterEvents *ev)
 {
-    k_tv<NB><<<kGrid, kBlock, 0, s>>>(W.f[par], W.f[1 - par], W.G, W.lam, W.z, W.p, W.r, W.q, C, W.D, 0);
+    launch_tv<NB>(W, C, par, 0, s);
     if (C.nonneg)
         k_fwd<NB, Kern<NB>::GF, 2><<<kGrid, kBlock, 0, s>>>(P->rowptr, P->ent, W.f[1 - par], W.r, W.m,
                                                              W.beta, C, W.D);
@@ -769,6 +845,7 @@ dect_status run_chunk(const dect_plan *P, const float *m, float *x, int nimg,
     double xi = prm->xi > 0 ? prm->xi : prm->rho;
     C.xi = (float)xi;
     C.nonneg = prm->nonneg ? 1 : 0;
+    C.joint = prm->joint_tv ? 1 : 0;
     C.xi_is_rho = (xi == prm->rho && !C.nonneg) ? 1 : 0;
     C.mu_d = prm->mu;
     C.rho_d = prm->rho;
@@ -935,7 +1012,7 @@ dect_status run_chunk(const dect_plan *P, const float *m, float *x, int nimg,
     // final step f^K = f^{K-1} - alpha G and the objective at the result
     const int par = done_iters & 1;
     if (err == cudaSuccess) {
-        k_tv<NB><<<kGrid, kBlock, 0, cs>>>(W.f[par], W.f[1 - par], W.G, W.lam, W.z, W.p, W.r, W.q, C, D, 1);
+        launch_tv<NB>(W, C, par, 1, cs);
         if (C.nonneg)
             k_fwd<NB, Kern<NB>::GF, 2><<<kGrid, kBlock, 0, cs>>>(P->rowptr, P->ent, W.f[1 - par], W.r, m,
                                                                   W.beta, C, D);
@@ -975,7 +1052,13 @@ dect_status run_chunk(const dect_plan *P, const float *m, float *x, int nimg,
         for (int b = 0; b < nimg; ++b) {
             rep[b].iters = K == 0 ? 0 : hit[b];
             rep[b].converged = hconv[b];
-            rep[b].objective = hred[R_TV * NB + b] + 0.5 * prm->mu * hred[R_RR * NB + b];
+            if (C.joint) {  // the slice's joint objective, reported on both of its channels
+                const int b0 = b & ~1;
+                rep[b].objective = hred[R_TV * NB + b0] + hred[R_TV * NB + b0 + 1] +
+                                   0.5 * prm->mu * (hred[R_RR * NB + b0] + hred[R_RR * NB + b0 + 1]);
+            } else {
+                rep[b].objective = hred[R_TV * NB + b] + 0.5 * prm->mu * hred[R_RR * NB + b];
+            }
             rep[b].rel_change = hrel[b];
         }
     }
@@ -1002,7 +1085,7 @@ extern "C" dect_status dect_adm_tv_ex(const dect_plan *plan, const float *m, flo
         prm->max_iter < 0 || (prm->step_rule != DECT_STEP_BB1 && prm->step_rule != DECT_STEP_CAUCHY) ||
         !std::isfinite(prm->mu) || !std::isfinite(prm->rho) || !std::isfinite(prm->xi) ||
         !std::isfinite(prm->beta[0]) || !std::isfinite(prm->beta[1]) || prm->check_every < 0 ||
-        (prm->nonneg != 0 && prm->nonneg != 1))
+        (prm->nonneg != 0 && prm->nonneg != 1) || (prm->joint_tv != 0 && prm->joint_tv != 1))
         return DECT_ERR_INVALID_ARG;
     DECT_CUDA(cudaSetDevice(plan->device));
     cudaStream_t s = (cudaStream_t)stream;

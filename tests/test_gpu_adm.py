@@ -22,19 +22,19 @@ def rel_l2(a, b):
 
 
 def run_both(g, slices, K, rule=dect.CAUCHY, beta=(1.0, 0.6), xi=0.0, tol=0.0, x0=None,
-             nonneg=False):
+             nonneg=False, joint=False):
     plan = dect.Plan(g)
     t = oracle.table(g)
     m = np.stack([s.m for s in slices])
     prm = dect.AdmParams(mu=MU, rho=RHO, xi=xi, beta=beta, step_rule=rule, max_iter=K,
-                         rel_obj_tol=tol, warm_start=x0 is not None, nonneg=nonneg)
+                         rel_obj_tol=tol, warm_start=x0 is not None, nonneg=nonneg, joint=joint)
     xin = None if x0 is None else torch.tensor(x0, dtype=torch.float32, device="cuda")
     x, reps = dect.adm_tv(plan, torch.tensor(m, dtype=torch.float32, device="cuda"), prm, x=xin)
     x = x.cpu().numpy()
     outs = []
     for i, s in enumerate(slices):
         op = oracle.AdmParams(mu=MU, rho=RHO, xi=(xi if xi > 0 else None), beta=beta,
-                              step_rule=rule, max_iter=K, tol=tol, nonneg=nonneg)
+                              step_rule=rule, max_iter=K, tol=tol, nonneg=nonneg, joint=joint)
         # the oracle reads the same FP32 data the GPU reads
         xo, its = oracle.adm_dual(t, m[i].astype(np.float32).astype(np.float64), op,
                                   x0=None if x0 is None else x0[i].astype(np.float32).astype(np.float64))
@@ -124,6 +124,46 @@ def test_nonnegative_projection_warm_start_negative():
     x1, _, _, _ = run_both(g, [sl], 0, x0=x0, nonneg=True)
     np.testing.assert_allclose(x1, x0, rtol=1e-6, atol=0.0)
     assert x1.min() < 0.0
+
+
+@pytest.mark.parametrize("ns,rule,xi", [(1, dect.CAUCHY, 0.0), (5, dect.CAUCHY, 0.0), (3, dect.BB1, 100.0)])
+def test_joint_tv(ns, rule, xi):
+    """TV over both energies of a slice (4-vector shrink, one step per slice):
+    parity with the oracle's joint ADM and the slice's joint objective on
+    both channels' reports."""
+    g = synth.tiny_geometry(n=48, nv=24, nb=72, px=1.0, sod=120.0, sdd=240.0)
+    slices = [synth.make_slice(g, seed=60 + i, i0=1e4) for i in range(ns)]
+    K = 30
+    x, reps, outs, t = run_both(g, slices, K, rule=rule, xi=xi, joint=True)
+    for i in range(ns):
+        for e in range(2):
+            assert rel_l2(x[i, e], outs[i][0][e]) <= 1e-4
+        b = np.array([1.0, 0.6]).reshape(2, 1)
+        gm = b * slices[i].m.reshape(2, -1).astype(np.float32)
+        phi = oracle.objective_joint(t, gm, MU, b.reshape(2, 1, 1) * x[i].astype(np.float64))
+        for e in range(2):
+            assert reps[2 * i + e].iters == K
+            assert abs(reps[2 * i + e].objective - phi) <= 1e-4 * phi
+    # the coupling changes the result
+    xs, _, _, _ = run_both(g, slices[:1], K)
+    assert rel_l2(xs[0], x[0]) > 1e-3
+
+
+def test_joint_tv_stop_and_projection():
+    """Joint TV with the relative-objective stop (one test per slice: both
+    channels stop together) and with the projection onto f >= 0."""
+    g = synth.tiny_geometry(n=48, nv=24, nb=72, px=1.0, sod=120.0, sdd=240.0)
+    sl = [synth.make_slice(g, seed=70 + i, i0=3e2) for i in range(2)]
+    x, reps, outs, t = run_both(g, sl, 2000, tol=1e-4, joint=True)
+    for i in range(2):
+        assert reps[2 * i].iters == reps[2 * i + 1].iters
+        assert reps[2 * i].converged and reps[2 * i + 1].converged
+        assert abs(reps[2 * i].iters - outs[i][1][0]) <= 2
+    x, reps, outs, t = run_both(g, sl, 40, joint=True, nonneg=True)
+    assert x.min() >= 0.0
+    for i in range(2):
+        for e in range(2):
+            assert rel_l2(x[i, e], outs[i][0][e]) <= 1e-4
 
 
 def test_relative_objective_stop():
