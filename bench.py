@@ -496,7 +496,8 @@ def main():
     p0 = state["prof"][-1]
     width = min(32, 1 << (2 * S - 1).bit_length())
     choice, _ = plan.tuning(width)
-    bwd_name = ["k_bwd<tile4>", "k_bwd<tile8>", "k_bwd<tile16>", "k_bwd_win"][choice] if choice >= 0 else "k_bwd"
+    names = ["k_bwd<tile4>", "k_bwd<tile8>", "k_bwd<tile16>", "k_bwd_win", "k_bwd<1k,8x8>", "k_bwd<1k,16x8>"]
+    bwd_name = names[choice] if 0 <= choice < len(names) else "k_bwd"
     if fwd_ms >= bwd_ms:
         kname, avg_ms, bytes_ = "k_fwd", fwd_ms / max(fwd_n, 1), p0.table_bytes_fwd
     else:

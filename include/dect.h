@@ -301,11 +301,16 @@ dect_status dect_adm_tv_ex(const dect_plan *plan, const float *m, float *x, int 
  * batch of `images` interleaved channels (2, 4, 8, 16 or 32; a call with c
  * channels uses the next of these widths >= min(c, 32)), and the measured
  * median time of each variant in microseconds (-1 = not available):
- *   0-2 L1-cached gather with 4x4 / 8x8 / 16x16 pixel tiles per block,
- *   3   shared-memory sinogram windows (cp.async staged).
- * *choice = -1 until an ADM call with that width has run.  Host memory.
+ *   0-2 L1-cached gather with 4x4 / 8x8 / 16x16 pixel tiles per 256-thread block,
+ *   3   shared-memory sinogram windows (cp.async staged),
+ *   4-5 L1-cached gather, one 1024-thread block per SM, tiles of two / four
+ *       block steps (8x8 / 16x8 pixels at 32 channels, 8x16 / 16x16 below).
+ * *choice = -1 until an ADM call with that width has run.  Host memory:
+ * us has DECT_BWD_VARIANTS elements.
  */
-dect_status dect_plan_get_tuning(const dect_plan *plan, int images, int *choice, float us[4]);
+#define DECT_BWD_VARIANTS 6
+dect_status dect_plan_get_tuning(const dect_plan *plan, int images, int *choice,
+                                 float us[DECT_BWD_VARIANTS]);
 
 /* Fix the A^T variant used for batch width `images` (skipping the timing),
  * or pass choice = -1 to let the next ADM call time the candidates again.

@@ -212,9 +212,9 @@ class Plan:
             pass
 
     def tuning(self, images: int):
-        """(chosen A^T variant, [median us of variants 0..3]) for a batch width; see dect.h."""
+        """(chosen A^T variant, [median us of each variant]) for a batch width; see dect.h."""
         ch = C.c_int(-1)
-        us = (C.c_float * 4)()
+        us = (C.c_float * BWD_VARIANTS)()
         _check(load().dect_plan_get_tuning(self._h, images, C.byref(ch), us), "dect_plan_get_tuning")
         return ch.value, list(us)
 
@@ -265,6 +265,7 @@ def backproject(plan: Plan, y, x=None, stream=None):
 
 
 BB1, CAUCHY = 0, 1
+BWD_VARIANTS = 6                        # DECT_BWD_VARIANTS in include/dect.h
 
 
 @dataclasses.dataclass

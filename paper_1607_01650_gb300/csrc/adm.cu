@@ -53,6 +53,10 @@ namespace {
 
 constexpr int kBlock = 256;
 constexpr int kGrid = kSMs * 8;  // fixed grid of every reducing kernel
+// k_fwd: 1024-thread blocks, one per SM, so that 32 adjacent rays of a view
+// (one warp each) share an L1
+constexpr int kFwdBlock = 1024;
+constexpr int kFwdGrid = kSMs;
 
 // reduction slots; (TV, RR) and (DD, QQ) are reduced together
 enum { R_TV = 0, R_RR = 1, R_DD = 2, R_QQ = 3, R_GG = 4, R_COUNT = 5 };
@@ -297,30 +301,30 @@ __global__ void __launch_bounds__(kBlock, 4) k_tv(const float *__restrict__ f_in
     reduce_images<NB, 2>(acc, part_of<NB>(D, C_TV), D.red + R_TV * NB, D.ctr + C_TV, smem);
 }
 
-// G = mu A^T r + grad^T p over the pixel-major table.  A block takes
-// kTile x kTile pixel tiles, so the sinogram lines its pixels gather are
-// shared in L1.
-template <int NB, int G_, int kTile>
-__global__ void __launch_bounds__(kBlock) k_bwd(const int64_t *__restrict__ colptr,
+// G = mu A^T r + grad^T p over the pixel-major table.  A block of BLK
+// threads takes TW x TH pixel tiles (BLK / G_ pixels at a time), so the
+// sinogram lines its pixels gather are shared in L1.
+template <int NB, int G_, int TW, int TH, int BLK>
+__global__ void __launch_bounds__(BLK) k_bwd(const int64_t *__restrict__ colptr,
                                                 const Entry *__restrict__ tent,
                                                 const float *__restrict__ r, const float *__restrict__ p,
                                                 float *__restrict__ G, AdmConst C, AdmDev D)
 {
     constexpr int VW = Batch<NB>::VW, LPE = Batch<NB>::CPB;
-    constexpr int RPS = kBlock / G_;  // pixels per block step
-    static_assert((kTile * kTile) % RPS == 0, "tile split");
-    __shared__ double smem[reduce_smem_doubles<NB>(1)];
+    constexpr int RPS = BLK / G_;  // pixels per block step
+    static_assert((TW * TH) % RPS == 0, "tile split");
+    __shared__ double smem[reduce_smem_doubles<NB, BLK>(1)];
     const int lr = threadIdx.x % G_, grp = lr / LPE, vl = lr % LPE;
     const int64_t sN = C.N * NB;
-    const int tiles_x = (C.n + kTile - 1) / kTile;
-    const int ntiles = tiles_x * tiles_x;
+    const int tiles_x = (C.n + TW - 1) / TW;
+    const int ntiles = tiles_x * ((C.n + TH - 1) / TH);
     Vec<VW> nrm[1];
     nrm[0].zero();
     for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
         const int ty = tile / tiles_x, tx = tile % tiles_x;
-        for (int s0 = 0; s0 < kTile * kTile; s0 += RPS) {
+        for (int s0 = 0; s0 < TW * TH; s0 += RPS) {
             const int slot = s0 + threadIdx.x / G_;
-            const int i = ty * kTile + slot / kTile, j = tx * kTile + slot % kTile;
+            const int i = ty * TH + slot / TW, j = tx * TW + slot % TW;
             const bool ok = i < C.n && j < C.n;
             const int64_t pix = (int64_t)i * C.n + j;
             int64_t b = 0, e = 0;
@@ -345,7 +349,7 @@ __global__ void __launch_bounds__(kBlock) k_bwd(const int64_t *__restrict__ colp
             }
         }
     }
-    reduce_images<NB, 1>(nrm, part_of<NB>(D, C_BWD), D.red + R_GG * NB, D.ctr + C_BWD, smem);
+    reduce_images<NB, 1, BLK>(nrm, part_of<NB>(D, C_BWD), D.red + R_GG * NB, D.ctr + C_BWD, smem);
 }
 
 // G = mu A^T r + grad^T p with everything a tile needs staged in shared
@@ -573,17 +577,17 @@ __device__ void adm_finish(const AdmConst &C, const AdmDev &D)
 // last block forms the step.  MODE 0: r = A f - beta m (set-up).  MODE 2:
 // r = A f - beta m and |r|^2 into the RR slot (residual of the projected
 // f-step, run after k_tv).
-template <int NB, int G_, int MODE>
-__global__ void __launch_bounds__(kBlock) k_fwd(const int64_t *__restrict__ rowptr,
+template <int NB, int G_, int MODE, int BLK = kFwdBlock>
+__global__ void __launch_bounds__(BLK) k_fwd(const int64_t *__restrict__ rowptr,
                                                 const Entry *__restrict__ ent,
                                                 const float *__restrict__ src, float *__restrict__ dst,
                                                 const float *__restrict__ m_planar,
                                                 const float *__restrict__ beta_img, AdmConst C, AdmDev D)
 {
     constexpr int VW = Batch<NB>::VW, LPE = Batch<NB>::CPB, CPB = Batch<NB>::CPB;
-    __shared__ double smem[reduce_smem_doubles<NB>(2)];
+    __shared__ double smem[reduce_smem_doubles<NB, BLK>(2)];
     const int lr = threadIdx.x % G_, grp = lr / LPE, vl = lr % LPE;
-    const int64_t rpb = kBlock / G_;
+    const int64_t rpb = BLK / G_;
     Vec<VW> nrm[2];
     nrm[0].zero();
     nrm[1].zero();
@@ -629,11 +633,11 @@ __global__ void __launch_bounds__(kBlock) k_fwd(const int64_t *__restrict__ rowp
         }
     }
     if (MODE == 1) {
-        if (reduce_images<NB, 2>(nrm, part_of<NB>(D, C_FWD), D.red + R_DD * NB, D.ctr + C_FWD, smem))
+        if (reduce_images<NB, 2, BLK>(nrm, part_of<NB>(D, C_FWD), D.red + R_DD * NB, D.ctr + C_FWD, smem))
             adm_finish<NB>(C, D);
     } else if (MODE == 2) {
         Vec<VW> rr[1] = {nrm[0]};
-        reduce_images<NB, 1>(rr, part_of<NB>(D, C_RES), D.red + R_RR * NB, D.ctr + C_RES, smem);
+        reduce_images<NB, 1, BLK>(rr, part_of<NB>(D, C_RES), D.red + R_RR * NB, D.ctr + C_RES, smem);
     }
 }
 
@@ -712,19 +716,29 @@ cudaError_t setup_window(const dect_plan *P, Work &W)
 }
 
 // A^T variants (autotuner candidates): 0-2 L1-cached gather with 4x4 / 8x8 /
-// 16x16 pixel tiles per block; 3 shared-memory sinogram windows.
-constexpr int kBwdVariants = 4;
+// 16x16 pixel tiles per 256-thread block; 3 shared-memory sinogram windows;
+// 4-5 L1-cached gather with one 1024-thread block per SM over tiles of two
+// or four block steps (8 x 8 / 16 x 8 pixels at 32 lanes per pixel, 8 x 16 /
+// 16 x 16 at 16), whose lines then stay in one L1.
+constexpr int kBwdVariants = DECT_BWD_VARIANTS;
 
 template <int NB>
 void launch_bwd(const dect_plan *P, const Work &W, const AdmConst &C, int variant, cudaStream_t s)
 {
     constexpr int GB = Kern<NB>::GB;
+    constexpr int RPS1k = 1024 / GB;  // pixels per step of a 1024-thread block
     switch (variant) {
     case 0:
-        k_bwd<NB, GB, 4><<<kGrid, kBlock, 0, s>>>(P->colptr, P->tent, W.r, W.p, W.G, C, W.D);
+        k_bwd<NB, GB, 4, 4, kBlock><<<kGrid, kBlock, 0, s>>>(P->colptr, P->tent, W.r, W.p, W.G, C, W.D);
         break;
     case 2:
-        k_bwd<NB, GB, 16><<<kGrid, kBlock, 0, s>>>(P->colptr, P->tent, W.r, W.p, W.G, C, W.D);
+        k_bwd<NB, GB, 16, 16, kBlock><<<kGrid, kBlock, 0, s>>>(P->colptr, P->tent, W.r, W.p, W.G, C, W.D);
+        break;
+    case 4:
+        k_bwd<NB, GB, 8, RPS1k / 4, 1024><<<kSMs, 1024, 0, s>>>(P->colptr, P->tent, W.r, W.p, W.G, C, W.D);
+        break;
+    case 5:
+        k_bwd<NB, GB, 16, RPS1k / 4, 1024><<<kSMs, 1024, 0, s>>>(P->colptr, P->tent, W.r, W.p, W.G, C, W.D);
         break;
     case 3: {
         WinArgs A{P->tmaj, P->tbase, P->tpo, P->wray0, P->wcnt, P->woff, P->wtot, P->nv, P->nvp,
@@ -733,7 +747,7 @@ void launch_bwd(const dect_plan *P, const Work &W, const AdmConst &C, int varian
         break;
     }
     default:
-        k_bwd<NB, GB, 8><<<kGrid, kBlock, 0, s>>>(P->colptr, P->tent, W.r, W.p, W.G, C, W.D);
+        k_bwd<NB, GB, 8, 8, kBlock><<<kGrid, kBlock, 0, s>>>(P->colptr, P->tent, W.r, W.p, W.G, C, W.D);
         break;
     }
 }
@@ -817,13 +831,13 @@ void enqueue_iteration(const dect_plan *P, const Work &W, const AdmConst &C, int
 {
     launch_tv<NB>(W, C, par, 0, s);
     if (C.nonneg)
-        k_fwd<NB, Kern<NB>::GF, 2><<<kGrid, kBlock, 0, s>>>(P->rowptr, P->ent, W.f[1 - par], W.r, W.m,
+        k_fwd<NB, Kern<NB>::GF, 2><<<kFwdGrid, kFwdBlock, 0, s>>>(P->rowptr, P->ent, W.f[1 - par], W.r, W.m,
                                                              W.beta, C, W.D);
     if (ev) cudaEventRecordWithFlags(ev->b0, s, cudaEventRecordExternal);
     launch_bwd<NB>(P, W, C, W.bwd, s);
     if (ev) cudaEventRecordWithFlags(ev->b1, s, cudaEventRecordExternal);
     if (ev) cudaEventRecordWithFlags(ev->f0, s, cudaEventRecordExternal);
-    k_fwd<NB, Kern<NB>::GF, 1><<<kGrid, kBlock, 0, s>>>(P->rowptr, P->ent, W.G, W.q, nullptr, nullptr,
+    k_fwd<NB, Kern<NB>::GF, 1><<<kFwdGrid, kFwdBlock, 0, s>>>(P->rowptr, P->ent, W.G, W.q, nullptr, nullptr,
                                                          C, W.D);
     if (ev) cudaEventRecordWithFlags(ev->f1, s, cudaEventRecordExternal);
 }
@@ -915,7 +929,7 @@ dect_status run_chunk(const dect_plan *P, const float *m, float *x, int nimg,
         count_launches(1);
     }
     // r^0 = A f^0 - beta m
-    k_fwd<NB, Kern<NB>::GF, 0><<<kGrid, kBlock, 0, s>>>(P->rowptr, P->ent, W.f[0], W.r, m, W.beta, C, D);
+    k_fwd<NB, Kern<NB>::GF, 0><<<kFwdGrid, kFwdBlock, 0, s>>>(P->rowptr, P->ent, W.f[0], W.r, m, W.beta, C, D);
     DECT_LAUNCH_CHECK();
     count_launches(1);
     W.bwd = 1;
@@ -1014,7 +1028,7 @@ dect_status run_chunk(const dect_plan *P, const float *m, float *x, int nimg,
     if (err == cudaSuccess) {
         launch_tv<NB>(W, C, par, 1, cs);
         if (C.nonneg)
-            k_fwd<NB, Kern<NB>::GF, 2><<<kGrid, kBlock, 0, cs>>>(P->rowptr, P->ent, W.f[1 - par], W.r, m,
+            k_fwd<NB, Kern<NB>::GF, 2><<<kFwdGrid, kFwdBlock, 0, cs>>>(P->rowptr, P->ent, W.f[1 - par], W.r, m,
                                                                   W.beta, C, D);
         k_unpack<NB><<<(unsigned)((tn + 255) / 256), 256, 0, cs>>>(W.f[1 - par], x, N, nimg, W.beta);
         err = cudaGetLastError();

@@ -74,7 +74,7 @@ struct dect_plan {
     // Autotuner cache: chosen A^T variant per ADM batch width (index log2(NB) - 1),
     // -1 until the first ADM call with that width has timed the candidates.
     mutable int bwd_choice[5];
-    mutable float bwd_us[5][4];
+    mutable float bwd_us[5][DECT_BWD_VARIANTS];
 };
 
 namespace dect {

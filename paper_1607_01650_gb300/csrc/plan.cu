@@ -689,7 +689,8 @@ extern "C" dect_status dect_plan_copy_table(const dect_plan *p, int64_t *rowptr,
     return DECT_OK;
 }
 
-extern "C" dect_status dect_plan_get_tuning(const dect_plan *p, int images, int *choice, float us[4])
+extern "C" dect_status dect_plan_get_tuning(const dect_plan *p, int images, int *choice,
+                                            float us[DECT_BWD_VARIANTS])
 {
     if (!p || !choice || !us) return DECT_ERR_INVALID_ARG;
     int idx;
@@ -702,13 +703,13 @@ extern "C" dect_status dect_plan_get_tuning(const dect_plan *p, int images, int 
     default: return DECT_ERR_INVALID_ARG;
     }
     *choice = p->bwd_choice[idx];
-    for (int v = 0; v < 4; ++v) us[v] = p->bwd_choice[idx] >= 0 ? p->bwd_us[idx][v] : -1.f;
+    for (int v = 0; v < DECT_BWD_VARIANTS; ++v) us[v] = p->bwd_choice[idx] >= 0 ? p->bwd_us[idx][v] : -1.f;
     return DECT_OK;
 }
 
 extern "C" dect_status dect_plan_set_tuning(dect_plan *p, int images, int choice)
 {
-    if (!p || choice < -1 || choice > 3) return DECT_ERR_INVALID_ARG;
+    if (!p || choice < -1 || choice >= DECT_BWD_VARIANTS) return DECT_ERR_INVALID_ARG;
     int idx;
     switch (images) {
     case 2: idx = 0; break;
@@ -719,6 +720,6 @@ extern "C" dect_status dect_plan_set_tuning(dect_plan *p, int images, int choice
     default: return DECT_ERR_INVALID_ARG;
     }
     p->bwd_choice[idx] = choice;
-    for (int v = 0; v < 4; ++v) p->bwd_us[idx][v] = -1.f;
+    for (int v = 0; v < DECT_BWD_VARIANTS; ++v) p->bwd_us[idx][v] = -1.f;
     return DECT_OK;
 }

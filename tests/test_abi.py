@@ -104,3 +104,9 @@ def test_struct_layouts_match_the_header(tmp_path):
         assert got[(cname, "sizeof")] == C.sizeof(py), cname
         for fname, _ in py._fields_:
             assert got[(cname, fname)] == getattr(py, fname).offset, (cname, fname)
+
+
+def test_variant_count_matches_the_header():
+    import paper_1607_01650_gb300 as dect
+    m = re.search(r"#define\s+DECT_BWD_VARIANTS\s+(\d+)", open(HEADER).read())
+    assert m and int(m.group(1)) == dect.BWD_VARIANTS
