@@ -48,7 +48,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--slices", type=int, default=16, help="slices per step per GPU")
+    ap.add_argument("--slices", type=int, default=32, help="slices per step per GPU")
     ap.add_argument("--max-iter", type=int, default=2000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -494,7 +494,7 @@ def main():
     fwd_n = sum(p.fwd_launches for p in state["prof"])
     bwd_n = sum(p.bwd_launches for p in state["prof"])
     p0 = state["prof"][-1]
-    width = min(32, 1 << (2 * S - 1).bit_length())
+    width = min(64, 1 << (2 * S - 1).bit_length())
     choice, _ = plan.tuning(width)
     names = ["k_bwd<tile4>", "k_bwd<tile8>", "k_bwd<tile16>", "k_bwd_win", "k_bwd<1k,8x8>", "k_bwd<1k,16x8>"]
     bwd_name = names[choice] if 0 <= choice < len(names) else "k_bwd"
@@ -533,7 +533,7 @@ def main():
                    "all_converged": bool(state.get("conv", False)),
                    "mean_pcg_iterations": float(np.mean(state["pls_iters"])),
                    "plan_seconds": round(plan_s, 3), "nnz": plan.nnz,
-                   "bwd_autotune": dict(zip(("choice", "us"), plan.tuning(min(32, 1 << (2 * S - 1).bit_length())))),
+                   "bwd_autotune": dict(zip(("choice", "us"), plan.tuning(min(64, 1 << (2 * S - 1).bit_length())))),
                    "l2": "inputs larger than L2 (tables %.0f MB)" % (plan.table_bytes / 1e6),
                    "parallelism": "replicas" if world > 1 else "1 GPU"},
         "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,

@@ -298,13 +298,13 @@ dect_status dect_adm_tv_ex(const dect_plan *plan, const float *m, float *x, int 
 
 /*
  * Autotuner record of a plan: the A^T variant that dect_adm_tv chose for a
- * batch of `images` interleaved channels (2, 4, 8, 16 or 32; a call with c
- * channels uses the next of these widths >= min(c, 32)), and the measured
+ * batch of `images` interleaved channels (2, 4, 8, 16, 32 or 64; a call with
+ * c channels uses the next of these widths >= min(c, 64)), and the measured
  * median time of each variant in microseconds (-1 = not available):
  *   0-2 L1-cached gather with 4x4 / 8x8 / 16x16 pixel tiles per 256-thread block,
  *   3   shared-memory sinogram windows (cp.async staged),
  *   4-5 L1-cached gather, one 1024-thread block per SM, tiles of two / four
- *       block steps (8x8 / 16x8 pixels at 32 channels, 8x16 / 16x16 below).
+ *       block steps (8x8 / 16x8 pixels at 32 and 64 channels, 8x16 / 16x16 below).
  * *choice = -1 until an ADM call with that width has run.  Host memory:
  * us has DECT_BWD_VARIANTS elements.
  */

@@ -15,7 +15,7 @@
 // A^T (of r) and one A (of G).  The lambda step of iteration k is applied at
 // the start of iteration k+1, where grad f^{k+1} is formed anyway.
 //
-// Layout: up to 32 channels are interleaved pixel-major, f[pixel][NB], so a
+// Layout: up to 64 channels are interleaved pixel-major, f[pixel][NB], so a
 // table entry gathers one contiguous vector of all channels.
 //
 // Kernel sequence per iteration (captured in a CUDA graph):
@@ -755,7 +755,7 @@ void launch_bwd(const dect_plan *P, const Work &W, const AdmConst &C, int varian
 template <int NB>
 constexpr int nb_index()
 {
-    return NB == 2 ? 0 : NB == 4 ? 1 : NB == 8 ? 2 : NB == 16 ? 3 : 4;
+    return NB == 2 ? 0 : NB == 4 ? 1 : NB == 8 ? 2 : NB == 16 ? 3 : NB == 32 ? 4 : 5;
 }
 
 // Time every available A^T variant on this workspace (CUDA events, median of
@@ -1125,8 +1125,10 @@ extern "C" dect_status dect_adm_tv_ex(const dect_plan *plan, const float *m, flo
             st = run_chunk<8>(plan, mc, xc, nimg, prm, beta.data(), rc, prof, s);
         else if (nimg <= 16)
             st = run_chunk<16>(plan, mc, xc, nimg, prm, beta.data(), rc, prof, s);
-        else
+        else if (nimg <= 32)
             st = run_chunk<32>(plan, mc, xc, nimg, prm, beta.data(), rc, prof, s);
+        else
+            st = run_chunk<64>(plan, mc, xc, nimg, prm, beta.data(), rc, prof, s);
         if (st == DECT_ERR_NONFINITE) worst = st;
         else if (st != DECT_OK) return st;
     }

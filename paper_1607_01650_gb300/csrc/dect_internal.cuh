@@ -12,7 +12,7 @@
 namespace dect {
 
 constexpr int kSMs = 152;          // GB300: 2 dies x 76 SMs
-constexpr int kMaxBatchImages = 32; // images interleaved per ADM pass
+constexpr int kMaxBatchImages = 64; // images interleaved per ADM pass
 constexpr int kTablePad = 512;      // zero entries after the last row of each table
 // A^T with shared-memory sinogram windows: pixel tiles of kWinTH x kWinTW
 constexpr int kWinTH = 4, kWinTW = 4;
@@ -73,8 +73,8 @@ struct dect_plan {
     int tile_ent_max;
     // Autotuner cache: chosen A^T variant per ADM batch width (index log2(NB) - 1),
     // -1 until the first ADM call with that width has timed the candidates.
-    mutable int bwd_choice[5];
-    mutable float bwd_us[5][DECT_BWD_VARIANTS];
+    mutable int bwd_choice[6];
+    mutable float bwd_us[6][DECT_BWD_VARIANTS];
 };
 
 namespace dect {

@@ -470,7 +470,7 @@ extern "C" dect_status dect_plan_create(const dect_geometry *geom, int device, d
     p->nb = geom->n_bins;
     p->N = (int64_t)p->n * p->n;
     p->M = (int64_t)p->nv * p->nb;
-    for (int k = 0; k < 5; ++k) p->bwd_choice[k] = -1;
+    for (int k = 0; k < 6; ++k) p->bwd_choice[k] = -1;
 
     // ray end points on the host, FP64 (see file header)
     std::vector<RayPts> h(p->M);
@@ -700,6 +700,7 @@ extern "C" dect_status dect_plan_get_tuning(const dect_plan *p, int images, int 
     case 8: idx = 2; break;
     case 16: idx = 3; break;
     case 32: idx = 4; break;
+    case 64: idx = 5; break;
     default: return DECT_ERR_INVALID_ARG;
     }
     *choice = p->bwd_choice[idx];
@@ -717,6 +718,7 @@ extern "C" dect_status dect_plan_set_tuning(dect_plan *p, int images, int choice
     case 8: idx = 2; break;
     case 16: idx = 3; break;
     case 32: idx = 4; break;
+    case 64: idx = 5; break;
     default: return DECT_ERR_INVALID_ARG;
     }
     p->bwd_choice[idx] = choice;

@@ -223,7 +223,7 @@ def test_every_backprojector_variant(ns):
     plan = dect.Plan(g)
     t = oracle.table(g)
     m = np.stack([s.m for s in slices])
-    width = min(32, 1 << (2 * ns - 1).bit_length())
+    width = min(64, 1 << (2 * ns - 1).bit_length())
     prm = dect.AdmParams(mu=MU, rho=RHO, max_iter=12)
     for v in range(dect.BWD_VARIANTS):
         plan.set_tuning(width, v)
