@@ -34,6 +34,8 @@ if ROOT not in sys.path:
 import synth  # noqa: E402
 
 METRIC = "DECT slices/s to 1e-4 rel. objective at 512^2/60 views (2 energies + PLS)"
+METRIC_STRESS = "DECT slices/s, 300 ADM iterations at 1024^2/360 views (2 energies + PLS)"
+STRESS_ITERS, STRESS_I0, STRESS_SUB_VIEWS = 300, 1e5, 12
 UNIT = "slices/s"
 MU, RHO, BETA = 4.0, 256.0, (1.0, 0.6)
 TOL = 1e-4
@@ -48,21 +50,23 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--slices", type=int, default=32, help="slices per step per GPU")
+    ap.add_argument("--slices", type=int, default=None,
+                    help="slices per step per GPU (default 32; stress 16)")
     ap.add_argument("--max-iter", type=int, default=2000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--train-slices", type=int, default=1024, help="learned workload: training slices")
     ap.add_argument("--epochs", type=int, default=6, help="learned workload: training epochs")
-    ap.add_argument("--workload", default="paper", choices=["paper", "batched", "learned"],
-                    help="paper: 16 slices of 512^2/60 views per step (the headline); batched: "
+    ap.add_argument("--workload", default="paper", choices=["paper", "batched", "learned", "stress"],
+                    help="paper: 32 slices of 512^2/60 views per step (the headline); batched: "
                          "64 slices of uneven size (256^2-512^2) and view count (30-180) per step; "
-                         "learned: CNN warm start trained on 256^2 pairs, evaluated at 512^2")
+                         "learned: CNN warm start trained on 256^2 pairs, evaluated at 512^2; "
+                         "stress: 16 slices of 1024^2/360 views/1472 bins, 300 ADM iterations")
     return ap.parse_args()
 
 
-def make_inputs(geom, seeds):
-    m = np.stack([synth.make_slice(geom, s, kind="head", i0=I0).m for s in seeds]).astype(np.float32)
+def make_inputs(geom, seeds, i0=I0):
+    m = np.stack([synth.make_slice(geom, s, kind="head", i0=i0).m for s in seeds]).astype(np.float32)
     return m
 
 
@@ -196,6 +200,33 @@ def oracle_sample(geom, m_slice, iters_sample, x_for_pls):
     oracle.pls_decompose(x_for_pls[0], x_for_pls[1], pp)
     t_pls = time.perf_counter() - t0
     return t_adm, t_pls
+
+
+def oracle_sample_stress(geom, m_slice):
+    """Bounded oracle sample for the 1024^2 / 360-view workload, whose full
+    oracle table (6.9e8 entries) is too large for a timing run: the oracle
+    runs 2 ADM iterations on the same image with STRESS_SUB_VIEWS views, and
+    the 3 table passes of an iteration are scaled to 360 views.
+
+    Returns (estimated seconds per ADM iteration per energy, description)."""
+    import dataclasses as dc
+    import oracle
+    k = geom.nv // STRESS_SUB_VIEWS
+    sub = dc.replace(geom, nv=STRESS_SUB_VIEWS)
+    t = oracle.table(sub)
+    g = m_slice[0, ::k][:STRESS_SUB_VIEWS].astype(np.float64)
+    prm = oracle.AdmParams(mu=MU, rho=RHO, beta=BETA, step_rule=oracle.CAUCHY, max_iter=2, tol=0.0)
+    t0 = time.perf_counter()
+    oracle.adm_channel(t, g, prm)
+    t_it = (time.perf_counter() - t0) / 2
+    x = np.random.default_rng(0).random((geom.n, geom.n))
+    t0 = time.perf_counter()
+    oracle.project(t, x)
+    t_pass = time.perf_counter() - t0
+    est = t_it + 3 * (k - 1) * t_pass
+    return est, ("ADM iterations at 1024^2 with %d of 360 views (%.2f s each; one table pass %.2f s), "
+                 "the 3 table passes per iteration scaled by %d: %.1f s per iteration per energy, "
+                 "x 300 iterations x 2 energies" % (STRESS_SUB_VIEWS, t_it, t_pass, k, est))
 
 
 def reference_iterations():
@@ -410,18 +441,23 @@ def main():
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
 
-    geom = synth.paper_geometry()
-    S = args.slices
+    stress = args.workload == "stress"
+    geom = synth.stress_geometry() if stress else synth.paper_geometry()
+    S = args.slices or (16 if stress else 32)
     t0 = time.perf_counter()
     plan = dect.Plan(geom, device=local)
     plan_s = time.perf_counter() - t0
-    m_host = torch.from_numpy(make_inputs(geom, seeds_for(rank, S))).pin_memory()
+    m_host = torch.from_numpy(make_inputs(geom, seeds_for(rank, S), STRESS_I0 if stress else I0)).pin_memory()
     m_dev = m_host.to("cuda")
     x_dev = torch.zeros((S, 2, geom.n, geom.n), device="cuda")
     u_dev = torch.empty_like(x_dev)
     u_host = torch.empty(u_dev.shape, dtype=torch.float32).pin_memory()
-    prm = dect.AdmParams(mu=MU, rho=RHO, beta=BETA, step_rule=dect.CAUCHY, max_iter=args.max_iter,
-                         rel_obj_tol=TOL, check_every=10)
+    if stress:  # fixed iteration count, as the stress configuration states
+        prm = dect.AdmParams(mu=MU, rho=RHO, beta=BETA, step_rule=dect.CAUCHY, max_iter=STRESS_ITERS,
+                             rel_obj_tol=0.0)
+    else:
+        prm = dect.AdmParams(mu=MU, rho=RHO, beta=BETA, step_rule=dect.CAUCHY, max_iter=args.max_iter,
+                             rel_obj_tol=TOL, check_every=10)
     pp = dect.PlsParams(**PLS)
 
     state = {"iters": [], "pls_iters": [], "prof": []}
@@ -513,7 +549,17 @@ def main():
     clocks = clk.summary()
     mean_it = float(np.mean(state["iters"]))
     cpu = None
-    if world == 1 and not args.no_cpu_baseline:
+    if world == 1 and not args.no_cpu_baseline and stress:
+        import oracle
+        x_first = x_dev[0].double().cpu().numpy()
+        t_it, desc = oracle_sample_stress(geom, m_host[0].numpy())
+        t0 = time.perf_counter()
+        oracle.pls_decompose(x_first[0], x_first[1], oracle.PlsParams(
+            gamma=PLS["gamma"], tau=PLS["edge_tau"], eps=PLS["edge_eps"], max_iter=PLS["max_iter"], tol=1e-10))
+        t_pls = time.perf_counter() - t0
+        cpu = {"value": 1.0 / (2 * STRESS_ITERS * t_it + t_pls), "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": "1 slice: " + desc + ", plus one full PLS (%.2f s)" % t_pls}
+    elif world == 1 and not args.no_cpu_baseline:
         x_first = x_dev[0].double().cpu().numpy()
         t_adm, t_pls = oracle_sample(geom, m_host[0].numpy(), 3, x_first)
         sec_slice = 2 * mean_it * t_adm + t_pls
@@ -521,13 +567,18 @@ def main():
                "sample": "1 slice: 3 ADM iterations per energy (%.3f s each) scaled to the GPU run's "
                          "mean %.1f iterations, plus one full PLS (%.2f s)" % (t_adm, mean_it, t_pls)}
 
+    if stress:
+        wdesc = ("stress 1024x1024/0.25mm, 360 views over 360deg, 1472 bins x 0.3mm, SOD 500/SDD 1000, "
+                 "head phantom, I0=1e5, 300 ADM iterations (both energies) + PLS gamma 0.1")
+    else:
+        wdesc = ("paper-shaped 512x512/0.5mm, 60 views over 360deg, 736 bins x 0.6mm, "
+                 "SOD 500/SDD 1000, head phantom, I0=2e5, ADM to 1e-4 rel. objective "
+                 "(both energies) + PLS gamma 0.1")
     line = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "metric": METRIC_STRESS if stress else METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": "paper-shaped 512x512/0.5mm, 60 views over 360deg, 736 bins x 0.6mm, "
-                               "SOD 500/SDD 1000, head phantom, I0=2e5, ADM to 1e-4 rel. objective "
-                               "(both energies) + PLS gamma 0.1",
+        "config": {"workload": wdesc,
                    "slices_per_step_per_gpu": S, "mean_adm_iterations": mean_it,
                    "max_adm_iterations": int(max(state["iters"])),
                    "all_converged": bool(state.get("conv", False)),
