@@ -55,6 +55,8 @@ def parse():
     ap.add_argument("--max-iter", type=int, default=2000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--bwd-variant", type=int, default=-1,
+                    help="fix the A^T variant (0-5, see dect_plan_get_tuning) instead of autotuning")
     ap.add_argument("--train-slices", type=int, default=1024, help="learned workload: training slices")
     ap.add_argument("--epochs", type=int, default=6, help="learned workload: training epochs")
     ap.add_argument("--workload", default="paper", choices=["paper", "batched", "learned", "stress"],
@@ -98,14 +100,17 @@ def measured_peaks():
     return FALLBACK_HBM_GBS, "fallback"
 
 
+ADM_SOURCES = ("adm.cu", "dect_internal.cuh", "kernels.cuh")  # where k_tv, k_bwd*, k_fwd live
+
+
 def kernel_source_hash():
+    """Hash of the sources of the ADM kernels the roofline reports on."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1607_01650_gb300", "csrc")
-    for name in sorted(os.listdir(csrc)):
-        if name.endswith((".cu", ".cuh")):
-            with open(os.path.join(csrc, name), "rb") as f:
-                h.update(name.encode())
-                h.update(f.read())
+    for name in ADM_SOURCES:
+        with open(os.path.join(csrc, name), "rb") as f:
+            h.update(name.encode())
+            h.update(f.read())
     return h.hexdigest()[:16]
 
 
@@ -447,6 +452,8 @@ def main():
     t0 = time.perf_counter()
     plan = dect.Plan(geom, device=local)
     plan_s = time.perf_counter() - t0
+    if args.bwd_variant >= 0:
+        plan.set_tuning(min(64, 1 << (2 * S - 1).bit_length()), args.bwd_variant)
     m_host = torch.from_numpy(make_inputs(geom, seeds_for(rank, S), STRESS_I0 if stress else I0)).pin_memory()
     m_dev = m_host.to("cuda")
     x_dev = torch.zeros((S, 2, geom.n, geom.n), device="cuda")
