@@ -66,7 +66,7 @@ struct AdmDev {
     // per-channel scalars
     double *red;       // [R_COUNT][NB] reduction results
     double *part;      // [C_COUNT][2][kGrid][NB] block partials, per kernel
-    unsigned *ctr;     // [C_COUNT] last-block counters
+    unsigned *ctr;     // [C_COUNT] last-block counters, then the k_tv tile counter
     double *alpha;     // [NB] step applied by the next k_tv
     double *c_prev;    // [NB]
     double *phi_prev;  // [NB]
@@ -150,23 +150,23 @@ __device__ __forceinline__ float nonneg_step(float f, float a, float g, bool cla
 // the step is empty and f^0 is used as given), and r and |r|^2 are left to
 // k_fwd in mode 2.
 //
-// Traversal: a block takes tiles of W columns x H rows.  Thread (slot q,
-// vector vl) owns column j = j0 - 1 + q of the tile (slot 0 is the column
-// left of the tile: computed, never written) and walks down rows i0 - 1 ..
-// i0 + H - 1 (row i0 - 1 is only computed).  The updated f and G of the pixel
-// above are the thread's own values from the previous row, held in
-// registers; those of the pixel to the left come from the neighbouring slot
-// through shared memory (double-buffered by row parity: one barrier per
-// row).  Each row's f and G are loaded one row ahead.  Every stored array is
+// Traversal: blocks claim tiles of W columns x H rows from a counter (the
+// last block resets it).  Thread (slot q, vector vl) owns column
+// j = j0 - 1 + q of the tile (slot 0 is the column left of the tile:
+// computed, never written) and walks down rows i0 - 1 .. i0 + H - 1 (row
+// i0 - 1 is only computed).  The updated f and G of the pixel above are the
+// thread's own values from the previous row, held in registers; those of the
+// pixel to the left come from the neighbouring slot through shared memory
+// (double-buffered by row parity: one barrier per row).  Each row's f, G and
+// multiplier (p, or lambda) are loaded one row ahead.  Every stored array is
 // read and written once, in 16-byte vectors.
 // ---------------------------------------------------------------------------
 template <int NB>
 struct TvShape {
     static constexpr int VW = Batch<NB>::VW, CPB = Batch<NB>::CPB;
-    static constexpr int W = CPB >= 8 ? 32 : (CPB >= 2 ? 64 : 128);  // tile columns
-    static constexpr int H = 32;                                       // tile rows
-    static constexpr int RND = NB > 32 ? NB : 32;
-    static constexpr int BLK = (((W + 1) * CPB + RND - 1) / RND) * RND;  // threads per block
+    static constexpr int BLK = NB > 32 ? 512 : 256;  // threads per block
+    static constexpr int W = BLK / CPB - 1;           // tile columns (+1 halo slot)
+    static constexpr int H = 16;                      // tile rows
     static constexpr size_t XS_BYTES = sizeof(float) * 2 * 2 * (W + 1) * NB;
     static constexpr size_t RED_BYTES = sizeof(double) * reduce_smem_doubles<NB, BLK>(2);
     static constexpr size_t SMEM = XS_BYTES > RED_BYTES ? XS_BYTES : RED_BYTES;
@@ -198,29 +198,46 @@ __global__ void __launch_bounds__(TvShape<NB>::BLK) k_tv(const float *__restrict
     const int64_t sN = C.N * NB;  // component stride of lam, z, p
     const int64_t row = (int64_t)C.n * NB;
     const int tiles_x = (C.n + W - 1) / W, ntiles = tiles_x * ((C.n + H - 1) / H);
-    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    __shared__ int s_tile;
+    const float *lsrc = C.xi_is_rho ? p : lam;  // the multiplier rows read per pixel
+    const bool need_l = !final_pass;
+    for (;;) {
+        if (threadIdx.x == 0) s_tile = (int)atomicAdd(D.ctr + C_COUNT, 1u);
+        __syncthreads();
+        const int tile = s_tile;
+        if (tile >= ntiles) break;
         const int j0 = (tile % tiles_x) * W, i0 = (tile / tiles_x) * H;
         const int j = j0 - 1 + slot;
         const bool colok = in_tile && j >= 0 && j < C.n;
         const bool owner = colok && slot > 0;
         const int ibeg = i0 > 0 ? i0 - 1 : 0, iend = min(i0 + H, C.n);
-        Vec<VW> fn, gn, fup, gup;
+        Vec<VW> fn, gn, ln0, ln1, fup, gup;
         fn.zero();
         gn.zero();
+        ln0.zero();
+        ln1.zero();
         fup.zero();
         gup.zero();
         if (colok) {
             const int64_t o = ((int64_t)ibeg * C.n + j) * NB + vl * VW;
             fn = ld_v<VW>(f_in + o);
             gn = ld_v<VW>(G + o);
+            if (need_l && owner && ibeg >= i0) {
+                ln0 = ld_v<VW>(lsrc + o);
+                ln1 = ld_v<VW>(lsrc + sN + o);
+            }
         }
         for (int i = ibeg; i < iend; ++i) {
             const int par = i & 1;
             const int64_t o = ((int64_t)i * C.n + j) * NB + vl * VW;
-            Vec<VW> fc = fn, gc = gn;
+            Vec<VW> fc = fn, gc = gn, lc0 = ln0, lc1 = ln1;
             if (colok && i + 1 < iend) {
                 fn = ld_v<VW>(f_in + o + row);
                 gn = ld_v<VW>(G + o + row);
+                if (need_l && owner) {
+                    ln0 = ld_v<VW>(lsrc + o + row);
+                    ln1 = ld_v<VW>(lsrc + sN + o + row);
+                }
             }
 #pragma unroll
             for (int c = 0; c < VW; ++c) fc.v[c] = nonneg_step(fc.v[c], a.v[c], gc.v[c], clamp);
@@ -246,23 +263,15 @@ __global__ void __launch_bounds__(TvShape<NB>::BLK) k_tv(const float *__restrict
                     fl = fc;
                     gl_ = gc;
                 }
-                Vec<VW> l0, l1, z0, z1;
-                if (!final_pass) {
-                    if (C.xi_is_rho) {
-                        // With xi = rho the multiplier step of Eq. (7) and
-                        // p^{k-1} = rho(grad f^{k-1} - z^k) - lambda^{k-1} give
-                        // lambda^k = xi alpha^{k-1} grad G^{k-1} - p^{k-1}: neither
-                        // lambda nor z has to be stored (l0, l1 carry p^{k-1} here).
-                        l0 = ld_v<VW>(p + o);
-                        l1 = ld_v<VW>(p + sN + o);
-                    } else {
-                        l0 = ld_v<VW>(lam + o);
-                        l1 = ld_v<VW>(lam + sN + o);
-                        if (k > 0) {
-                            z0 = ld_v<VW>(z + o);
-                            z1 = ld_v<VW>(z + sN + o);
-                        }
-                    }
+                // With xi = rho the multiplier step of Eq. (7) and
+                // p^{k-1} = rho(grad f^{k-1} - z^k) - lambda^{k-1} give
+                // lambda^k = xi alpha^{k-1} grad G^{k-1} - p^{k-1}: neither
+                // lambda nor z has to be stored (l0, l1 carry p^{k-1} then;
+                // otherwise lambda^{k-1}).
+                Vec<VW> l0 = lc0, l1 = lc1, z0, z1;
+                if (!final_pass && !C.xi_is_rho && k > 0) {
+                    z0 = ld_v<VW>(z + o);
+                    z1 = ld_v<VW>(z + sN + o);
                 }
                 Vec<VW> p0, p1, d0, d1;
 #pragma unroll
@@ -335,7 +344,7 @@ __global__ void __launch_bounds__(TvShape<NB>::BLK) k_tv(const float *__restrict
             fup = fc;
             gup = gc;
         }
-        __syncthreads();  // the next tile's first row reuses the exchange buffer
+        __syncthreads();  // the next tile's first row reuses the exchange buffer (and s_tile)
     }
     const int64_t rn = C.nonneg ? 0 : C.M * CPB;  // with the projection r is rebuilt by k_fwd
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -349,8 +358,10 @@ __global__ void __launch_bounds__(TvShape<NB>::BLK) k_tv(const float *__restrict
         }
         st_v<VW>(rp, rv);
     }
-    reduce_images<NB, 2, S::BLK>(acc, part_of<NB>(D, C_TV), D.red + R_TV * NB, D.ctr + C_TV,
-                                 reinterpret_cast<double *>(sbuf));
+    if (reduce_images<NB, 2, S::BLK>(acc, part_of<NB>(D, C_TV), D.red + R_TV * NB, D.ctr + C_TV,
+                                     reinterpret_cast<double *>(sbuf)) &&
+        threadIdx.x == 0)
+        D.ctr[C_COUNT] = 0u;  // every block has left the tile loop: reset the tile counter
 }
 
 // G = mu A^T r + grad^T p over the pixel-major table.  A block of BLK
@@ -941,7 +952,7 @@ dect_status run_chunk(const dect_plan *P, const float *m, float *x, int nimg,
         W.beta = (float *)take(64 * 4);
         W.dbl = (double *)take(ndbl * 8);
         W.ints = (int *)take(nint * 4);
-        W.ctr = (unsigned *)take(C_COUNT * 4);
+        W.ctr = (unsigned *)take((C_COUNT + 1) * 4);  // + the k_tv tile counter
         return o;
     };
     const size_t bytes = layout(nullptr);
