@@ -395,7 +395,7 @@ __global__ void __launch_bounds__(BLK) k_bwd(const int64_t *__restrict__ colptr,
                 b = colptr[pix];
                 e = colptr[pix + 1];
             }
-            Vec<VW> acc = row_dot<NB, G_, true>(tent, b, e, r, 0, lr);
+            Vec<VW> acc = row_dot<NB, G_, true, true>(tent, b, e, r, 0, lr);
             if (ok && grp == 0) {
                 const int64_t o = pix * NB + vl * VW;
                 Vec<VW> p0 = ld_v<VW>(p + o), p1 = ld_v<VW>(p + sN + o), pd, pr;

@@ -86,19 +86,42 @@ __device__ __forceinline__ Entry ld_entry(const Entry *p)
 // Deterministic per-image reduction of K quantities at once: every thread
 // holds K vectors of VW partial values for images (lane % CPB) * VW + c.
 // Values are summed in FP32 inside a warp and in FP64 across warps and
-// blocks, always in the same order.  The block that finishes last writes the
-// grid totals to out[k][img] and returns true (in every thread of that
-// block); `counter` is reset for the next launch.  Blocks have BLOCK threads;
-// smem must hold reduce_smem_doubles<NB, BLOCK>(K) doubles; part holds
-// K * gridDim.x * NB doubles.
+// blocks, always in the same order: the warps of a block add into RED_SLOTS
+// shared slots in rounds of RED_SLOTS warps, then the slots are added.  The
+// block that finishes last writes the grid totals to out[k][img] and
+// returns true (in every thread of that block); `counter` is reset for the
+// next launch.  Blocks have BLOCK threads; smem must hold
+// reduce_smem_doubles<NB, BLOCK>(K) doubles (kept small: the table kernels
+// need the L1 that shared memory would take); part holds K * gridDim.x * NB
+// doubles.
 // ---------------------------------------------------------------------------
+template <int BLOCK>
+__host__ __device__ constexpr int red_slots()
+{
+    return (BLOCK / 32) % 8 == 0 ? 8 : BLOCK / 32;
+}
+
+template <int NB, int BLOCK>
+__host__ __device__ constexpr int red_split()
+{
+    return BLOCK / NB < 8 ? BLOCK / NB : 8;
+}
+
+template <int NB, int BLOCK = 256>
+__host__ __device__ constexpr int reduce_smem_doubles(int K)
+{
+    return K * (red_slots<BLOCK>() > red_split<NB, BLOCK>() ? red_slots<BLOCK>() : red_split<NB, BLOCK>()) * NB;
+}
+
 template <int NB, int K, int BLOCK = 256>
 __device__ __forceinline__ bool reduce_images(Vec<Batch<NB>::VW> (&v)[K], double *__restrict__ part,
                                               double *__restrict__ out, unsigned *counter,
                                               double *smem)
 {
     constexpr int VW = Batch<NB>::VW, CPB = Batch<NB>::CPB;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    constexpr int NW = BLOCK / 32, SL = red_slots<BLOCK>(), SPLIT = red_split<NB, BLOCK>();
+    static_assert(NW % SL == 0 && BLOCK % NB == 0, "reduce_images: block shape");
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const size_t pstride = (size_t)gridDim.x * NB;
 #pragma unroll
     for (int q = 0; q < K; ++q)
@@ -106,16 +129,22 @@ __device__ __forceinline__ bool reduce_images(Vec<Batch<NB>::VW> (&v)[K], double
         for (int off = CPB; off < 32; off <<= 1)
 #pragma unroll
             for (int c = 0; c < VW; ++c) v[q].v[c] += __shfl_xor_sync(0xffffffffu, v[q].v[c], off);
-    if (lane < CPB)
+#pragma unroll 1
+    for (int rnd = 0; rnd < NW / SL; ++rnd) {
+        if (warp / SL == rnd && lane < CPB)
 #pragma unroll
-        for (int q = 0; q < K; ++q)
+            for (int q = 0; q < K; ++q)
 #pragma unroll
-            for (int c = 0; c < VW; ++c) smem[(q * nw + warp) * NB + lane * VW + c] = (double)v[q].v[c];
-    __syncthreads();
+                for (int c = 0; c < VW; ++c) {
+                    double &d = smem[(q * SL + warp % SL) * NB + lane * VW + c];
+                    d = (rnd == 0 ? 0.0 : d) + (double)v[q].v[c];
+                }
+        __syncthreads();
+    }
     if (threadIdx.x < K * NB) {
         const int q = threadIdx.x / NB, img = threadIdx.x % NB;
         double s = 0.0;
-        for (int w = 0; w < nw; ++w) s += smem[(q * nw + w) * NB + img];
+        for (int w = 0; w < SL; ++w) s += smem[(q * SL + w) * NB + img];
         part[q * pstride + (size_t)blockIdx.x * NB + img] = s;
     }
     __threadfence();
@@ -127,19 +156,20 @@ __device__ __forceinline__ bool reduce_images(Vec<Batch<NB>::VW> (&v)[K], double
     __threadfence();
     // grid total: SPLIT threads per image each sum a fixed stride of the block
     // partials, then one thread per image adds the SPLIT sub-sums in order
-    constexpr int SPLIT = BLOCK / NB;
-    static_assert(SPLIT * NB == BLOCK, "reduce_images: BLOCK must be a multiple of NB");
     const int img = threadIdx.x % NB, sub = threadIdx.x / NB;
-    double s[K];
+    double sv[K];
 #pragma unroll
     for (int q = 0; q < K; ++q) {
-        s[q] = 0.0;
+        sv[q] = 0.0;
+        if (sub < SPLIT) {
 #pragma unroll 4
-        for (unsigned b = sub; b < gridDim.x; b += SPLIT) s[q] += __ldcg(&part[q * pstride + (size_t)b * NB + img]);
+            for (unsigned b = sub; b < gridDim.x; b += SPLIT) sv[q] += __ldcg(&part[q * pstride + (size_t)b * NB + img]);
+        }
     }
     __syncthreads();  // smem is reused below
+    if (sub < SPLIT)
 #pragma unroll
-    for (int q = 0; q < K; ++q) smem[(q * SPLIT + sub) * NB + img] = s[q];
+        for (int q = 0; q < K; ++q) smem[(q * SPLIT + sub) * NB + img] = sv[q];
     __syncthreads();
     if (threadIdx.x < K * NB) {
         const int q = threadIdx.x / NB, im = threadIdx.x % NB;
@@ -152,25 +182,21 @@ __device__ __forceinline__ bool reduce_images(Vec<Batch<NB>::VW> (&v)[K], double
     return true;
 }
 
-template <int NB, int BLOCK = 256>
-__host__ __device__ constexpr int reduce_smem_doubles(int K)
-{
-    return K * (BLOCK / 32 > BLOCK / NB ? BLOCK / 32 : BLOCK / NB) * NB;
-}
-
 // ---------------------------------------------------------------------------
 // Row kernel core: one row (a ray of the ray-major table or a pixel of the
 // pixel-major table) is handled by G lanes.  The G lanes load the row's
 // entries cooperatively, G at a time (coalesced, streamed past L1), one batch
 // ahead of use, so a table entry's DRAM latency overlaps the gathers of the
-// previous batch.  Inside a batch, entry j is broadcast by shuffle to the
-// LPE = CPB lanes that gather its VW-wide vectors of the NB images; the
+// previous batch.  Inside a batch, entry j is broadcast (by shuffle, or with
+// SBC through a per-warp shared-memory slot, 8 KB per block, when a lane
+// holds one entry per batch) to the LPE = CPB lanes that gather its VW-wide
+// vectors of the NB images; the
 // batch's EG = G / LPE entry groups give every lane LPE independent gathers.
 // Groups are summed by a fixed xor-butterfly: the result is bitwise
 // reproducible.  After the call, the lanes with group == 0 hold the row's sums.
 // Every lane of the warp must call it (rows past the end pass b = e).
 // ---------------------------------------------------------------------------
-template <int NB, int G, typename Gather>
+template <int NB, int G, typename Gather, bool SBC = false>
 __device__ __forceinline__ Vec<Batch<NB>::VW> row_dot_g(const Entry *__restrict__ ent, int64_t b,
                                                         int64_t e, int lr, Gather gather)
 {
@@ -178,7 +204,7 @@ __device__ __forceinline__ Vec<Batch<NB>::VW> row_dot_g(const Entry *__restrict_
     constexpr int U = LPE >= 4 ? 1 : 4 / LPE;  // batches in flight per step
     static_assert(G % LPE == 0 && G <= 32, "bad row split");
     const int grp = lr / LPE, vl = lr % LPE;
-    const unsigned lane = threadIdx.x & 31;
+    const unsigned lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const unsigned gbase = lane & ~(unsigned)(G - 1);  // first lane of this row group
     Vec<VW> acc;
     acc.zero();
@@ -198,17 +224,34 @@ __device__ __forceinline__ Vec<Batch<NB>::VW> row_dot_g(const Entry *__restrict_
             const int64_t k = base + (U + u) * G + lr;
             nxt[u] = k < e ? ld_entry(ent + k) : make_int2(0, 0);
         }
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
+        if constexpr (SBC && U == 1) {
+            // one batch per warp: broadcast through shared memory, one 8-byte
+            // load per round instead of two shuffles
+            __shared__ Entry s_ent[32][32];  // per-warp entry batch
+            __syncwarp();
+            s_ent[warp][lane] = cur[0];
+            __syncwarp();
 #pragma unroll
             for (int j = 0; j < G / EG; ++j) {
-                const unsigned srcl = gbase + j * EG + grp;
-                const int pix = __shfl_sync(0xffffffffu, cur[u].x, srcl);
-                const float w = __int_as_float(__shfl_sync(0xffffffffu, cur[u].y, srcl));
+                const Entry en = s_ent[warp][gbase + j * EG + grp];
                 // padded entries carry w = 0 and index 0: a valid address, no contribution
-                const Vec<VW> xv = gather(pix, vl);
+                const Vec<VW> xv = gather(en.x, vl);
+                const float w = __int_as_float(en.y);
 #pragma unroll
                 for (int c = 0; c < VW; ++c) acc.v[c] = fmaf(w, xv.v[c], acc.v[c]);
+            }
+        } else {
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+#pragma unroll
+                for (int j = 0; j < G / EG; ++j) {
+                    const unsigned srcl = gbase + j * EG + grp;
+                    const int pix = __shfl_sync(0xffffffffu, cur[u].x, srcl);
+                    const float w = __int_as_float(__shfl_sync(0xffffffffu, cur[u].y, srcl));
+                    const Vec<VW> xv = gather(pix, vl);
+#pragma unroll
+                    for (int c = 0; c < VW; ++c) acc.v[c] = fmaf(w, xv.v[c], acc.v[c]);
+                }
             }
         }
 #pragma unroll
@@ -256,13 +299,13 @@ struct GatherShared {  // interleaved [index][NB] in shared memory
     }
 };
 
-template <int NB, int G, bool IL>
+template <int NB, int G, bool IL, bool SBC = false>
 __device__ __forceinline__ Vec<Batch<NB>::VW> row_dot(const Entry *__restrict__ ent, int64_t b,
                                                       int64_t e, const float *__restrict__ src,
                                                       int64_t src_stride, int lr, int nimg = NB)
 {
     if constexpr (IL)
-        return row_dot_g<NB, G>(ent, b, e, lr, GatherIL<NB>{src});
+        return row_dot_g<NB, G, GatherIL<NB>, SBC>(ent, b, e, lr, GatherIL<NB>{src});
     else
         return row_dot_g<NB, G>(ent, b, e, lr, GatherPlanar<NB>{src, src_stride, nimg});
 }
