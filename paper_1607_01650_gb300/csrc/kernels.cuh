@@ -47,6 +47,34 @@ __device__ __forceinline__ Vec<VW> ld_il(const float *__restrict__ p)
     return r;
 }
 
+// Gather of read-only data that other rows of the same launch will gather
+// again: kept in L1 and in L2 with evict-last priority, so that the streamed
+// table entries (evict-first) are the lines that make room.
+__device__ __forceinline__ unsigned long long l2_evict_last_policy()
+{
+    unsigned long long pol;
+    asm("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
+    return pol;
+}
+
+template <int VW>
+__device__ __forceinline__ Vec<VW> ld_gather(const float *__restrict__ p, unsigned long long pol)
+{
+    Vec<VW> r;
+    if constexpr (VW == 4) {
+        asm("ld.global.nc.L1::evict_last.L2::cache_hint.v4.f32 {%0,%1,%2,%3}, [%4], %5;"
+            : "=f"(r.v[0]), "=f"(r.v[1]), "=f"(r.v[2]), "=f"(r.v[3])
+            : "l"(p), "l"(pol));
+    } else if constexpr (VW == 2) {
+        asm("ld.global.nc.L1::evict_last.L2::cache_hint.v2.f32 {%0,%1}, [%2], %3;"
+            : "=f"(r.v[0]), "=f"(r.v[1])
+            : "l"(p), "l"(pol));
+    } else {
+        asm("ld.global.nc.L1::evict_last.L2::cache_hint.f32 %0, [%1], %2;" : "=f"(r.v[0]) : "l"(p), "l"(pol));
+    }
+    return r;
+}
+
 // plain (coherent) load, for data written earlier in the same kernel sequence
 template <int VW>
 __device__ __forceinline__ Vec<VW> ld_v(const float *p)
@@ -268,9 +296,10 @@ __device__ __forceinline__ Vec<Batch<NB>::VW> row_dot_g(const Entry *__restrict_
 template <int NB>
 struct GatherIL {  // interleaved [index][NB] in global memory
     const float *src;
+    unsigned long long pol = l2_evict_last_policy();
     __device__ __forceinline__ Vec<Batch<NB>::VW> operator()(int pix, int vl) const
     {
-        return ld_il<Batch<NB>::VW>(src + (int64_t)pix * NB + vl * Batch<NB>::VW);
+        return ld_gather<Batch<NB>::VW>(src + (int64_t)pix * NB + vl * Batch<NB>::VW, pol);
     }
 };
 template <int NB>
