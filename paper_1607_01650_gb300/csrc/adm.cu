@@ -1103,8 +1103,10 @@ dect_status run_chunk(const dect_plan *P, const float *m, float *x, int nimg,
     if (err == cudaSuccess) err = cudaEventRecord(ev, cs);
     if (err == cudaSuccess) err = cudaStreamWaitEvent(s, ev, 0);
     if (prof) {
+        // A: table + row pointers, G read, q written
         prof->table_bytes_fwd = 8 * P->nnz + 8 * (P->M + 1) + 4LL * NB * (P->N + P->M);
-        prof->table_bytes_bwd = 8 * P->nnz + 8 * (P->N + 1) + 4LL * NB * (P->M + 4 * P->N);
+        // A^T: table + column pointers, r and the two components of p read, G written
+        prof->table_bytes_bwd = 8 * P->nnz + 8 * (P->N + 1) + 4LL * NB * (P->M + 3 * P->N);
     }
 
     std::vector<double> hred(R_COUNT * NB), hrel(NB);
