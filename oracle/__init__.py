@@ -89,6 +89,8 @@ def _load():
             "orc_adm_run": (C.c_int, [C.c_int, C.c_int64, i64, i32, d, d,
                                       C.POINTER(_AdmParams), d, d, d]),
             "orc_shrink4": (None, [C.c_int64, d, d, C.c_double, d, d]),
+            "orc_fbp_filter": (None, [G, d, d]),
+            "orc_fbp": (None, [G, d, d]),
             "orc_tv_joint": (C.c_double, [C.c_int, d]),
             "orc_objective_joint": (C.c_double, [C.c_int, C.c_int64, i64, i32, d, d, C.c_double, d]),
             "orc_adm_joint_iterate": (C.c_double, [C.c_int, C.c_int64, i64, i32, d, d,
@@ -340,6 +342,27 @@ def adm_dual(t: Table, m_he, prm: AdmParams, x0=None):
         xs.append(f / b)
         its.append(k)
     return np.stack(xs), its
+
+
+# ---------------------------------------------------------------------------
+# Fan-beam FBP (the analytic reconstruction of Sec. 2.4 and Sec. 3; textbook
+# algorithm for an equally spaced flat detector over 360 degrees)
+# ---------------------------------------------------------------------------
+
+def fbp_filter(geom, p) -> np.ndarray:
+    """Cosine-weighted, ramp-filtered projections [nv][nb] (see dect_oracle.c)."""
+    p = _f64(p).reshape(geom.nv, geom.nb)
+    qf = np.zeros_like(p)
+    _load().orc_fbp_filter(C.byref(_geom(geom)), _d(p), _d(qf))
+    return qf
+
+
+def fbp(geom, p) -> np.ndarray:
+    """FBP image [n][n] from projections [nv][nb]."""
+    p = _f64(p).reshape(geom.nv, geom.nb)
+    f = np.zeros((geom.n, geom.n))
+    _load().orc_fbp(C.byref(_geom(geom)), _d(p), _d(f))
+    return f
 
 
 # ---------------------------------------------------------------------------

@@ -413,6 +413,96 @@ int orc_adm_run(int n, int64_t m, const int64_t *rowptr, const int32_t *idx, con
 }
 
 /* ------------------------------------------------------------------------ */
+/* Fan-beam filtered backprojection (the analytic reconstruction of         */
+/* Sec. 2.4 and Sec. 3), here the textbook algorithm for a flat detector    */
+/* with equally spaced bins over a full 360-degree scan (Kak and Slaney,    */
+/* Principles of Computerized Tomographic Imaging, ch. 3).  Steps:          */
+/*  1. bins moved to a virtual detector through the isocentre:              */
+/*     s_b = u_b SOD / SDD, spacing ds = pitch SOD / SDD;                   */
+/*  2. cosine pre-weight q = p SOD / sqrt(SOD^2 + s_b^2);                   */
+/*  3. ramp filter, the band-limited (Ram-Lak) kernel sampled at ds:        */
+/*     h(0) = 1 / (4 ds^2), h(k) = 0 for even k != 0,                       */
+/*     h(k) = -1 / (pi^2 k^2 ds^2) for odd k;  qf(b) = ds sum_k q(k) h(b-k);*/
+/*  4. backprojection: for a point P and view v with source S, central-ray  */
+/*     direction c and lateral direction e (increasing bin index), with     */
+/*     d = P - S, L = d.c, the ray through P meets the virtual detector at  */
+/*     s = (d.e) SOD / L; f(P) = sum_v (dtheta / 2) (SOD / L)^2 qf(v, s),   */
+/*     qf interpolated linearly between bins and 0 outside them.  The 1/2   */
+/*     counts each line twice over 360 degrees.                             */
+/* ------------------------------------------------------------------------ */
+
+/* Ramp-filtered, cosine-weighted projections qf [nv][nb] (steps 1-3). */
+void orc_fbp_filter(const orc_geom *g, const double *p, double *qf)
+{
+    const int nb = g->nb;
+    const double scale = g->sod / g->sdd, ds = g->pitch * scale;
+    double *q = (double *)malloc(sizeof(double) * (size_t)nb);
+    double *h = (double *)malloc(sizeof(double) * (size_t)(2 * nb - 1));
+    const double pi = 3.14159265358979323846;
+    for (int k = -(nb - 1); k <= nb - 1; ++k) {
+        double v;
+        if (k == 0) v = 1.0 / (4.0 * ds * ds);
+        else if (k % 2 == 0) v = 0.0;
+        else v = -1.0 / (pi * pi * (double)k * (double)k * ds * ds);
+        h[k + nb - 1] = v;
+    }
+    for (int v = 0; v < g->nv; ++v) {
+        for (int b = 0; b < nb; ++b) {
+            double u = ((double)b - 0.5 * (double)(nb - 1)) * g->pitch + g->det_offset;
+            double sb = u * scale;
+            q[b] = p[(int64_t)v * nb + b] * g->sod / sqrt(g->sod * g->sod + sb * sb);
+        }
+        for (int b = 0; b < nb; ++b) {
+            double acc = 0.0;
+            for (int k = 0; k < nb; ++k) acc += q[k] * h[b - k + nb - 1];
+            qf[(int64_t)v * nb + b] = ds * acc;
+        }
+    }
+    free(q);
+    free(h);
+}
+
+/* FBP image f [n][n] (row = y, column = x) from projections p [nv][nb]. */
+void orc_fbp(const orc_geom *g, const double *p, double *f)
+{
+    const int n = g->n, nb = g->nb;
+    const double scale = g->sod / g->sdd, ds = g->pitch * scale;
+    const double s0 = (-0.5 * (double)(nb - 1) * g->pitch + g->det_offset) * scale;
+    const double dth = g->arc / (double)g->nv;
+    double *qf = (double *)malloc(sizeof(double) * (size_t)g->nv * (size_t)nb);
+    orc_fbp_filter(g, p, qf);
+    for (int64_t i = 0; i < (int64_t)n * n; ++i) f[i] = 0.0;
+    const double lo = -0.5 * (double)n * g->px;
+    for (int v = 0; v < g->nv; ++v) {
+        double th = g->start + (double)v * dth;
+        double cth = cos(th), sth = sin(th);
+        double Sx = g->sod * cth, Sy = g->sod * sth;
+        double cx = -cth, cy = -sth;      /* central ray, source -> isocentre */
+        double ex = -sth, ey = cth;       /* lateral, increasing bin index    */
+        for (int i = 0; i < n; ++i) {
+            double y = lo + ((double)i + 0.5) * g->px;
+            for (int j = 0; j < n; ++j) {
+                double x = lo + ((double)j + 0.5) * g->px;
+                double dx = x - Sx, dy = y - Sy;
+                double L = dx * cx + dy * cy;
+                double s = (dx * ex + dy * ey) * g->sod / L;
+                double t = (s - s0) / ds;     /* bin coordinate */
+                double val = 0.0;
+                if (t >= 0.0 && t <= (double)(nb - 1)) {
+                    int b0 = (int)floor(t);
+                    if (b0 > nb - 2) b0 = nb - 2;
+                    double w = t - (double)b0;
+                    val = (1.0 - w) * qf[(int64_t)v * nb + b0] + w * qf[(int64_t)v * nb + b0 + 1];
+                }
+                double wgt = g->sod / L;
+                f[(int64_t)i * n + j] += 0.5 * dth * wgt * wgt * val;
+            }
+        }
+    }
+    free(qf);
+}
+
+/* ------------------------------------------------------------------------ */
 /* Joint (channel-coupled) TV on the combined image f = (f_h, f_l), Eq. (4)  */
 /* read with the TV norm taken over both channels at every pixel:           */
 /*   Phi(f) = sum_p |(grad f_h, grad f_l)_p|_2 + mu/2 sum_c |A f_c - g_c|^2  */
