@@ -16,6 +16,7 @@ reduced (max over ranks).  Rank 0 prints one JSON line.
 from __future__ import annotations
 
 import argparse
+import dataclasses
 import hashlib
 import json
 import os
@@ -59,11 +60,12 @@ def parse():
                     help="fix the A^T variant (0-5, see dect_plan_get_tuning) instead of autotuning")
     ap.add_argument("--train-slices", type=int, default=1024, help="learned workload: training slices")
     ap.add_argument("--epochs", type=int, default=6, help="learned workload: training epochs")
-    ap.add_argument("--workload", default="paper", choices=["paper", "batched", "learned", "stress"],
+    ap.add_argument("--workload", default="paper", choices=["paper", "batched", "learned", "stress", "fbp"],
                     help="paper: 32 slices of 512^2/60 views per step (the headline); batched: "
                          "64 slices of uneven size (256^2-512^2) and view count (30-180) per step; "
                          "learned: CNN warm start trained on 256^2 pairs, evaluated at 512^2; "
-                         "stress: 16 slices of 1024^2/360 views/1472 bins, 300 ADM iterations")
+                         "stress: 16 slices of 1024^2/360 views/1472 bins, 300 ADM iterations; "
+                         "fbp: the paper workload warm-started from dect_fbp, beside the cold run")
     return ap.parse_args()
 
 
@@ -359,6 +361,60 @@ def run_learned(args, rank, world, local):
     return 0
 
 
+def run_fbp(args, rank, world, local):
+    """FBP warm start: the headline's slices (512^2 / 60 views, 32 per step),
+    each step FBP of both energies (dect_fbp), ADM from it to the 1e-4 stop,
+    then PLS; the same steps from zero are timed beside it."""
+    import torch
+    import paper_1607_01650_gb300 as dect
+    torch.cuda.set_device(local)
+    geom = synth.paper_geometry()
+    S = args.slices or 32
+    plan = dect.Plan(geom, device=local)
+    m = torch.tensor(make_inputs(geom, seeds_for(rank, S)), device="cuda")
+    x0 = torch.empty((S, 2, geom.n, geom.n), device="cuda")
+    cold = dect.AdmParams(mu=MU, rho=RHO, beta=BETA, step_rule=dect.CAUCHY, max_iter=args.max_iter,
+                          rel_obj_tol=TOL, check_every=10)
+    warm = dataclasses.replace(cold, warm_start=True)
+    pp = dect.PlsParams(**PLS)
+    res = {}
+
+    def step(use_fbp):
+        if use_fbp:
+            dect.fbp(plan, m, x=x0)
+            x, reps = dect.adm_tv(plan, m, warm, x=x0)
+        else:
+            x, reps = dect.adm_tv(plan, m, cold)
+        dect.pls_decompose(x, pp)
+        return [r.iters for r in reps], [r.objective for r in reps]
+
+    for use_fbp in (False, True):
+        for _ in range(args.warmup):
+            step(use_fbp)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(args.steps):
+            iters, objs = step(use_fbp)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        res["fbp" if use_fbp else "cold"] = {"slices_per_s": S * args.steps / (ms / 1e3),
+                                              "mean_iterations": float(np.mean(iters)),
+                                              "max_iterations": int(max(iters)),
+                                              "mean_objective": float(np.mean(objs))}
+    line = {"metric": "DECT slices/s to 1e-4 rel. objective at 512^2/60 views, FBP warm start (2 energies + PLS)",
+            "value": res["fbp"]["slices_per_s"], "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * S / res["fbp"]["slices_per_s"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": "FBP (dect_fbp) then ADM from it, the headline's 512^2/60-view slices",
+                       "slices_per_step_per_gpu": S, "cold": res["cold"], "fbp": res["fbp"],
+                       "speedup_vs_cold": res["fbp"]["slices_per_s"] / res["cold"]["slices_per_s"]}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_batched(args, rank, world, local):
     """Uneven-slice workload: 64 slices, n in {256..512} at 0.5 mm, 30-180 views,
     bins 368 + round((n - 256) / 256 * 368) x 0.6 mm; one dect_adm_tv_groups
@@ -440,6 +496,8 @@ def main():
         return run_batched(args, rank, world, local)
     if args.workload == "learned":
         return run_learned(args, rank, world, local)
+    if args.workload == "fbp":
+        return run_fbp(args, rank, world, local)
     torch.cuda.set_device(local)
     dist = None
     if world > 1:

@@ -126,6 +126,25 @@ dect_status dect_project(const dect_plan *plan, const float *x, float *y, int ba
 dect_status dect_backproject(const dect_plan *plan, const float *y, float *x, int batch,
                              dect_stream stream);
 
+/*
+ * Fan-beam filtered backprojection of `batch` sinograms, the analytic
+ * reconstruction the paper compares against (Sec. 2.4) and shows for its
+ * real data (Sec. 3); here an initial image for dect_adm_tv (warm_start = 1).
+ * Textbook algorithm for an equally spaced flat detector: bins moved to the
+ * isocentre, cosine pre-weight SOD / sqrt(SOD^2 + s^2), Ram-Lak ramp filter
+ * at the isocentre bin spacing, back-projection with the (SOD / L)^2 weight,
+ * linear interpolation between bins, 1/2 for the double coverage of 360 deg.
+ * m: [batch][n_views][n_bins] line integrals; x: [batch][n][n] (1/mm).
+ * Device scratch (filtered sinograms) is taken from the stream-ordered
+ * allocator and returned before the call ends.  The filter and the geometry
+ * run in FP64 (the ramp filter cancels the projections' mean), the
+ * back-projection sums in FP32; deterministic.
+ * Errors: DECT_ERR_INVALID_ARG (NULL plan/pointer, batch < 0, a plan whose
+ * arc is not 2 pi, fewer than 2 bins), DECT_ERR_OOM, DECT_ERR_CUDA.
+ * batch = 0 is a no-op.
+ */
+dect_status dect_fbp(const dect_plan *plan, const float *m, float *x, int batch, dect_stream stream);
+
 /* Step rules for the f-subproblem (Eq. (9)); c(G) = |G|^2/(mu|AG|^2 + rho|grad G|^2). */
 enum { DECT_STEP_BB1 = 0,     /* alpha^k = c(G^{k-1}), alpha^0 = c(G^0) (lagged, BB-like) */
        DECT_STEP_CAUCHY = 1   /* alpha^k = c(G^k) (exact line search along -G)           */ };

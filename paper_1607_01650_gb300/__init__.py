@@ -81,6 +81,7 @@ _SIGS = {
     "dect_plan_copy_table": (C.c_int, [_P, _P, _P, _P, _P]),
     "dect_project": (C.c_int, [_P, _P, _P, C.c_int, _P]),
     "dect_backproject": (C.c_int, [_P, _P, _P, C.c_int, _P]),
+    "dect_fbp": (C.c_int, [_P, _P, _P, C.c_int, _P]),
     "dect_adm_tv": (C.c_int, [_P, _P, _P, C.c_int, C.POINTER(_AdmParams), _P, _P]),
     "dect_adm_tv_ex": (C.c_int, [_P, _P, _P, C.c_int, C.POINTER(_AdmParams), _P, _P, _P]),
     "dect_pls_decompose": (C.c_int, [_P, C.c_int, C.c_int, C.POINTER(_PlsParams), _P, _P, _P]),
@@ -261,6 +262,23 @@ def backproject(plan: Plan, y, x=None, stream=None):
     _check(load().dect_backproject(plan.handle, _ptr(y, torch.float32, plan.device),
                                    _ptr(x, torch.float32, plan.device), batch, _stream(stream)),
            "dect_backproject")
+    return x
+
+
+def fbp(plan: Plan, m, x=None, stream=None):
+    """Fan-beam FBP of m [..., nv, nb] float32 CUDA -> x [..., n, n] (1/mm); see dect_fbp.
+
+    The analytic reconstruction of Sec. 2.4 / Sec. 3, used as an initial image
+    for adm_tv (warm_start=True).  Needs a plan over a full 360-degree arc."""
+    import torch
+    g = plan.geom
+    if m.shape[-2:] != (g.nv, g.nb):
+        raise DectError("m must end in (nv, nb)")
+    batch = m.numel() // (g.nv * g.nb)
+    if x is None:
+        x = torch.empty(m.shape[:-2] + (g.n, g.n), device=m.device, dtype=torch.float32)
+    _check(load().dect_fbp(plan.handle, _ptr(m, torch.float32, plan.device),
+                           _ptr(x, torch.float32, plan.device), batch, _stream(stream)), "dect_fbp")
     return x
 
 
