@@ -55,9 +55,9 @@ def test_small_config_100_iterations():
         assert abs(reps[e].objective - phi) <= 1e-4 * phi
 
 
-@pytest.mark.parametrize("ns", [1, 3, 17])
+@pytest.mark.parametrize("ns", [1, 3, 17, 33])
 def test_batched_slices(ns):
-    """Batches exercise the 2/8/32-channel interleaved paths and the chunking over 32 channels."""
+    """Batches exercise the 2/8/64-channel interleaved paths and the chunking over 64 channels."""
     g = synth.tiny_geometry(n=48, nv=24, nb=72, px=1.0, sod=120.0, sdd=240.0)
     slices = [synth.make_slice(g, seed=100 + i, i0=1e5) for i in range(ns)]
     x, reps, outs, t = run_both(g, slices, 30)
@@ -83,7 +83,7 @@ def test_warm_start():
         assert rel_l2(x[0, e], outs[0][0][e]) <= 1e-4
 
 
-@pytest.mark.parametrize("ns", [1, 5])
+@pytest.mark.parametrize("ns", [1, 5, 20])
 def test_nonnegative_projection(ns):
     """f-step projected onto f >= 0 (x in R_+^N, Eq. (1)): parity with the
     oracle's projected iteration, a nonnegative result, and the objective
@@ -126,7 +126,7 @@ def test_nonnegative_projection_warm_start_negative():
     assert x1.min() < 0.0
 
 
-@pytest.mark.parametrize("ns,rule,xi", [(1, dect.CAUCHY, 0.0), (5, dect.CAUCHY, 0.0), (3, dect.BB1, 100.0)])
+@pytest.mark.parametrize("ns,rule,xi", [(1, dect.CAUCHY, 0.0), (5, dect.CAUCHY, 0.0), (3, dect.BB1, 100.0), (20, dect.CAUCHY, 0.0)])
 def test_joint_tv(ns, rule, xi):
     """TV over both energies of a slice (4-vector shrink, one step per slice):
     parity with the oracle's joint ADM and the slice's joint objective on
@@ -215,7 +215,7 @@ def test_paper_size_first_iterations():
             assert rel_l2(x[i, e], outs[i][0][e]) <= 1e-4
 
 
-@pytest.mark.parametrize("ns", [1, 3, 16])
+@pytest.mark.parametrize("ns", [1, 3, 16, 32])
 def test_every_backprojector_variant(ns):
     """Each A^T variant the autotuner can pick gives the oracle's result."""
     g = synth.tiny_geometry(n=52, nv=24, nb=80, px=1.0, sod=130.0, sdd=260.0)
