@@ -215,6 +215,42 @@ def test_paper_size_first_iterations():
             assert rel_l2(x[i, e], outs[i][0][e]) <= 1e-4
 
 
+def test_paper_size_bench_configuration():
+    """The benchmark's launch configuration: 32 slices (64 interleaved channels,
+    the autotuned 1024-thread table kernels) of the benchmark's inputs at
+    512^2 / 60 views / 736 bins with its parameters, 4 iterations; three of
+    the slices against the oracle."""
+    g = synth.paper_geometry()
+    S = 32
+    m = np.stack([synth.make_slice(g, seed=1000 + i, kind="head", i0=2e5).m for i in range(S)]).astype(np.float32)
+    plan = dect.Plan(g)
+    prm = dect.AdmParams(mu=4.0, rho=256.0, beta=(1.0, 0.6), max_iter=4)
+    x, reps = dect.adm_tv(plan, torch.tensor(m, device="cuda"), prm)
+    x = x.cpu().numpy()
+    assert all(r.iters == 4 for r in reps)
+    t = oracle.table(g)
+    op = oracle.AdmParams(mu=4.0, rho=256.0, beta=(1.0, 0.6), max_iter=4, step_rule=oracle.CAUCHY)
+    for i in (0, 17, 31):
+        xo, _ = oracle.adm_dual(t, m[i].astype(np.float64), op)
+        for e in range(2):
+            assert rel_l2(x[i, e], xo[e]) <= 1e-4, (i, e)
+
+
+def test_zero_data_gives_the_zero_image():
+    """m = 0: the minimiser of Eq. (4) is f = 0; no step is taken, nothing
+    becomes non-finite, and the stop test fires on the zero objective."""
+    g = synth.tiny_geometry(n=24, nv=12, nb=36)
+    plan = dect.Plan(g)
+    m = torch.zeros((2, 2, g.nv, g.nb), device="cuda")
+    x, reps = dect.adm_tv(plan, m, dect.AdmParams(mu=MU, rho=RHO, max_iter=50, rel_obj_tol=1e-4))
+    assert torch.count_nonzero(x) == 0
+    for r in reps:
+        assert r.objective == 0.0 and r.converged
+    f, k, phi, _ = oracle.adm_channel(oracle.table(g), np.zeros((g.nv, g.nb)),
+                                      oracle.AdmParams(mu=MU, rho=RHO, max_iter=5))
+    assert np.count_nonzero(f) == 0 and np.all(phi == 0.0)
+
+
 @pytest.mark.parametrize("ns", [1, 3, 16, 32])
 def test_every_backprojector_variant(ns):
     """Each A^T variant the autotuner can pick gives the oracle's result."""
