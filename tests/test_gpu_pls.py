@@ -87,3 +87,17 @@ def test_paper_size_sampled():
     op = oracle.PlsParams(gamma=0.1, tau=0.2, eps=0.05, max_iter=500, tol=1e-10)
     o1, o2, _, _ = oracle.pls_decompose(xh.astype(np.float64), xl.astype(np.float64), op)
     assert rel_l2(u1[0], o1) <= 2e-4 and rel_l2(u2[0], o2) <= 2e-4
+
+
+def test_paper_size_bench_batch():
+    """The benchmark's launch configuration: 32 slices of 512^2 in one call
+    (PCG to 1e-6, as the benchmark runs it); the first and last slices against
+    the oracle."""
+    maps = [noisy_mixture(512, 0.5, 40 + s) for s in range(32)]
+    xh = np.stack([m[0] for m in maps])
+    xl = np.stack([m[1] for m in maps])
+    u1, u2, reps = run(xh, xl, K=500, tol=1e-6)
+    op = oracle.PlsParams(gamma=0.1, tau=0.2, eps=0.05, max_iter=500, tol=1e-10)
+    for s in (0, 31):
+        o1, o2, _, _ = oracle.pls_decompose(xh[s].astype(np.float64), xl[s].astype(np.float64), op)
+        assert rel_l2(u1[s], o1) <= 2e-4 and rel_l2(u2[s], o2) <= 2e-4, s
