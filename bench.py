@@ -646,6 +646,7 @@ def main():
         "config": {"workload": wdesc,
                    "slices_per_step_per_gpu": S, "mean_adm_iterations": mean_it,
                    "max_adm_iterations": int(max(state["iters"])),
+                   "adm_iteration_quantiles": [int(v) for v in np.percentile(state["iters"], [0, 25, 50, 75, 100])],
                    "all_converged": bool(state.get("conv", False)),
                    "mean_pcg_iterations": float(np.mean(state["pls_iters"])),
                    "plan_seconds": round(plan_s, 3), "nnz": plan.nnz,

@@ -301,8 +301,9 @@ typedef struct {
     double bwd_ms_total;   /* G = mu A^T r + ... (pixel-major table)  */
     int64_t fwd_launches;
     int64_t bwd_launches;
-    int64_t table_bytes_fwd;  /* algorithmic bytes of one fwd launch  */
-    int64_t table_bytes_bwd;  /* algorithmic bytes of one bwd launch  */
+    int64_t table_bytes_fwd;  /* algorithmic bytes per fwd launch (mean over the
+                                 launches timed: narrowed batches move fewer) */
+    int64_t table_bytes_bwd;  /* the same for the bwd launches            */
 } dect_adm_profile;
 
 /*

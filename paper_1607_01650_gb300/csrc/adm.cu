@@ -74,6 +74,7 @@ struct AdmDev {
     int *iters;        // [NB]
     int *conv;         // [NB]
     int *active;       // [NB]
+    int *slot;         // [NB] caller image (index in the chunk) held by each slot; -1: none
     int *k;            // iteration counter
     int *all_done;     // 1 once no channel is active
     int *bad;          // 1 once a non-finite objective was seen
@@ -89,7 +90,6 @@ struct AdmConst {
     double mu_d, rho_d;  // FP64 for the step and objective
     double tol;
     int rule;
-    int nimg;
 };
 
 template <int NB>
@@ -684,7 +684,8 @@ __global__ void __launch_bounds__(BLK) k_fwd(const int64_t *__restrict__ rowptr,
 #pragma unroll
                 for (int c = 0; c < VW; ++c) {
                     const int img = vl * VW + c;
-                    float g = img < C.nimg ? beta_img[img] * m_planar[(int64_t)img * C.M + ray] : 0.f;
+                    const int im = D.slot[img];
+                    float g = im >= 0 ? beta_img[img] * m_planar[(int64_t)im * C.M + ray] : 0.f;
                     acc.v[c] -= g;
                     if (MODE == 2) nrm[0].v[c] = fmaf(acc.v[c], acc.v[c], nrm[0].v[c]);
                 }
@@ -716,15 +717,56 @@ __global__ void k_pack(const float *__restrict__ x, float *__restrict__ f, int64
     f[t] = img < nimg ? beta_img[img] * x[(int64_t)img * N + pix] : 0.f;
 }
 
+// Slots that hold a caller image (and, with only_stopped, whose channel has
+// stopped) write it to x[image].
 template <int NB>
-__global__ void k_unpack(const float *__restrict__ f, float *__restrict__ x, int64_t N, int nimg,
+__global__ void k_unpack(const float *__restrict__ f, float *__restrict__ x, int64_t N,
+                         const int *__restrict__ slot, const int *__restrict__ active, int only_stopped,
                          const float *__restrict__ beta_img)
 {
     int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= N * NB) return;
     int64_t pix = t / NB;
-    int img = (int)(t % NB);
-    if (img < nimg) x[(int64_t)img * N + pix] = f[t] / beta_img[img];
+    const int j = (int)(t % NB), img = slot[j];
+    if (img >= 0 && !(only_stopped && active[j])) x[(int64_t)img * N + pix] = f[t] / beta_img[j];
+}
+
+// Narrowing a batch: slot i of the NB2-wide state takes slot map[i] of the
+// NB-wide one (map[i] < 0: an empty slot, zero).
+template <int NB, int NB2>
+__global__ void k_repack(const float *__restrict__ src, float *__restrict__ dst, int64_t rows,
+                         const int *__restrict__ map)
+{
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= rows * NB2) return;
+    const int64_t row = t / NB2;
+    const int i = (int)(t % NB2), j = map[i];
+    dst[t] = j >= 0 ? src[row * NB + j] : 0.f;
+}
+
+template <int NB, int NB2>
+__global__ void k_repack_scalars(AdmDev D, AdmDev D2, const int *__restrict__ map,
+                                 const float *__restrict__ beta, float *__restrict__ beta2)
+{
+    const int i = threadIdx.x;
+    if (i < NB2) {
+        const int j = map[i];
+        const bool on = j >= 0;
+        D2.alpha[i] = on ? D.alpha[j] : 0.0;
+        D2.c_prev[i] = on ? D.c_prev[j] : 0.0;
+        D2.phi_prev[i] = on ? D.phi_prev[j] : 0.0;
+        D2.rel[i] = on ? D.rel[j] : 0.0;
+        D2.iters[i] = on ? D.iters[j] : 0;
+        D2.conv[i] = on ? D.conv[j] : 0;
+        D2.active[i] = on ? D.active[j] : 0;
+        D2.slot[i] = on ? D.slot[j] : -1;
+        beta2[i] = on ? beta[j] : 1.f;
+    }
+    if (i == 0) {
+        *D2.k = *D.k;
+        *D2.all_done = 0;
+        *D2.bad = *D.bad;
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -741,6 +783,7 @@ struct Work {
     const float *m;  // measured sinograms, planar [nimg][M]
     double *dbl;
     int *ints;
+    int *map;         // [NB] slot map while narrowing into this workspace
     unsigned *ctr;
     AdmDev D;
     int win_grid;     // > 0: A^T through shared-memory windows with this grid
@@ -910,34 +953,15 @@ void enqueue_iteration(const dect_plan *P, const Work &W, const AdmConst &C, int
 
 int kernels_per_iteration(const AdmConst &C) { return C.nonneg ? 4 : 3; }
 
+// Workspace of one batch width: one allocation, laid out once to size and
+// then for real, zeroed; the windowed A^T set up for this width.
 template <int NB>
-dect_status run_chunk(const dect_plan *P, const float *m, float *x, int nimg,
-                      const dect_adm_params *prm, const float *beta_host, dect_adm_report *rep,
-                      dect_adm_profile *prof, cudaStream_t s)
+cudaError_t alloc_work(const dect_plan *P, Work &W, char **base_out, const float *m, cudaStream_t s)
 {
     const int64_t N = P->N, M = P->M;
-    AdmConst C;
-    C.n = P->n;
-    C.N = N;
-    C.M = M;
-    C.mu = (float)prm->mu;
-    C.rho = (float)prm->rho;
-    double xi = prm->xi > 0 ? prm->xi : prm->rho;
-    C.xi = (float)xi;
-    C.nonneg = prm->nonneg ? 1 : 0;
-    C.joint = prm->joint_tv ? 1 : 0;
-    C.xi_is_rho = (xi == prm->rho && !C.nonneg) ? 1 : 0;
-    C.mu_d = prm->mu;
-    C.rho_d = prm->rho;
-    C.tol = prm->rel_obj_tol;
-    C.rule = prm->step_rule;
-    C.nimg = nimg;
-
-    // one allocation for everything: lay out once to size, then for real
     const size_t nf = (size_t)N * NB, nr = (size_t)M * NB;
     const size_t ndbl = (size_t)R_COUNT * NB + (size_t)C_COUNT * 2 * kGrid * NB + 4 * NB;
-    const size_t nint = 4 * NB + 8;
-    Work W;
+    const size_t nint = 5 * NB + 8;
     auto layout = [&](char *b) -> size_t {
         size_t o = 0;
         auto take = [&](size_t nbytes) { char *p = b ? b + o : nullptr; o = (o + nbytes + 255) & ~(size_t)255; return p; };
@@ -957,11 +981,11 @@ dect_status run_chunk(const dect_plan *P, const float *m, float *x, int nimg,
     };
     const size_t bytes = layout(nullptr);
     char *base = nullptr;
-    DECT_CUDA(cudaMallocAsync((void **)&base, bytes, s));
+    cudaError_t e = cudaMallocAsync((void **)&base, bytes, s);
+    if (e != cudaSuccess) return e;
+    *base_out = base;
     layout(base);
     W.m = m;
-    DECT_CUDA(setup_window<NB>(P, W));
-
     AdmDev &D = W.D;
     D.red = W.dbl;
     D.part = D.red + R_COUNT * NB;
@@ -972,56 +996,80 @@ dect_status run_chunk(const dect_plan *P, const float *m, float *x, int nimg,
     D.iters = W.ints;
     D.conv = D.iters + NB;
     D.active = D.conv + NB;
-    D.k = D.active + NB;
+    D.slot = D.active + NB;
+    W.map = D.slot + NB;
+    D.k = W.map + NB;
     D.all_done = D.k + 1;
     D.bad = D.all_done + 1;
     D.ctr = W.ctr;
+    e = cudaMemsetAsync(base, 0, bytes, s);
+    if (e == cudaSuccess) e = setup_window<NB>(P, W);
+    return e;
+}
 
-    std::vector<float> hbeta(64, 1.f);
-    std::vector<int> hact(NB, 0);
-    for (int b = 0; b < nimg; ++b) {
-        hbeta[b] = beta_host[b];
-        hact[b] = 1;
+// Average algorithmic bytes per profiled launch, folded over batch widths.
+template <int NB>
+void add_profile_bytes(const dect_plan *P, dect_adm_profile *prof, int64_t launches_before)
+{
+    if (!prof) return;
+    const int64_t now = prof->fwd_launches, add = now - launches_before;
+    if (now <= 0 || add <= 0) return;
+    // A: table + row pointers, G read, q written
+    const double fwd = 8.0 * P->nnz + 8.0 * (P->M + 1) + 4.0 * NB * (P->N + P->M);
+    // A^T: table + column pointers, r and the two components of p read, G written
+    const double bwd = 8.0 * P->nnz + 8.0 * (P->N + 1) + 4.0 * NB * (P->M + 3 * P->N);
+    prof->table_bytes_fwd = (int64_t)(((double)prof->table_bytes_fwd * launches_before + fwd * add) / now);
+    prof->table_bytes_bwd = (int64_t)(((double)prof->table_bytes_bwd * launches_before + bwd * add) / now);
+}
+
+// Report of the caller image held by slot j, from host copies of the
+// reduction slots and per-slot counters.
+inline void fill_report(dect_adm_report &r, int NB, int j, const AdmConst &C, double mu, int K,
+                        const std::vector<double> &hred, const std::vector<double> &hrel,
+                        const std::vector<int> &hit, const std::vector<int> &hconv)
+{
+    r.iters = K == 0 ? 0 : hit[j];
+    r.converged = hconv[j];
+    if (C.joint) {  // the slice's joint objective, reported on both of its channels
+        const int j0 = j & ~1;
+        r.objective = hred[R_TV * NB + j0] + hred[R_TV * NB + j0 + 1] +
+                      0.5 * mu * (hred[R_RR * NB + j0] + hred[R_RR * NB + j0 + 1]);
+    } else {
+        r.objective = hred[R_TV * NB + j] + 0.5 * mu * hred[R_RR * NB + j];
     }
-    // zero state; G = q = 0 and alpha = 0 make the first step of k_tv a no-op
-    DECT_CUDA(cudaMemsetAsync(base, 0, bytes, s));
-    DECT_CUDA(cudaMemcpyAsync(W.beta, hbeta.data(), 64 * 4, cudaMemcpyHostToDevice, s));
-    DECT_CUDA(cudaMemcpyAsync(D.active, hact.data(), NB * 4, cudaMemcpyHostToDevice, s));
+    r.rel_change = hrel[j];
+}
 
-    const int64_t tn = (int64_t)N * NB;
-    if (prm->warm_start) {
-        k_pack<NB><<<(unsigned)((tn + 255) / 256), 256, 0, s>>>(x, W.f[0], N, nimg, W.beta);
-        DECT_LAUNCH_CHECK();
-        count_launches(1);
-    }
-    // r^0 = A f^0 - beta m
-    k_fwd<NB, Kern<NB>::GF, 0><<<kFwdGrid, kFwdBlock, 0, s>>>(P->rowptr, P->ent, W.f[0], W.r, m, W.beta, C, D);
-    DECT_LAUNCH_CHECK();
-    count_launches(1);
-    W.bwd = 1;
-    DECT_CUDA(tune_bwd<NB>(P, W, C, s));
-
-    // iterations: CUDA graphs of `block` iterations (an even number, so the
-    // f double buffer returns to the same parity) and single-iteration graphs
-    // of either parity for the remainder
+// The iteration loop at batch width NB from iteration done_iters on, with W
+// holding the state (freed before return).  With the relative-objective stop,
+// once no more than half of the slots hold running channels the batch is
+// narrowed: the stopped channels' images and reports are written out (their
+// f no longer changes: alpha = 0), the running channels' whole state (f, G,
+// lambda, z, p, r, q and the per-channel scalars) is repacked into an
+// NB/2-wide workspace, and the loop goes on there with the narrower kernels.
+// The iterates are those of the NB-wide run; only the order of the FP64
+// cross-block sums follows the new width.
+template <int NB>
+dect_status iterate(const dect_plan *P, const AdmConst &C, Work W, char *base, float *x,
+                    const dect_adm_params *prm, dect_adm_report *rep, dect_adm_profile *prof, cudaStream_t s,
+                    int done_iters)
+{
+    const int64_t N = P->N, tn = N * NB;
+    AdmDev &D = W.D;
+    const int64_t prof_before = prof ? prof->fwd_launches : 0;
     const int K = prm->max_iter;
     const bool use_tol = prm->rel_obj_tol > 0.0;
     int block = use_tol ? (prm->check_every > 0 ? prm->check_every : 10) : 10;
     block = std::max(2, block + (block & 1));
     cudaStream_t cs = nullptr;
-    DECT_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
     cudaEvent_t ev = nullptr;
-    DECT_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
     std::vector<IterEvents> evs;  // [block] for the block graph, then [2] for the single graphs
-    auto destroy_events = [&]() {
-        for (auto &e : evs) {
-            cudaEventDestroy(e.b0); cudaEventDestroy(e.b1);
-            cudaEventDestroy(e.f0); cudaEventDestroy(e.f1);
-        }
-        evs.clear();
-    };
-    cudaError_t err = cudaSuccess;
-    if (prof) {
+    cudaGraphExec_t gx_block = nullptr, gx_one[2] = {nullptr, nullptr};
+    int *h_flags = nullptr;       // pinned: [0] all_done, [1 .. NB] active
+    char *base2 = nullptr;        // the narrowed workspace, once handed on
+    cudaError_t err = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+    if (err == cudaSuccess) err = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+    if (err == cudaSuccess && prof) {
         evs.resize(block + 2);
         for (auto &e : evs) {
             if (err == cudaSuccess) err = cudaEventCreate(&e.b0);
@@ -1030,7 +1078,6 @@ dect_status run_chunk(const dect_plan *P, const float *m, float *x, int nimg,
             if (err == cudaSuccess) err = cudaEventCreate(&e.f1);
         }
     }
-    cudaGraphExec_t gx_block = nullptr, gx_one[2] = {nullptr, nullptr};
     auto make_graph = [&](int iters, int par0, int ev0, cudaGraphExec_t *out) -> cudaError_t {
         cudaGraph_t gr = nullptr;
         cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
@@ -1061,27 +1108,109 @@ dect_status run_chunk(const dect_plan *P, const float *m, float *x, int nimg,
     // the caller's stream orders the set-up; the capture stream runs the loop
     if (err == cudaSuccess) err = cudaEventRecord(ev, s);
     if (err == cudaSuccess) err = cudaStreamWaitEvent(cs, ev, 0);
-    if (err == cudaSuccess && K >= block) err = make_graph(block, 0, 0, &gx_block);
-    if (err == cudaSuccess && K % block) {
+    const int remaining = K - done_iters;
+    if (err == cudaSuccess && remaining >= block) err = make_graph(block, done_iters & 1, 0, &gx_block);
+    if (err == cudaSuccess && remaining % block) {
         err = make_graph(1, 0, block, &gx_one[0]);
         if (err == cudaSuccess) err = make_graph(1, 1, block + 1, &gx_one[1]);
     }
-    int *h_done = nullptr;
-    if (err == cudaSuccess) err = cudaMallocHost((void **)&h_done, sizeof(int));
-    if (h_done) *h_done = 0;
-    int done_iters = 0;
+    if (err == cudaSuccess) err = cudaMallocHost((void **)&h_flags, sizeof(int) * (NB + 1));
+    if (h_flags) h_flags[0] = 0;
     while (err == cudaSuccess && done_iters + block <= K) {
         err = cudaGraphLaunch(gx_block, cs);
         count_launches((int64_t)kernels_per_iteration(C) * block);
         done_iters += block;
         if (err == cudaSuccess) err = collect(block, 0);
         if (err == cudaSuccess && use_tol) {
-            err = cudaMemcpyAsync(h_done, D.all_done, sizeof(int), cudaMemcpyDeviceToHost, cs);
+            err = cudaMemcpyAsync(h_flags, D.all_done, sizeof(int), cudaMemcpyDeviceToHost, cs);
+            if (err == cudaSuccess && NB >= 4)
+                err = cudaMemcpyAsync(h_flags + 1, D.active, sizeof(int) * NB, cudaMemcpyDeviceToHost, cs);
             if (err == cudaSuccess) err = cudaStreamSynchronize(cs);
-            if (err == cudaSuccess && *h_done) break;
+            if (err == cudaSuccess && h_flags[0]) break;
+            if constexpr (NB >= 4) {
+                int live = 0;
+                for (int j = 0; j < NB; ++j) live += h_flags[1 + j] ? 1 : 0;
+                if (err == cudaSuccess && live <= NB / 2 && done_iters < K) {
+                    // narrow: write out the stopped channels, repack the running ones
+                    constexpr int NB2 = NB / 2;
+                    const int par = done_iters & 1;
+                    std::vector<double> hred(R_COUNT * NB), hrel(NB);
+                    std::vector<int> hit(NB), hconv(NB), hslot(NB);
+                    err = cudaMemcpyAsync(hred.data(), D.red, sizeof(double) * R_COUNT * NB, cudaMemcpyDeviceToHost, cs);
+                    if (err == cudaSuccess) err = cudaMemcpyAsync(hrel.data(), D.rel, sizeof(double) * NB, cudaMemcpyDeviceToHost, cs);
+                    if (err == cudaSuccess) err = cudaMemcpyAsync(hit.data(), D.iters, sizeof(int) * NB, cudaMemcpyDeviceToHost, cs);
+                    if (err == cudaSuccess) err = cudaMemcpyAsync(hconv.data(), D.conv, sizeof(int) * NB, cudaMemcpyDeviceToHost, cs);
+                    if (err == cudaSuccess) err = cudaMemcpyAsync(hslot.data(), D.slot, sizeof(int) * NB, cudaMemcpyDeviceToHost, cs);
+                    if (err == cudaSuccess) {
+                        k_unpack<NB><<<(unsigned)((tn + 255) / 256), 256, 0, cs>>>(W.f[par], x, N, D.slot, D.active, 1,
+                                                                                   W.beta);
+                        err = cudaGetLastError();
+                        count_launches(1);
+                    }
+                    if (err == cudaSuccess) err = cudaStreamSynchronize(cs);
+                    if (err != cudaSuccess) break;
+                    if (rep)
+                        for (int j = 0; j < NB; ++j)
+                            if (hslot[j] >= 0 && !h_flags[1 + j])
+                                fill_report(rep[hslot[j]], NB, j, C, prm->mu, K, hred, hrel, hit, hconv);
+                    std::vector<int> map(NB2, -1);
+                    for (int j = 0, i = 0; j < NB; ++j)
+                        if (h_flags[1 + j]) map[i++] = j;  // running channels, in order (pairs stay pairs)
+                    Work W2;
+                    err = alloc_work<NB2>(P, W2, &base2, W.m, cs);
+                    if (err == cudaSuccess) {
+                        W2.bwd = 1;
+                        // time the A^T variants on the empty workspace, before the state arrives
+                        err = tune_bwd<NB2>(P, W2, C, cs);
+                    }
+                    if (err == cudaSuccess)
+                        err = cudaMemcpyAsync(W2.map, map.data(), sizeof(int) * NB2, cudaMemcpyHostToDevice, cs);
+                    if (err == cudaSuccess) {
+                        auto rp = [&](const float *src, float *dst, int64_t rows) {
+                            const int64_t t = rows * NB2;
+                            k_repack<NB, NB2><<<(unsigned)((t + 255) / 256), 256, 0, cs>>>(src, dst, rows, W2.map);
+                        };
+                        rp(W.f[par], W2.f[par], N);
+                        rp(W.G, W2.G, N);
+                        rp(W.lam, W2.lam, 2 * N);
+                        rp(W.z, W2.z, 2 * N);
+                        rp(W.p, W2.p, 2 * N);
+                        rp(W.r, W2.r, P->M);
+                        rp(W.q, W2.q, P->M);
+                        k_repack_scalars<NB, NB2><<<1, 64, 0, cs>>>(D, W2.D, W2.map, W.beta, W2.beta);
+                        err = cudaGetLastError();
+                        count_launches(8);
+                    }
+                    // the state now lives in the narrowed workspace
+                    if (err == cudaSuccess) err = cudaEventRecord(ev, cs);
+                    if (err == cudaSuccess) err = cudaStreamWaitEvent(s, ev, 0);
+                    if (err == cudaSuccess) {
+                        // release this phase, then continue at NB2
+                        add_profile_bytes<NB>(P, prof, prof_before);
+                        cudaFreeAsync(base, s);
+                        base = nullptr;
+                        if (gx_block) cudaGraphExecDestroy(gx_block);
+                        if (gx_one[0]) cudaGraphExecDestroy(gx_one[0]);
+                        if (gx_one[1]) cudaGraphExecDestroy(gx_one[1]);
+                        gx_block = gx_one[0] = gx_one[1] = nullptr;
+                        cudaStreamSynchronize(cs);
+                        for (auto &e : evs) {
+                            cudaEventDestroy(e.b0); cudaEventDestroy(e.b1);
+                            cudaEventDestroy(e.f0); cudaEventDestroy(e.f1);
+                        }
+                        evs.clear();
+                        cudaFreeHost(h_flags);
+                        h_flags = nullptr;
+                        cudaEventDestroy(ev);
+                        cudaStreamDestroy(cs);
+                        return iterate<NB2>(P, C, W2, base2, x, prm, rep, prof, s, done_iters);
+                    }
+                    break;
+                }
+            }
         }
     }
-    bool finished = use_tol && err == cudaSuccess && *h_done;
+    bool finished = use_tol && err == cudaSuccess && h_flags && h_flags[0];
     while (err == cudaSuccess && !finished && done_iters < K) {
         const int par = done_iters & 1;
         err = cudaGraphLaunch(gx_one[par], cs);
@@ -1094,57 +1223,110 @@ dect_status run_chunk(const dect_plan *P, const float *m, float *x, int nimg,
     if (err == cudaSuccess) {
         launch_tv<NB>(W, C, par, 1, cs);
         if (C.nonneg)
-            k_fwd<NB, Kern<NB>::GF, 2><<<kFwdGrid, kFwdBlock, 0, cs>>>(P->rowptr, P->ent, W.f[1 - par], W.r, m,
+            k_fwd<NB, Kern<NB>::GF, 2><<<kFwdGrid, kFwdBlock, 0, cs>>>(P->rowptr, P->ent, W.f[1 - par], W.r, W.m,
                                                                   W.beta, C, D);
-        k_unpack<NB><<<(unsigned)((tn + 255) / 256), 256, 0, cs>>>(W.f[1 - par], x, N, nimg, W.beta);
+        k_unpack<NB><<<(unsigned)((tn + 255) / 256), 256, 0, cs>>>(W.f[1 - par], x, N, D.slot, D.active, 0,
+                                                                   W.beta);
         err = cudaGetLastError();
         count_launches(C.nonneg ? 3 : 2);
     }
     if (err == cudaSuccess) err = cudaEventRecord(ev, cs);
     if (err == cudaSuccess) err = cudaStreamWaitEvent(s, ev, 0);
-    if (prof) {
-        // A: table + row pointers, G read, q written
-        prof->table_bytes_fwd = 8 * P->nnz + 8 * (P->M + 1) + 4LL * NB * (P->N + P->M);
-        // A^T: table + column pointers, r and the two components of p read, G written
-        prof->table_bytes_bwd = 8 * P->nnz + 8 * (P->N + 1) + 4LL * NB * (P->M + 3 * P->N);
-    }
+    add_profile_bytes<NB>(P, prof, prof_before);
 
     std::vector<double> hred(R_COUNT * NB), hrel(NB);
-    std::vector<int> hit(NB), hconv(NB);
+    std::vector<int> hit(NB), hconv(NB), hslot(NB);
     int hbad = 0;
     if (err == cudaSuccess) err = cudaMemcpyAsync(hred.data(), D.red, sizeof(double) * R_COUNT * NB, cudaMemcpyDeviceToHost, s);
     if (err == cudaSuccess) err = cudaMemcpyAsync(hrel.data(), D.rel, sizeof(double) * NB, cudaMemcpyDeviceToHost, s);
     if (err == cudaSuccess) err = cudaMemcpyAsync(hit.data(), D.iters, sizeof(int) * NB, cudaMemcpyDeviceToHost, s);
     if (err == cudaSuccess) err = cudaMemcpyAsync(hconv.data(), D.conv, sizeof(int) * NB, cudaMemcpyDeviceToHost, s);
+    if (err == cudaSuccess) err = cudaMemcpyAsync(hslot.data(), D.slot, sizeof(int) * NB, cudaMemcpyDeviceToHost, s);
     if (err == cudaSuccess) err = cudaMemcpyAsync(&hbad, D.bad, sizeof(int), cudaMemcpyDeviceToHost, s);
-    cudaFreeAsync(base, s);
+    if (base) cudaFreeAsync(base, s);
+    if (base2) cudaFreeAsync(base2, s);  // a narrowing that failed half-way
     if (err == cudaSuccess) err = cudaStreamSynchronize(s);
     if (gx_block) cudaGraphExecDestroy(gx_block);
     if (gx_one[0]) cudaGraphExecDestroy(gx_one[0]);
     if (gx_one[1]) cudaGraphExecDestroy(gx_one[1]);
-    if (h_done) cudaFreeHost(h_done);
-    destroy_events();
-    cudaEventDestroy(ev);
-    cudaStreamDestroy(cs);
+    if (h_flags) cudaFreeHost(h_flags);
+    for (auto &e : evs) {
+        cudaEventDestroy(e.b0); cudaEventDestroy(e.b1);
+        cudaEventDestroy(e.f0); cudaEventDestroy(e.f1);
+    }
+    if (ev) cudaEventDestroy(ev);
+    if (cs) cudaStreamDestroy(cs);
     if (err != cudaSuccess) {
         set_error("dect_adm_tv", err);
         return err == cudaErrorMemoryAllocation ? DECT_ERR_OOM : DECT_ERR_CUDA;
     }
-    if (rep) {
-        for (int b = 0; b < nimg; ++b) {
-            rep[b].iters = K == 0 ? 0 : hit[b];
-            rep[b].converged = hconv[b];
-            if (C.joint) {  // the slice's joint objective, reported on both of its channels
-                const int b0 = b & ~1;
-                rep[b].objective = hred[R_TV * NB + b0] + hred[R_TV * NB + b0 + 1] +
-                                   0.5 * prm->mu * (hred[R_RR * NB + b0] + hred[R_RR * NB + b0 + 1]);
-            } else {
-                rep[b].objective = hred[R_TV * NB + b] + 0.5 * prm->mu * hred[R_RR * NB + b];
-            }
-            rep[b].rel_change = hrel[b];
-        }
-    }
+    if (rep)
+        for (int j = 0; j < NB; ++j)
+            if (hslot[j] >= 0) fill_report(rep[hslot[j]], NB, j, C, prm->mu, K, hred, hrel, hit, hconv);
     return (hbad & 1) ? DECT_ERR_NONFINITE : DECT_OK;
+}
+
+template <int NB>
+dect_status run_chunk(const dect_plan *P, const float *m, float *x, int nimg,
+                      const dect_adm_params *prm, const float *beta_host, dect_adm_report *rep,
+                      dect_adm_profile *prof, cudaStream_t s)
+{
+    const int64_t N = P->N;
+    AdmConst C;
+    C.n = P->n;
+    C.N = N;
+    C.M = P->M;
+    C.mu = (float)prm->mu;
+    C.rho = (float)prm->rho;
+    double xi = prm->xi > 0 ? prm->xi : prm->rho;
+    C.xi = (float)xi;
+    C.nonneg = prm->nonneg ? 1 : 0;
+    C.joint = prm->joint_tv ? 1 : 0;
+    C.xi_is_rho = (xi == prm->rho && !C.nonneg) ? 1 : 0;
+    C.mu_d = prm->mu;
+    C.rho_d = prm->rho;
+    C.tol = prm->rel_obj_tol;
+    C.rule = prm->step_rule;
+
+    Work W;
+    char *base = nullptr;
+    cudaError_t e = alloc_work<NB>(P, W, &base, m, s);
+    if (e != cudaSuccess) {
+        if (base) cudaFreeAsync(base, s);
+        set_error("dect_adm_tv", e);
+        return e == cudaErrorMemoryAllocation ? DECT_ERR_OOM : DECT_ERR_CUDA;
+    }
+    AdmDev &D = W.D;
+    std::vector<float> hbeta(64, 1.f);
+    std::vector<int> hact(NB, 0), hslot(NB, -1);
+    for (int b = 0; b < nimg; ++b) {
+        hbeta[b] = beta_host[b];
+        hact[b] = 1;
+        hslot[b] = b;
+    }
+    // zero state (the workspace is cleared); G = q = 0 and alpha = 0 make the
+    // first step of k_tv a no-op
+    auto fail = [&](cudaError_t err) {
+        cudaFreeAsync(base, s);
+        set_error("dect_adm_tv", err);
+        return err == cudaErrorMemoryAllocation ? DECT_ERR_OOM : DECT_ERR_CUDA;
+    };
+    if ((e = cudaMemcpyAsync(W.beta, hbeta.data(), 64 * 4, cudaMemcpyHostToDevice, s)) != cudaSuccess) return fail(e);
+    if ((e = cudaMemcpyAsync(D.active, hact.data(), NB * 4, cudaMemcpyHostToDevice, s)) != cudaSuccess) return fail(e);
+    if ((e = cudaMemcpyAsync(D.slot, hslot.data(), NB * 4, cudaMemcpyHostToDevice, s)) != cudaSuccess) return fail(e);
+    const int64_t tn = N * NB;
+    if (prm->warm_start) {
+        k_pack<NB><<<(unsigned)((tn + 255) / 256), 256, 0, s>>>(x, W.f[0], N, nimg, W.beta);
+        count_launches(1);
+    }
+    // r^0 = A f^0 - beta m
+    k_fwd<NB, Kern<NB>::GF, 0><<<kFwdGrid, kFwdBlock, 0, s>>>(P->rowptr, P->ent, W.f[0], W.r, m, W.beta, C, D);
+    count_launches(1);
+    if ((e = cudaGetLastError()) != cudaSuccess) return fail(e);
+    W.bwd = 1;
+    if ((e = tune_bwd<NB>(P, W, C, s)) != cudaSuccess) return fail(e);
+    // (hbeta, hact and hslot are pageable: their copies have read them by now)
+    return iterate<NB>(P, C, W, base, x, prm, rep, prof, s, 0);
 }
 
 }  // namespace
@@ -1169,6 +1351,7 @@ extern "C" dect_status dect_adm_tv_ex(const dect_plan *plan, const float *m, flo
     cudaStream_t s = (cudaStream_t)stream;
     if (prof) {
         prof->fwd_ms_total = prof->bwd_ms_total = 0.0;
+        prof->table_bytes_fwd = prof->table_bytes_bwd = 0;
         prof->fwd_launches = prof->bwd_launches = 0;
     }
     const int total = 2 * n_slices;

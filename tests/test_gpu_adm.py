@@ -215,6 +215,48 @@ def test_paper_size_first_iterations():
             assert rel_l2(x[i, e], outs[i][0][e]) <= 1e-4
 
 
+@pytest.mark.parametrize("ns,joint", [(8, False), (6, True)])
+def test_narrowing_batch_matches_oracle(ns, joint):
+    """Channels whose relative-objective stop comes at different iterations
+    (slices of very different dose): once half of a batch has stopped, the
+    running channels continue in a batch half as wide.  Every channel ends as
+    the oracle does at the channel's own iteration count, with the report of
+    that result."""
+    g = synth.tiny_geometry(n=48, nv=24, nb=72, px=1.0, sod=120.0, sdd=240.0)
+    doses = [3e2, 1e6, 1e3, 3e5, 1e4, 3e3, 1e5, 5e2][:ns]
+    slices = [synth.make_slice(g, seed=500 + i, i0=doses[i]) for i in range(ns)]
+    plan = dect.Plan(g)
+    t = oracle.table(g)
+    m = np.stack([s.m for s in slices]).astype(np.float32)
+    prm = dect.AdmParams(mu=MU, rho=RHO, max_iter=3000, rel_obj_tol=1e-4, check_every=10, joint=joint)
+    x, reps, prof = dect.adm_tv(plan, torch.tensor(m, device="cuda"), prm, profile=True)
+    x = x.cpu().numpy()
+    iters = [r.iters for r in reps]
+    assert all(r.converged for r in reps)
+    assert max(iters) - min(iters) >= 20          # the stops are spread over several checks
+    nb = 1 << (2 * ns - 1).bit_length()
+    full = 8 * plan.nnz + 8 * (g.nv * g.nb + 1) + 4 * nb * (g.n * g.n + g.nv * g.nb)
+    assert prof.table_bytes_fwd < full           # part of the launches ran narrowed
+    b = (1.0, 0.6)
+    for i in range(ns):
+        k = reps[2 * i].iters
+        if joint:
+            assert reps[2 * i + 1].iters == k
+        op = oracle.AdmParams(mu=MU, rho=RHO, max_iter=k, step_rule=oracle.CAUCHY, joint=joint)
+        xo, _ = oracle.adm_dual(t, m[i].astype(np.float64), op) if joint else (None, None)
+        for e in range(2):
+            if not joint:
+                op = oracle.AdmParams(mu=MU, rho=RHO, max_iter=reps[2 * i + e].iters, step_rule=oracle.CAUCHY)
+                f, _, _, _ = oracle.adm_channel(t, b[e] * m[i, e].astype(np.float64), op)
+                xe = f / b[e]
+            else:
+                xe = xo[e]
+            assert rel_l2(x[i, e], xe) <= 1e-4, (i, e)
+            if not joint:
+                phi = oracle.objective(t, b[e] * m[i, e].astype(np.float64), MU, b[e] * x[i, e].astype(np.float64))
+                assert abs(reps[2 * i + e].objective - phi) <= 1e-4 * phi
+
+
 def test_paper_size_bench_configuration():
     """The benchmark's launch configuration: 32 slices (64 interleaved channels,
     the autotuned 1024-thread table kernels) of the benchmark's inputs at
