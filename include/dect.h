@@ -194,6 +194,10 @@ typedef struct {
  * with grad the backward differences of Eq. (2) and Phi the objective of
  * Eq. (4).  Bulk arithmetic is FP32; the norms that give alpha and Phi are
  * accumulated in FP64 across warps and blocks.
+ * Up to 64 channels (32 slices) share one pass over the system matrix.  With
+ * rel_obj_tol > 0, once no more than half of such a batch is still running,
+ * the running channels continue in a batch half as wide (the same iterates;
+ * only the order of the FP64 cross-block sums changes).
  * reports: HOST array [n_slices * 2] (may be NULL).  Synchronises `stream`.
  * Device scratch is taken from the stream-ordered allocator and returned
  * before the call ends.
