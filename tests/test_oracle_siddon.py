@@ -75,6 +75,21 @@ def test_rotation_by_quarter_turn_shifts_views():
     np.testing.assert_allclose(np.roll(yr, -g.nv // 4, axis=0), y, rtol=1e-12, atol=1e-14)
 
 
+def test_mirror_flip_reverses_views_and_bins():
+    """Mirroring the image in y (row i -> n - 1 - i) mirrors the source orbit
+    (view angle t -> -t) and the detector axis (u -> -u): ray (v, b) of the
+    flipped image is ray ((nv - v) mod nv, nb - 1 - b) of the original.  The
+    image side is odd so that no ray runs along a grid line (there the
+    midpoint rule gives the +side pixel, which mirroring does not keep)."""
+    g = synth.tiny_geometry(n=11, nv=18, nb=21, px=1.0)
+    t = oracle.table(g)
+    x = synth.random_image(g.n, 6)
+    y = oracle.project(t, x)
+    yf = oracle.project(t, x[::-1, :].copy())
+    v = np.arange(g.nv)
+    np.testing.assert_allclose(yf, y[(g.nv - v) % g.nv][:, ::-1], rtol=1e-12, atol=1e-14)
+
+
 def test_adjoint_identity():
     """<A x, y> = <x, A^T y> to 1e-12, and A^T equals the pixel-clip transpose."""
     g = GEOMS[1]
