@@ -122,3 +122,20 @@ def test_paper_size_sampled_rays():
         np.testing.assert_array_equal(ln[s:e], lens.astype(np.float32))
         want = float(np.dot(lens, x.reshape(-1)[idx]))
         assert abs(y[v, b] - want) <= 1e-5 * max(abs(want), 1e-3)
+
+
+def test_paper_size_mirror_symmetry():
+    """At 512^2 / 60 views / 736 bins, A of the image flipped in y equals A of
+    the image with views mirrored ((nv - v) mod nv) and bins reversed: a
+    property of the geometry that checks the whole GPU table, not samples.
+    No ray of this geometry runs along a grid line (where the midpoint rule
+    breaks the symmetry on purpose)."""
+    g = synth.paper_geometry()
+    plan = dect.Plan(g)
+    assert plan.n_grid_aligned == 0
+    x = torch.rand((1, g.n, g.n), device="cuda") * 0.02
+    y = dect.project(plan, x)[0]
+    yf = dect.project(plan, torch.flip(x, dims=[1]).contiguous())[0]
+    v = torch.arange(g.nv, device="cuda")
+    ym = torch.flip(y[(g.nv - v) % g.nv], dims=[1])
+    assert float((yf - ym).norm() / ym.norm()) <= 1e-5
