@@ -56,6 +56,10 @@ def parse():
     ap.add_argument("--max-iter", type=int, default=2000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--nonneg", action="store_true",
+                    help="paper workload with the f-step projected onto f >= 0 (dect_adm_params.nonneg)")
+    ap.add_argument("--joint", action="store_true",
+                    help="paper workload with the TV taken jointly over both energies (joint_tv)")
     ap.add_argument("--bwd-variant", type=int, default=-1,
                     help="fix the A^T variant (0-5, see dect_plan_get_tuning) instead of autotuning")
     ap.add_argument("--train-slices", type=int, default=1024, help="learned workload: training slices")
@@ -524,6 +528,7 @@ def main():
     else:
         prm = dect.AdmParams(mu=MU, rho=RHO, beta=BETA, step_rule=dect.CAUCHY, max_iter=args.max_iter,
                              rel_obj_tol=TOL, check_every=10)
+    prm = dataclasses.replace(prm, nonneg=args.nonneg, joint=args.joint)
     pp = dect.PlsParams(**PLS)
 
     state = {"iters": [], "pls_iters": [], "prof": []}
@@ -640,6 +645,9 @@ def main():
         wdesc = ("paper-shaped 512x512/0.5mm, 60 views over 360deg, 736 bins x 0.6mm, "
                  "SOD 500/SDD 1000, head phantom, I0=2e5, ADM to 1e-4 rel. objective "
                  "(both energies) + PLS gamma 0.1")
+    if args.nonneg or args.joint:
+        wdesc += "; options: " + ", ".join(o for o, on in (("f-step projected onto f >= 0", args.nonneg),
+                                                            ("joint TV over both energies", args.joint)) if on)
     line = {
         "metric": METRIC_STRESS if stress else METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
