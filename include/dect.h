@@ -158,8 +158,9 @@ typedef struct {
     int max_iter;       /* iterations, >= 0                                             */
     double rel_obj_tol; /* stop a channel once |Phi_k - Phi_{k-1}| / Phi_{k-1} < tol;
                            <= 0: always run max_iter                                    */
-    int check_every;    /* host checks "all channels stopped" every this many
-                           iterations (>= 1; 0 = 10); only used when rel_obj_tol > 0    */
+    int check_every;    /* host checks "all channels stopped" (and whether the batch
+                           can narrow) every this many iterations, rounded up to an
+                           even number (>= 1; 0 = 10); used when rel_obj_tol > 0       */
     int warm_start;     /* 0: start from x = 0; 1: start from the x passed in           */
     int nonneg;         /* 1: project f onto f >= 0 after every f-step (x in R_+^N,
                            Eq. (1)); costs one extra A per iteration to rebuild the
