@@ -120,8 +120,9 @@ def kernel_source_hash():
     return h.hexdigest()[:16]
 
 
-def committed_traffic(kernel):
-    """DRAM bytes per launch from the committed ncu summary, if it matches the current sources."""
+def committed_traffic(kernel, workload):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken on
+    this workload and matches the current sources."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(p):
         return None
@@ -130,7 +131,9 @@ def committed_traffic(kernel):
     if d.get("source_hash") != kernel_source_hash():
         return None
     k = d.get("kernels", {}).get(kernel)
-    return None if k is None else k.get("dram_bytes_per_launch")
+    if k is None or k.get("workload") != workload:
+        return None
+    return k.get("dram_bytes_per_launch")
 
 
 class ClockSampler:
@@ -611,7 +614,7 @@ def main():
         kname, avg_ms, bytes_ = bwd_name, bwd_ms / max(bwd_n, 1), p0.table_bytes_bwd
     peak, peak_src = measured_peaks()
     achieved = bytes_ / (avg_ms / 1e3) / 1e9
-    traffic = committed_traffic(kname)
+    traffic = committed_traffic(kname, "1024^2/360 views/1472 bins" if stress else "512^2/60 views/736 bins")
     roofline = {"bound": "hbm", "kernel": kname, "achieved": round(achieved, 1), "peak": peak,
                 "peak_source": peak_src, "unit": "GB/s", "frac": round(achieved / peak, 4),
                 "traffic": traffic, "algorithmic_bytes": int(bytes_), "avg_launch_ms": avg_ms,

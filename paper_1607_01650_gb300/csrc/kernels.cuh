@@ -269,16 +269,28 @@ __device__ __forceinline__ Vec<Batch<NB>::VW> row_dot_g(const Entry *__restrict_
                 for (int c = 0; c < VW; ++c) acc.v[c] = fmaf(w, xv.v[c], acc.v[c]);
             }
         } else {
+            // rounds in groups of R: R entries broadcast, then R independent
+            // gathers in flight, then their multiply-adds
+            constexpr int NR = G / EG, R = NR < 8 ? NR : 8;
 #pragma unroll
             for (int u = 0; u < U; ++u) {
 #pragma unroll
-                for (int j = 0; j < G / EG; ++j) {
-                    const unsigned srcl = gbase + j * EG + grp;
-                    const int pix = __shfl_sync(0xffffffffu, cur[u].x, srcl);
-                    const float w = __int_as_float(__shfl_sync(0xffffffffu, cur[u].y, srcl));
-                    const Vec<VW> xv = gather(pix, vl);
+                for (int j0 = 0; j0 < NR; j0 += R) {
+                    int pix[R];
+                    float w[R];
+                    Vec<VW> xv[R];
 #pragma unroll
-                    for (int c = 0; c < VW; ++c) acc.v[c] = fmaf(w, xv.v[c], acc.v[c]);
+                    for (int j = 0; j < R; ++j) {
+                        const unsigned srcl = gbase + (j0 + j) * EG + grp;
+                        pix[j] = __shfl_sync(0xffffffffu, cur[u].x, srcl);
+                        w[j] = __int_as_float(__shfl_sync(0xffffffffu, cur[u].y, srcl));
+                    }
+#pragma unroll
+                    for (int j = 0; j < R; ++j) xv[j] = gather(pix[j], vl);
+#pragma unroll
+                    for (int j = 0; j < R; ++j)
+#pragma unroll
+                        for (int c = 0; c < VW; ++c) acc.v[c] = fmaf(w[j], xv[j].v[c], acc.v[c]);
                 }
             }
         }
