@@ -300,7 +300,6 @@ def run_learned(args, rank, world, local):
     headline's batch) run to the 1e-4 stop from the network's output and, for
     comparison, from zero."""
     import torch
-    import oracle
     import paper_1607_01650_gb300 as dect
     from paper_1607_01650_gb300 import warmstart as ws
     torch.cuda.set_device(local)
@@ -313,7 +312,7 @@ def run_learned(args, rank, world, local):
     torch.cuda.synchronize()
     t_pairs = time.perf_counter() - t0
     net = dect.Cnn(device=local, max_pixels=64 * 512 * 512)  # 32 slices x 2 energies
-    net.set_params(oracle.cnn_init(0).astype(np.float32))
+    net.set_params(synth.cnn_init(0).astype(np.float32))
     t0 = time.perf_counter()
     losses = ws.train(net, pairs, epochs=args.epochs, batch=16, lr=1e-3)
     torch.cuda.synchronize()

@@ -248,7 +248,7 @@ typedef struct {
  *   d = D^{-1} x per pixel (2x2 closed form in FP64), Eq. (11)-(12);
  *   edge map: 3x3 Prewitt magnitude of x_h and of x_l (replicate padding),
  *   each divided by its own maximum, edge where either exceeds edge_tau
- *   (decided in FP32 with a fixed order of operations);
+ *   (decided in FP32, as dect_pls_edge_mask returns it);
  *   e_ik = edge_eps if pixel i or k is an edge, else 1, Eq. (14);
  *   solve (I + gamma L_e) u_m = d_m for m = 1, 2, (L_e u)_i = sum over the
  *   4-neighbours k inside the image of e_ik (u_i - u_k) -- Eq. (15), whose
@@ -261,6 +261,24 @@ typedef struct {
  */
 dect_status dect_pls_decompose(const float *x, int n, int batch, const dect_pls_params *params,
                                float *u, dect_pls_report *reports, dect_stream stream);
+
+/*
+ * The edge map of Eq. (14) (Sec. 2.3) that dect_pls_decompose uses, for
+ * `batch` slices: for each of x_h and x_l the 3x3 Prewitt magnitude
+ * (replicate padding) divided by that image's largest magnitude; a pixel is
+ * an edge (1) when either ratio exceeds edge_tau, else 0.  Magnitudes,
+ * maxima and the division are FP32 (the precision of the images), so the
+ * result can differ from an FP64 decision only at pixels whose ratio lies
+ * within FP32 rounding of edge_tau.
+ * x: [batch][2][n][n] device (x_h, x_l per slice); mask: [batch][n][n] uint8,
+ * device, written.  Device scratch (the magnitudes) is taken from the
+ * stream-ordered allocator and returned before the call ends; the call does
+ * not synchronise.
+ * Errors: DECT_ERR_INVALID_ARG (NULL pointer, n outside 1..16384, batch < 0
+ * or > 65535, non-finite edge_tau), DECT_ERR_CUDA.  batch = 0 is a no-op.
+ */
+dect_status dect_pls_edge_mask(const float *x, int n, int batch, double edge_tau, uint8_t *mask,
+                               dect_stream stream);
 
 /*
  * dect_pls_decompose without any device allocation.  (The paper has no

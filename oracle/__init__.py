@@ -471,6 +471,14 @@ def edge_mask(xh, xl, tau: float) -> np.ndarray:
     return mask
 
 
+def pls_diag(mask, gamma: float, eps: float) -> np.ndarray:
+    """Jacobi diagonal 1 + gamma sum_k e_ik of (I + gamma L_e) (readings R13, R16)."""
+    mask = np.ascontiguousarray(mask, np.uint8)
+    out = np.zeros(mask.shape, np.float64)
+    _load().orc_pls_diag(mask.shape[-1], mask.ctypes.data_as(C.POINTER(C.c_uint8)), gamma, eps, _d(out))
+    return out
+
+
 def pls_apply(mask, gamma: float, eps: float, u) -> np.ndarray:
     """(I + gamma L_e) u, Eq. (14)-(15) under reading R13."""
     u = _f64(u)
@@ -539,20 +547,3 @@ def cnn_loss_grad(params, x, target, scale: float):
     _load().orc_cnn_run(_d(params), scale, _d(x), x.shape[0], x.shape[1], None, _d(target), _d(grad),
                         C.byref(loss))
     return float(loss.value), grad
-
-
-CNN_LAYERS = [(1, 32), (32, 32), (32, 64), (64, 64), (64, 128), (128, 128), (192, 64), (64, 64),
-              (96, 32), (32, 32)]
-
-
-def cnn_init(seed: int) -> np.ndarray:
-    """He-normal weights, zero biases, zero head (so the untrained net is the identity)."""
-    rng = np.random.default_rng(seed)
-    parts = []
-    for cin, cout in CNN_LAYERS:
-        parts.append(rng.standard_normal(cout * cin * 9) * np.sqrt(2.0 / (cin * 9)))
-        parts.append(np.zeros(cout))
-    parts.append(np.zeros(33))
-    p = np.concatenate(parts)
-    assert p.size == cnn_num_params()
-    return p

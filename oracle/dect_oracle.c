@@ -46,8 +46,8 @@
  *   R13 Eq. (15) with Hessian(R) = 2 L_e reads (I + gamma L_e) u = D^{-1} x.
  *   R14 edges: 3x3 Prewitt magnitude of x_h and x_l (replicate padding), each
  *      divided by its maximum; a pixel is an edge if either exceeds tau;
- *      e_ik = eps if pixel i or k is an edge, else 1.  The decision is taken
- *      in FP32 (see orc_edge_mask).
+ *      e_ik = eps if pixel i or k is an edge, else 1.  Magnitudes, maxima
+ *      and the comparison with tau are FP64.
  *   R16 PCG: Jacobi preconditioner, initial guess D^{-1} x.
  */
 #include <math.h>
@@ -681,57 +681,48 @@ void orc_direct_decompose(int64_t npix, const double *eta, const double *xh, con
 }
 
 /*
- * 3x3 Prewitt gradient magnitude with replicate padding (R14).
- * The edge map is an integer decided by floating point; the paper fixes no
- * precision, so the decision is taken in FP32 (the precision of the
- * reconstructed images) with a fixed order of operations:
- *   gx = sum over t = -1, 0, 1 (in that order) of (x[i+t][j+1] - x[i+t][j-1]),
+ * 3x3 Prewitt gradient magnitude with replicate padding (R14), FP64:
+ *   gx = sum over t = -1, 0, 1 of (x[i+t][j+1] - x[i+t][j-1]),
  *   gy = sum over t = -1, 0, 1 of (x[i+1][j+t] - x[i-1][j+t]),
- *   |g| = sqrtf(gx*gx + gy*gy), edge where |g| / max|g| > tau (FP32 divide).
+ *   |g| = sqrt(gx^2 + gy^2), indices clamped to the image.
  */
-static void prewitt_f32(int n, const double *x, float *mag)
+void orc_prewitt(int n, const double *x, double *mag)
 {
     for (int i = 0; i < n; ++i)
         for (int j = 0; j < n; ++j) {
-            float gx = 0.0f, gy = 0.0f;
+            double gx = 0.0, gy = 0.0;
             int jl = j - 1 < 0 ? 0 : j - 1, jr = j + 1 >= n ? n - 1 : j + 1;
             int iu = i - 1 < 0 ? 0 : i - 1, id = i + 1 >= n ? n - 1 : i + 1;
             for (int t = -1; t <= 1; ++t) {
                 int ii = i + t < 0 ? 0 : (i + t >= n ? n - 1 : i + t);
                 int jj = j + t < 0 ? 0 : (j + t >= n ? n - 1 : j + t);
-                gx = gx + ((float)x[(int64_t)ii * n + jr] - (float)x[(int64_t)ii * n + jl]);
-                gy = gy + ((float)x[(int64_t)id * n + jj] - (float)x[(int64_t)iu * n + jj]);
+                gx += x[(int64_t)ii * n + jr] - x[(int64_t)ii * n + jl];
+                gy += x[(int64_t)id * n + jj] - x[(int64_t)iu * n + jj];
             }
-            mag[(int64_t)i * n + j] = sqrtf(gx * gx + gy * gy);
+            mag[(int64_t)i * n + j] = sqrt(gx * gx + gy * gy);
         }
 }
 
-void orc_prewitt(int n, const double *x, double *mag)
-{
-    int64_t N = (int64_t)n * n;
-    float *m = (float *)malloc(sizeof(float) * (size_t)N);
-    prewitt_f32(n, x, m);
-    for (int64_t p = 0; p < N; ++p) mag[p] = (double)m[p];
-    free(m);
-}
-
-/* Edge mask (1 = edge) from both energy images (R14), decided in FP32. */
+/*
+ * Edge mask (1 = edge) from both energy images (R14), decided in FP64: a
+ * pixel is an edge when its Prewitt magnitude divided by the image's largest
+ * magnitude exceeds tau in either image.
+ */
 void orc_edge_mask(int n, const double *xh, const double *xl, double tau, uint8_t *mask)
 {
     int64_t N = (int64_t)n * n;
-    float *mh = (float *)malloc(sizeof(float) * (size_t)N);
-    float *ml = (float *)malloc(sizeof(float) * (size_t)N);
-    prewitt_f32(n, xh, mh);
-    prewitt_f32(n, xl, ml);
-    float Mh = 0.0f, Ml = 0.0f;
+    double *mh = (double *)malloc(sizeof(double) * (size_t)N);
+    double *ml = (double *)malloc(sizeof(double) * (size_t)N);
+    orc_prewitt(n, xh, mh);
+    orc_prewitt(n, xl, ml);
+    double Mh = 0.0, Ml = 0.0;
     for (int64_t p = 0; p < N; ++p) {
         if (mh[p] > Mh) Mh = mh[p];
         if (ml[p] > Ml) Ml = ml[p];
     }
-    const float t = (float)tau;
     for (int64_t p = 0; p < N; ++p) {
-        int eh = Mh > 0.0f && mh[p] / Mh > t;
-        int el = Ml > 0.0f && ml[p] / Ml > t;
+        int eh = Mh > 0.0 && mh[p] / Mh > tau;
+        int el = Ml > 0.0 && ml[p] / Ml > tau;
         mask[p] = (uint8_t)(eh || el);
     }
     free(mh);

@@ -18,7 +18,7 @@ from typing import List, Optional, Sequence, Tuple
 from . import _build
 
 __all__ = ["Geometry", "Plan", "AdmParams", "PlsParams", "AdmReport", "AdmProfile", "DectError",
-           "load", "project", "backproject", "adm_tv", "pls_decompose", "kernel_launches",
+           "load", "project", "backproject", "adm_tv", "pls_decompose", "pls_edge_mask", "kernel_launches",
            "library_path"]
 
 
@@ -87,6 +87,7 @@ _SIGS = {
     "dect_pls_decompose": (C.c_int, [_P, C.c_int, C.c_int, C.POINTER(_PlsParams), _P, _P, _P]),
     "dect_adm_tv_groups": (C.c_int, [C.POINTER(_AdmGroup), C.c_int, C.POINTER(_AdmParams), C.c_int, _P]),
     "dect_pls_decompose_noalloc": (C.c_int, [_P, C.c_int, C.c_int, C.POINTER(_PlsParams), _P, _P, _P]),
+    "dect_pls_edge_mask": (C.c_int, [_P, C.c_int, C.c_int, C.c_double, _P, _P]),
     "dect_kernel_launches": (C.c_int64, []),
     "dect_cnn_num_params": (C.c_int64, []),
     "dect_cnn_create": (C.c_int, [C.c_int, C.c_int, C.POINTER(_P)]),
@@ -427,6 +428,21 @@ def pls_decompose(x, params: PlsParams, u=None, stream=None):
                                      _stream(stream)), "dect_pls_decompose")
     reps = [(tuple(r.iters), tuple(r.relres)) for r in rep[:batch]]
     return u, reps
+
+
+def pls_edge_mask(x, tau: float, mask=None, stream=None):
+    """Edge map of Eq. (14) as the decomposition decides it: x [B, 2, n, n] -> uint8 [B, n, n]."""
+    import torch
+    if x.dim() != 4 or x.shape[1] != 2 or x.shape[2] != x.shape[3]:
+        raise DectError("x must be [B, 2, n, n]")
+    n = x.shape[-1]
+    batch = x.shape[0]
+    dev = x.device.index
+    if mask is None:
+        mask = torch.empty((batch, n, n), dtype=torch.uint8, device=x.device)
+    _check(load().dect_pls_edge_mask(_ptr(x, torch.float32, dev), n, batch, float(tau),
+                                     _ptr(mask, torch.uint8, dev), _stream(stream)), "dect_pls_edge_mask")
+    return mask
 
 
 # Limits of the allocation-free decomposition (include/dect.h).

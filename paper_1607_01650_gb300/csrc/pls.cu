@@ -11,8 +11,10 @@
 // Vectors: v = 2 s + m (slice s, material m) at u + v N (the [slice][2][n][n]
 // layout of the input and output); the CG runs
 // all vectors of the batch in lockstep with per-vector step sizes and stop
-// flags.  The edge decision is taken in FP32 with a fixed order of
-// operations (the paper fixes no precision for it).
+// flags.  The edge decision is taken in FP32 (the precision of the
+// reconstructed images; the paper fixes none for it): it can differ from the
+// FP64 decision only at pixels whose normalised magnitude lies within FP32
+// rounding of the threshold.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -114,7 +116,8 @@ __device__ __forceinline__ float prewitt_at(const float *__restrict__ x, int n, 
     return __fsqrt_rn(__fadd_rn(__fmul_rn(gx, gx), __fmul_rn(gy, gy)));
 }
 
-// d = D^{-1} x (FP64), written as the initial u; Prewitt magnitudes and their maxima.
+// d = D^{-1} x (FP64), written as the initial u (skipped when u is null);
+// Prewitt magnitudes and their maxima.
 __global__ void k_prep(const float *__restrict__ x, int n, int64_t N, double a, double b, double c,
                        double e, float *__restrict__ u, float *__restrict__ mh,
                        float *__restrict__ ml, int *__restrict__ maxbits)
@@ -128,8 +131,10 @@ __global__ void k_prep(const float *__restrict__ x, int n, int64_t N, double a, 
         const double h = xs[p], l = ls[p];
         const double d1 = __ddiv_rn(__dsub_rn(__dmul_rn(e, h), __dmul_rn(b, l)), det);
         const double d2 = __ddiv_rn(__dadd_rn(__dmul_rn(-c, h), __dmul_rn(a, l)), det);
-        u[(int64_t)(2 * s) * N + p] = (float)d1;
-        u[(int64_t)(2 * s + 1) * N + p] = (float)d2;
+        if (u) {
+            u[(int64_t)(2 * s) * N + p] = (float)d1;
+            u[(int64_t)(2 * s + 1) * N + p] = (float)d2;
+        }
         const int i = (int)(p / n), j = (int)(p % n);
         const float g1 = prewitt_at(xs, n, i, j), g2 = prewitt_at(ls, n, i, j);
         mh[(int64_t)s * N + p] = g1;
@@ -479,6 +484,37 @@ extern "C" dect_status dect_pls_decompose(const float *x, int n, int batch, cons
             }
     }
     (void)dev;
+    return DECT_OK;
+}
+
+extern "C" dect_status dect_pls_edge_mask(const float *x, int n, int batch, double edge_tau,
+                                          uint8_t *mask, dect_stream stream)
+{
+    if (n < 1 || batch < 0 || n > 16384 || !std::isfinite(edge_tau)) return DECT_ERR_INVALID_ARG;
+    if (batch == 0) return DECT_OK;
+    if (!x || !mask || batch > 65535) return DECT_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    const int64_t N = (int64_t)n * n;
+    const int64_t want = (N + kBlock - 1) / kBlock;
+    const int gx = (int)std::max<int64_t>(1, std::min<int64_t>(want, std::max(1, (kSMs * 8) / batch)));
+    const size_t mag_bytes = ((size_t)batch * N * 4 + 255) & ~(size_t)255;
+    char *base = nullptr;
+    DECT_CUDA(cudaMallocAsync((void **)&base, 2 * mag_bytes + (size_t)2 * batch * 4, s));
+    float *mh = (float *)base, *ml = (float *)(base + mag_bytes);
+    int *maxbits = (int *)(base + 2 * mag_bytes);
+    cudaError_t err = cudaMemsetAsync(maxbits, 0, (size_t)2 * batch * 4, s);
+    if (err == cudaSuccess) {
+        dim3 gs((unsigned)gx, (unsigned)batch);
+        k_prep<<<gs, kBlock, 0, s>>>(x, n, N, 1.0, 0.0, 0.0, 1.0, nullptr, mh, ml, maxbits);
+        k_mask<<<gs, kBlock, 0, s>>>(mh, ml, N, maxbits, (float)edge_tau, mask);
+        count_launches(2);
+        err = cudaGetLastError();
+    }
+    cudaFreeAsync(base, s);
+    if (err != cudaSuccess) {
+        set_error("dect_pls_edge_mask", err);
+        return DECT_ERR_CUDA;
+    }
     return DECT_OK;
 }
 

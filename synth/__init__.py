@@ -306,3 +306,32 @@ def random_batched_shapes(count: int, seed: int) -> List[Tuple[int, int]]:
     rng = np.random.default_rng(seed)
     ns = [256, 320, 384, 448, 512]
     return [(int(ns[rng.integers(0, 5)]), int(rng.integers(30, 181))) for _ in range(count)]
+
+
+# ---------------------------------------------------------------------------
+# Initial weights of the warm-start network (the learned part of the
+# workload; not in the paper).  Random numbers only: the network itself is
+# defined by the CUDA library and by the oracle, each in its own code.
+# ---------------------------------------------------------------------------
+
+# (input, output) channels of the ten 3x3 convolutions, in parameter order;
+# the 1x1 head (32 weights + 1 bias) follows them.
+CNN_LAYERS = [(1, 32), (32, 32), (32, 64), (64, 64), (64, 128), (128, 128), (192, 64), (64, 64),
+              (96, 32), (32, 32)]
+
+
+def cnn_num_params() -> int:
+    return sum(co * ci * 9 + co for ci, co in CNN_LAYERS) + 33
+
+
+def cnn_init(seed: int) -> np.ndarray:
+    """He-normal 3x3 weights (std sqrt(2 / (9 Cin))), zero biases and a zero
+    head, so that the untrained network x + s * net(x / s) is the identity.
+    Flat float64 vector in the layout of dect_cnn_set_params."""
+    rng = np.random.default_rng(seed)
+    parts = []
+    for cin, cout in CNN_LAYERS:
+        parts.append(rng.standard_normal(cout * cin * 9) * np.sqrt(2.0 / (cin * 9)))
+        parts.append(np.zeros(cout))
+    parts.append(np.zeros(33))
+    return np.concatenate(parts)

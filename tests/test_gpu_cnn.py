@@ -11,6 +11,7 @@ import numpy as np
 import pytest
 
 import oracle
+import synth
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -21,12 +22,12 @@ S = 0.02
 
 
 def _params(seed):
-    p = oracle.cnn_init(seed)
+    p = synth.cnn_init(seed)
     rng = np.random.default_rng(seed + 1)
     p[-33:] = rng.standard_normal(33) * 0.3
     # non-zero biases so every path of the network is exercised
     o = 0
-    for cin, cout in oracle.CNN_LAYERS:
+    for cin, cout in synth.CNN_LAYERS:
         o += cout * cin * 9
         p[o:o + cout] = 0.05 * rng.standard_normal(cout)
         o += cout
@@ -70,7 +71,7 @@ def test_gradient_matches_oracle(net):
     assert np.linalg.norm(g - gref) <= 8e-2 * np.linalg.norm(gref)
     # per layer as well (each layer's gradient block)
     o = 0
-    for cin, cout in oracle.CNN_LAYERS:
+    for cin, cout in synth.CNN_LAYERS:
         n = cout * cin * 9
         blk = slice(o, o + n)
         assert np.linalg.norm(g[blk] - gref[blk]) <= 1.2e-1 * np.linalg.norm(gref[blk]) + 1e-12
@@ -82,7 +83,7 @@ def test_training_reduces_the_loss(net):
     B, H, W = 4, 32, 32
     x = (0.02 * rng.random((B, H, W))).astype(np.float32)
     t = x * 1.1
-    net.set_params(oracle.cnn_init(13).astype(np.float32))
+    net.set_params(synth.cnn_init(13).astype(np.float32))
     xt, tt = torch.tensor(x, device="cuda"), torch.tensor(t, device="cuda")
     l0 = net.loss_grad(xt, tt, S)
     for _ in range(30):

@@ -31,7 +31,7 @@ def test_trained_network_reduces_adm_iterations():
     prm = dect.AdmParams(mu=4.0, rho=256.0)
     pairs = ws.make_pairs(plan, _sinos(g, range(20000, 20256)), prm)
     net = dect.Cnn(max_pixels=64 * 128 * 128)
-    net.set_params(oracle.cnn_init(1).astype(np.float32))
+    net.set_params(synth.cnn_init(1).astype(np.float32))
     losses = ws.train(net, pairs, epochs=6, batch=16, lr=1e-3)
     assert losses[-1] < losses[0]
     # held-out slices

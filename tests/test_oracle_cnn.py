@@ -7,6 +7,7 @@ import numpy as np
 import pytest
 
 import oracle
+import synth
 
 torch = pytest.importorskip("torch")
 F = torch.nn.functional
@@ -18,7 +19,7 @@ def torch_net(p, x, s):
     """Same network written with torch ops (float64, CPU)."""
     i = 0
     W = []
-    for cin, cout in oracle.CNN_LAYERS:
+    for cin, cout in synth.CNN_LAYERS:
         w = p[i:i + cout * cin * 9].view(cout, cin, 3, 3)
         i += cout * cin * 9
         b = p[i:i + cout]
@@ -37,7 +38,7 @@ def torch_net(p, x, s):
 
 
 def _params(seed):
-    p = oracle.cnn_init(seed)
+    p = synth.cnn_init(seed)
     p[-33:] = np.random.default_rng(seed + 1).standard_normal(33) * 0.1
     return p
 
@@ -78,8 +79,8 @@ def test_gradient_matches_finite_differences():
 
 def test_untrained_net_is_the_identity_and_head_bias_shifts():
     x = 0.02 * np.random.default_rng(4).random((8, 12))
-    p = oracle.cnn_init(5)
+    p = synth.cnn_init(5)
     np.testing.assert_array_equal(oracle.cnn_forward(p, x, S), x)
     p[-1] = 0.5
     np.testing.assert_allclose(oracle.cnn_forward(p, x, S), x + S * 0.5, rtol=0, atol=1e-15)
-    assert oracle.cnn_num_params() == 470977
+    assert oracle.cnn_num_params() == 470977 == synth.cnn_num_params() == synth.cnn_init(0).size

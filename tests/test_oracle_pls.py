@@ -98,15 +98,65 @@ def test_prewitt_closed_form_and_mask():
     mag = oracle.prewitt(x)
     want = np.zeros((n, n))
     want[:, 4:6] = 3 * h
-    np.testing.assert_allclose(mag, want, rtol=1e-6, atol=1e-7)   # FP32 decision arithmetic
+    np.testing.assert_allclose(mag, want, atol=1e-14)
     # horizontal step: same response on rows
-    np.testing.assert_allclose(oracle.prewitt(x.T), want.T, rtol=1e-6, atol=1e-7)
+    np.testing.assert_allclose(oracle.prewitt(x.T), want.T, atol=1e-14)
     # mask: either image above tau (after normalising by its own maximum)
     y = np.zeros((n, n))
     y[3:, :] = 0.01
     m = oracle.edge_mask(x, y, 0.5)
     want_m = (want > 0) | (oracle.prewitt(y) / oracle.prewitt(y).max() > 0.5)
     np.testing.assert_array_equal(m.astype(bool), want_m)
+
+
+def test_prewitt_of_a_plane_and_mask_threshold():
+    """A plane x = a i + b j has Prewitt components 6b (along j) and 6a (along i)
+    inside the image and half of that on a replicated border; the mask keeps
+    exactly the pixels whose magnitude over the maximum exceeds tau."""
+    n, a, b = 9, 0.013, -0.004
+    i, j = np.mgrid[0:n, 0:n].astype(np.float64)
+    mag = oracle.prewitt(a * i + b * j)
+    fi = np.where((i == 0) | (i == n - 1), 3.0, 6.0)
+    fj = np.where((j == 0) | (j == n - 1), 3.0, 6.0)
+    want = np.hypot(fi * a, fj * b)
+    np.testing.assert_allclose(mag, want, rtol=1e-13, atol=1e-15)
+    # the magnitudes take 4 distinct values: tau between them selects whole classes
+    levels = np.unique(np.round(want / want.max(), 12))
+    for lo, hi in zip(levels[:-1], levels[1:]):
+        tau = 0.5 * (lo + hi)
+        m = oracle.edge_mask(a * i + b * j, np.zeros((n, n)), tau)
+        np.testing.assert_array_equal(m.astype(bool), want / want.max() > tau)
+    # an empty image has no edges
+    assert not oracle.edge_mask(np.zeros((n, n)), np.zeros((n, n)), 0.2).any()
+
+
+def test_jacobi_diagonal_is_hessian_diagonal():
+    """The PCG preconditioner is the diagonal of (I + gamma L_e) assembled pair
+    by pair from Eq. (14); closed forms: 1 + gamma * (number of in-image
+    neighbours) without edges, 1 + gamma * eps * (that number) when every
+    pixel is an edge."""
+    rng = np.random.default_rng(7)
+    for n, frac in ((7, 0.3), (12, 0.1), (5, 1.0)):
+        mask = (rng.random((n, n)) < frac).astype(np.uint8)
+        gamma, eps = 0.37, 0.05
+        want = np.diag(indep.pls_matrix(mask, gamma, eps)).reshape(n, n)
+        np.testing.assert_allclose(oracle.pls_diag(mask, gamma, eps), want, rtol=1e-15, atol=1e-15)
+    n, gamma, eps = 6, 0.5, 0.05
+    deg = np.full((n, n), 4.0)
+    deg[0, :] -= 1
+    deg[-1, :] -= 1
+    deg[:, 0] -= 1
+    deg[:, -1] -= 1
+    np.testing.assert_array_equal(oracle.pls_diag(np.zeros((n, n), np.uint8), gamma, eps), 1 + gamma * deg)
+    np.testing.assert_allclose(oracle.pls_diag(np.ones((n, n), np.uint8), gamma, eps),
+                               1 + gamma * eps * deg, rtol=1e-15)
+    # one edge pixel lowers the weight of its own four links and of each neighbour's link to it
+    mask = np.zeros((n, n), np.uint8)
+    mask[2, 3] = 1
+    d = oracle.pls_diag(mask, gamma, eps)
+    assert d[2, 3] == 1 + gamma * 4 * eps
+    for (ii, jj) in ((1, 3), (3, 3), (2, 2), (2, 4)):
+        assert abs(d[ii, jj] - (1 + gamma * (3 + eps))) < 1e-15
 
 
 def test_pls_reduces_noise_on_mixture():
