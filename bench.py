@@ -61,7 +61,9 @@ def parse():
     ap.add_argument("--joint", action="store_true",
                     help="paper workload with the TV taken jointly over both energies (joint_tv)")
     ap.add_argument("--bwd-variant", type=int, default=-1,
-                    help="fix the A^T variant (0-5, see dect_plan_get_tuning) instead of autotuning")
+                    help="fix the A^T variant (0-7, see dect_plan_get_tuning) instead of autotuning")
+    ap.add_argument("--fwd-variant", type=int, default=-1,
+                    help="fix the A variant (0-3, see dect_plan_get_fwd_tuning) instead of autotuning")
     ap.add_argument("--train-slices", type=int, default=1024, help="learned workload: training slices")
     ap.add_argument("--epochs", type=int, default=6, help="learned workload: training epochs")
     ap.add_argument("--workload", default="paper", choices=["paper", "batched", "learned", "stress", "fbp"],
@@ -519,6 +521,8 @@ def main():
     plan_s = time.perf_counter() - t0
     if args.bwd_variant >= 0:
         plan.set_tuning(min(64, 1 << (2 * S - 1).bit_length()), args.bwd_variant)
+    if args.fwd_variant >= 0:
+        plan.set_fwd_tuning(min(64, 1 << (2 * S - 1).bit_length()), args.fwd_variant)
     m_host = torch.from_numpy(make_inputs(geom, seeds_for(rank, S), STRESS_I0 if stress else I0)).pin_memory()
     m_dev = m_host.to("cuda")
     x_dev = torch.zeros((S, 2, geom.n, geom.n), device="cuda")
@@ -605,10 +609,14 @@ def main():
     p0 = state["prof"][-1]
     width = min(64, 1 << (2 * S - 1).bit_length())
     choice, _ = plan.tuning(width)
-    names = ["k_bwd<tile4>", "k_bwd<tile8>", "k_bwd<tile16>", "k_bwd_win", "k_bwd<1k,8x8>", "k_bwd<1k,16x8>"]
+    names = ["k_bwd<tile4>", "k_bwd<tile8>", "k_bwd<tile16>", "k_bwd_win", "k_bwd<1k,8x8>", "k_bwd<1k,16x8>",
+             "k_bwd<1k,8x8,w8>", "k_bwd<1k,8x8,w8,2px>"]
     bwd_name = names[choice] if 0 <= choice < len(names) else "k_bwd"
+    fchoice, _ = plan.fwd_tuning(width)
+    fnames = ["k_fwd", "k_fwd<w8,r4>", "k_fwd<w8,r2>"]
+    fwd_name = fnames[fchoice] if 0 <= fchoice < len(fnames) else "k_fwd"
     if fwd_ms >= bwd_ms:
-        kname, avg_ms, bytes_ = "k_fwd", fwd_ms / max(fwd_n, 1), p0.table_bytes_fwd
+        kname, avg_ms, bytes_ = fwd_name, fwd_ms / max(fwd_n, 1), p0.table_bytes_fwd
     else:
         kname, avg_ms, bytes_ = bwd_name, bwd_ms / max(bwd_n, 1), p0.table_bytes_bwd
     peak, peak_src = measured_peaks()
@@ -620,6 +628,19 @@ def main():
                 "fwd_ms_avg": fwd_ms / max(fwd_n, 1), "bwd_ms_avg": bwd_ms / max(bwd_n, 1)}
 
     clocks = clk.summary()
+    # the bound that applies to the table kernels: loaded data returned from
+    # L1 to registers, 128 B per cycle per SM; gathered bytes = 4 NB per entry
+    bytes_fixed = 8.0 * plan.nnz + 8.0 * ((plan.n_rays if kname.startswith("k_fwd") else plan.n_pixels) + 1)
+    per_chan = 4.0 * (plan.n_pixels + plan.n_rays) if kname.startswith("k_fwd") else 4.0 * (plan.n_rays + 3 * plan.n_pixels)
+    nb_mean = (bytes_ - bytes_fixed) / per_chan
+    gathered = 4.0 * nb_mean * plan.nnz
+    sm_mhz = clocks.get("sm_mhz") or 2070.0
+    l1_peak = 128.0 * 152 * sm_mhz * 1e6 / 1e9
+    roofline_l1 = {"bound": "l1_writeback", "kernel": kname,
+                   "achieved": round(gathered / (avg_ms / 1e3) / 1e9, 1), "peak": round(l1_peak, 1),
+                   "peak_source": "128 B per cycle per SM returned from L1 to registers x 152 SMs x sampled SM clock",
+                   "unit": "GB/s", "frac": round(gathered / (avg_ms / 1e3) / 1e9 / l1_peak, 4),
+                   "gathered_bytes": int(gathered), "mean_channels": round(nb_mean, 2)}
     mean_it = float(np.mean(state["iters"]))
     cpu = None
     if world == 1 and not args.no_cpu_baseline and stress:
@@ -661,10 +682,11 @@ def main():
                    "all_converged": bool(state.get("conv", False)),
                    "mean_pcg_iterations": float(np.mean(state["pls_iters"])),
                    "plan_seconds": round(plan_s, 3), "nnz": plan.nnz,
-                   "bwd_autotune": dict(zip(("choice", "us"), plan.tuning(min(64, 1 << (2 * S - 1).bit_length())))),
+                   "bwd_autotune": dict(zip(("choice", "us"), plan.tuning(width))),
+                   "fwd_autotune": dict(zip(("choice", "us"), plan.fwd_tuning(width))),
                    "l2": "inputs larger than L2 (tables %.0f MB)" % (plan.table_bytes / 1e6),
                    "parallelism": "replicas" if world > 1 else "1 GPU"},
-        "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+        "roofline": roofline, "roofline_l1": roofline_l1, "cpu_baseline": cpu, "e2e": e2e,
         "gpu_launches": int(launches), "clocks": clocks,
     }
     print(json.dumps(line), flush=True)

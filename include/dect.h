@@ -177,6 +177,12 @@ typedef struct {
     int converged;      /* 1 if the relative-objective test fired                       */
     double objective;   /* Phi = |grad f|_TV + mu/2 |A f - g|^2 at the result (f = beta x) */
     double rel_change;  /* last relative objective change                               */
+    double primal_res;  /* |A f - g| at the result, recomputed from f at the end of the
+                           call (FP32 projection, FP64 norm)                             */
+    double resid_drift; /* |r - (A f - g)|: how far the residual r carried through the
+                           iterations by r <- r - alpha A G (Eq. (9) by linearity) has
+                           moved from the recomputed one; `objective` and the stopping
+                           test use the carried r                                         */
 } dect_adm_report;
 
 /*
@@ -347,11 +353,15 @@ dect_status dect_adm_tv_ex(const dect_plan *plan, const float *m, float *x, int 
  *   0-2 L1-cached gather with 4x4 / 8x8 / 16x16 pixel tiles per 256-thread block,
  *   3   shared-memory sinogram windows (cp.async staged),
  *   4-5 L1-cached gather, one 1024-thread block per SM, tiles of two / four
- *       block steps (8x8 / 16x8 pixels at 32 and 64 channels, 8x16 / 16x16 below).
+ *       block steps (8x8 / 16x8 pixels at 32 and 64 channels, 8x16 / 16x16 below),
+ *   6-7 (16, 32 or 64 channels; otherwise 4 is used) each lane gathers 8
+ *       channels of an entry (two 16-byte loads), so fewer lanes receive
+ *       each entry's (index, length): 6 with the lanes and tiles of 4, 7 with
+ *       16 lanes per pixel over 8x8 tiles.
  * *choice = -1 until an ADM call with that width has run.  Host memory:
  * us has DECT_BWD_VARIANTS elements.
  */
-#define DECT_BWD_VARIANTS 6
+#define DECT_BWD_VARIANTS 8
 dect_status dect_plan_get_tuning(const dect_plan *plan, int images, int *choice,
                                  float us[DECT_BWD_VARIANTS]);
 
@@ -359,6 +369,29 @@ dect_status dect_plan_get_tuning(const dect_plan *plan, int images, int *choice,
  * or pass choice = -1 to let the next ADM call time the candidates again.
  * Variant 3 falls back to 1 where the windows do not fit shared memory. */
 dect_status dect_plan_set_tuning(dect_plan *plan, int images, int choice);
+
+/*
+ * Autotuner record of the forward projector A G inside dect_adm_tv, as
+ * dect_plan_get_tuning gives it for A^T: the variant chosen for batch width
+ * `images` and the measured median time of each (microseconds; -1 = not
+ * timed).  All variants run one 1024-thread block per SM and a warp per ray:
+ *   0 each lane gathers 4 channels of an entry (one 16-byte load); the row's
+ *     table entries are loaded by the warp together and handed to the lanes
+ *     by shuffles,
+ *   1 each lane gathers 8 channels of an entry (two 16-byte loads), so fewer
+ *     lanes receive each entry's (index, length), four entries per lane in
+ *     flight; 16, 32 or 64 channels only (otherwise 0 is used),
+ *   2 as 1 with two entries per lane in flight.
+ * Timed on the set-up projection r = A f - beta m of the first ADM call
+ * with that width.  Host memory: us has DECT_FWD_VARIANTS elements.
+ */
+#define DECT_FWD_VARIANTS 3
+dect_status dect_plan_get_fwd_tuning(const dect_plan *plan, int images, int *choice,
+                                     float us[DECT_FWD_VARIANTS]);
+
+/* Fix the A variant for batch width `images`, or -1 to time the candidates
+ * again on the next ADM call with that width. */
+dect_status dect_plan_set_fwd_tuning(dect_plan *plan, int images, int choice);
 
 /* Number of kernels libdect has launched in this process so far (kernel
  * launches plus the kernel nodes of every graph launch). */

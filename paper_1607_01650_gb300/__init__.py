@@ -47,7 +47,7 @@ class _AdmParams(C.Structure):
 
 class _AdmReport(C.Structure):
     _fields_ = [("iters", C.c_int), ("converged", C.c_int), ("objective", C.c_double),
-                ("rel_change", C.c_double)]
+                ("rel_change", C.c_double), ("primal_res", C.c_double), ("resid_drift", C.c_double)]
 
 
 class _AdmProfile(C.Structure):
@@ -101,6 +101,8 @@ _SIGS = {
     "dect_selftest_bounded_wait": (C.c_int, [C.c_uint, _P]),
     "dect_plan_get_tuning": (C.c_int, [_P, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_float)]),
     "dect_plan_set_tuning": (C.c_int, [_P, C.c_int, C.c_int]),
+    "dect_plan_get_fwd_tuning": (C.c_int, [_P, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_float)]),
+    "dect_plan_set_fwd_tuning": (C.c_int, [_P, C.c_int, C.c_int]),
     "dect_status_string": (C.c_char_p, [C.c_int]),
     "dect_last_error": (C.c_char_p, []),
     "dect_version": (C.c_int, []),
@@ -195,6 +197,8 @@ class Plan:
         info = _PlanInfo()
         _check(lib.dect_plan_get_info(h, C.byref(info)), "dect_plan_get_info")
         self.nnz = int(info.nnz)
+        self.n_pixels = int(info.n_pixels)
+        self.n_rays = int(info.n_rays)
         self.table_bytes = int(info.table_bytes)
         self.n_grid_aligned = int(info.n_grid_aligned)
 
@@ -223,6 +227,17 @@ class Plan:
     def set_tuning(self, images: int, choice: int):
         """Force the A^T variant for a batch width (-1: re-time on the next ADM call)."""
         _check(load().dect_plan_set_tuning(self._h, images, choice), "dect_plan_set_tuning")
+
+    def fwd_tuning(self, images: int):
+        """(chosen A variant, [median us of each variant]) for a batch width; see dect.h."""
+        ch = C.c_int(-1)
+        us = (C.c_float * FWD_VARIANTS)()
+        _check(load().dect_plan_get_fwd_tuning(self._h, images, C.byref(ch), us), "dect_plan_get_fwd_tuning")
+        return ch.value, list(us)
+
+    def set_fwd_tuning(self, images: int, choice: int):
+        """Force the A variant for a batch width (-1: re-time on the next ADM call)."""
+        _check(load().dect_plan_set_fwd_tuning(self._h, images, choice), "dect_plan_set_fwd_tuning")
 
     def table(self):
         """(rowptr int64 [M+1], pix int32 [nnz], len float32 [nnz]) as numpy arrays."""
@@ -284,7 +299,8 @@ def fbp(plan: Plan, m, x=None, stream=None):
 
 
 BB1, CAUCHY = 0, 1
-BWD_VARIANTS = 6                        # DECT_BWD_VARIANTS in include/dect.h
+BWD_VARIANTS = 8                        # DECT_BWD_VARIANTS in include/dect.h
+FWD_VARIANTS = 3                        # DECT_FWD_VARIANTS in include/dect.h
 
 
 @dataclasses.dataclass
@@ -315,6 +331,12 @@ class AdmReport:
     converged: bool
     objective: float
     rel_change: float
+    primal_res: float = 0.0    # |A f - g| recomputed from the result
+    resid_drift: float = 0.0   # |r_carried - (A f - g)|
+
+
+def _report(r) -> AdmReport:
+    return AdmReport(r.iters, bool(r.converged), r.objective, r.rel_change, r.primal_res, r.resid_drift)
 
 
 @dataclasses.dataclass
@@ -350,7 +372,7 @@ def adm_tv(plan: Plan, m, params: AdmParams, x=None, stream=None, profile: bool 
                                  C.cast(rep, C.c_void_p),
                                  C.cast(C.pointer(prof), C.c_void_p) if prof is not None else None,
                                  _stream(stream)), "dect_adm_tv")
-    reps = [AdmReport(r.iters, bool(r.converged), r.objective, r.rel_change) for r in rep[:2 * S]]
+    reps = [_report(r) for r in rep[:2 * S]]
     if profile:
         return x, reps, AdmProfile(prof.fwd_ms_total, prof.bwd_ms_total, prof.fwd_launches,
                                    prof.bwd_launches, prof.table_bytes_fwd, prof.table_bytes_bwd)
@@ -382,8 +404,7 @@ def adm_tv_groups(groups, params: AdmParams, workers: int = 0, stream=None):
         out.append((x, rep, S))
     _check(load().dect_adm_tv_groups(cg, len(groups), C.byref(params._c()), workers, _stream(stream)),
            "dect_adm_tv_groups")
-    return [(x, [AdmReport(r.iters, bool(r.converged), r.objective, r.rel_change) for r in rep[:2 * S]])
-            for x, rep, S in out]
+    return [(x, [_report(r) for r in rep[:2 * S]]) for x, rep, S in out]
 
 
 def kernel_launches() -> int:

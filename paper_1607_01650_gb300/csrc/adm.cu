@@ -367,7 +367,10 @@ __global__ void __launch_bounds__(TvShape<NB>::BLK) k_tv(const float *__restrict
 // G = mu A^T r + grad^T p over the pixel-major table.  A block of BLK
 // threads takes TW x TH pixel tiles (BLK / G_ pixels at a time), so the
 // sinogram lines its pixels gather are shared in L1.
-template <int NB, int G_, int TW, int TH, int BLK>
+// VWL = 4: lanes gather 4 images of an entry, entries broadcast through a
+// per-warp shared-memory slot; VWL = 8 or 16: lanes gather VWL images of an
+// entry, R rounds in flight (row_dot_w; NB >= 16 only).
+template <int NB, int G_, int TW, int TH, int BLK, int VWL = 4, int R = 2>
 __global__ void __launch_bounds__(BLK) k_bwd(const int64_t *__restrict__ colptr,
                                                 const Entry *__restrict__ tent,
                                                 const float *__restrict__ r, const float *__restrict__ p,
@@ -383,6 +386,7 @@ __global__ void __launch_bounds__(BLK) k_bwd(const int64_t *__restrict__ colptr,
     const int ntiles = tiles_x * ((C.n + TH - 1) / TH);
     Vec<VW> nrm[1];
     nrm[0].zero();
+    const unsigned long long pol = l2_evict_last_policy();
     for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
         const int ty = tile / tiles_x, tx = tile % tiles_x;
         for (int s0 = 0; s0 < TW * TH; s0 += RPS) {
@@ -395,7 +399,11 @@ __global__ void __launch_bounds__(BLK) k_bwd(const int64_t *__restrict__ colptr,
                 b = colptr[pix];
                 e = colptr[pix + 1];
             }
-            Vec<VW> acc = row_dot<NB, G_, true, true>(tent, b, e, r, 0, lr);
+            Vec<VW> acc;
+            if constexpr (VWL > 4 && NB >= 16)
+                acc = row_dot_w<NB, G_, VWL, R>(tent, b, e, lr, r, pol);
+            else
+                acc = row_dot<NB, G_, true, true>(tent, b, e, r, 0, lr);
             if (ok && grp == 0) {
                 const int64_t o = pix * NB + vl * VW;
                 Vec<VW> p0 = ld_v<VW>(p + o), p1 = ld_v<VW>(p + sN + o), pd, pr;
@@ -639,13 +647,19 @@ __device__ void adm_finish(const AdmConst &C, const AdmDev &D)
 // MODE 1: |grad G|^2, then q = A G over the ray-major table and |q|^2; the
 // last block forms the step.  MODE 0: r = A f - beta m (set-up).  MODE 2:
 // r = A f - beta m and |r|^2 into the RR slot (residual of the projected
-// f-step, run after k_tv).
-template <int NB, int G_, int MODE, int BLK = kFwdBlock>
+// f-step, run after k_tv).  MODE 3 (check of the result): the exact
+// residual A f - beta m into dst, |A f - beta m|^2 into the QQ slot and
+// |r_carried - (A f - beta m)|^2 into the GG slot (r_carried = rc).
+// VWL = 4: lanes gather 4 images of an entry (row_dot_g); VWL = 8 or 16:
+// lanes gather VWL images of an entry, R rounds in flight (row_dot_w; NB >=
+// 16 only).
+template <int NB, int G_, int MODE, int VWL = 4, int R = 2, int BLK = kFwdBlock>
 __global__ void __launch_bounds__(BLK) k_fwd(const int64_t *__restrict__ rowptr,
                                                 const Entry *__restrict__ ent,
                                                 const float *__restrict__ src, float *__restrict__ dst,
                                                 const float *__restrict__ m_planar,
-                                                const float *__restrict__ beta_img, AdmConst C, AdmDev D)
+                                                const float *__restrict__ beta_img, AdmConst C, AdmDev D,
+                                                const float *__restrict__ rc = nullptr)
 {
     constexpr int VW = Batch<NB>::VW, LPE = Batch<NB>::CPB, CPB = Batch<NB>::CPB;
     __shared__ double smem[reduce_smem_doubles<NB, BLK>(2)];
@@ -671,14 +685,20 @@ __global__ void __launch_bounds__(BLK) k_fwd(const int64_t *__restrict__ rowptr,
             }
         }
     }
-    for (int64_t row0 = (int64_t)blockIdx.x * rpb; row0 < C.M; row0 += (int64_t)gridDim.x * rpb) {
+    const int64_t rstep = (int64_t)gridDim.x * rpb;
+    const unsigned long long pol = l2_evict_last_policy();
+    for (int64_t row0 = (int64_t)blockIdx.x * rpb; row0 < C.M; row0 += rstep) {
         const int64_t ray = row0 + threadIdx.x / G_;
         int64_t b = 0, e = 0;
         if (ray < C.M) {
             b = rowptr[ray];
             e = rowptr[ray + 1];
         }
-        Vec<VW> acc = row_dot<NB, G_, true>(ent, b, e, src, 0, lr);
+        Vec<VW> acc;
+        if constexpr (VWL > 4 && NB >= 16)
+            acc = row_dot_w<NB, G_, VWL, R>(ent, b, e, lr, src, pol);
+        else
+            acc = row_dot<NB, G_, true>(ent, b, e, src, 0, lr);
         if (ray < C.M && grp == 0) {
             if (MODE != 1) {
 #pragma unroll
@@ -687,7 +707,15 @@ __global__ void __launch_bounds__(BLK) k_fwd(const int64_t *__restrict__ rowptr,
                     const int im = D.slot[img];
                     float g = im >= 0 ? beta_img[img] * m_planar[(int64_t)im * C.M + ray] : 0.f;
                     acc.v[c] -= g;
-                    if (MODE == 2) nrm[0].v[c] = fmaf(acc.v[c], acc.v[c], nrm[0].v[c]);
+                    if (MODE >= 2) nrm[0].v[c] = fmaf(acc.v[c], acc.v[c], nrm[0].v[c]);
+                }
+                if (MODE == 3) {
+                    const Vec<VW> rv = ld_v<VW>(rc + ray * NB + vl * VW);
+#pragma unroll
+                    for (int c = 0; c < VW; ++c) {
+                        const float d = rv.v[c] - acc.v[c];
+                        nrm[1].v[c] = fmaf(d, d, nrm[1].v[c]);
+                    }
                 }
             } else {
 #pragma unroll
@@ -702,8 +730,17 @@ __global__ void __launch_bounds__(BLK) k_fwd(const int64_t *__restrict__ rowptr,
     } else if (MODE == 2) {
         Vec<VW> rr[1] = {nrm[0]};
         reduce_images<NB, 1, BLK>(rr, part_of<NB>(D, C_RES), D.red + R_RR * NB, D.ctr + C_RES, smem);
+    } else if (MODE == 3) {
+        // QQ and GG are adjacent slots: (|A f - beta m|^2, |r_carried - (A f - beta m)|^2)
+        static_assert(R_GG == R_QQ + 1, "slot order");
+        reduce_images<NB, 2, BLK>(nrm, part_of<NB>(D, C_RES), D.red + R_QQ * NB, D.ctr + C_RES, smem);
     }
 }
+
+// Exact residual of the current f (f_cur) against the carried one, for the
+// reports: QQ <- |A f - beta m|^2, GG <- |r - (A f - beta m)|^2 (q is
+// overwritten; call only where q is no longer needed).
+
 
 // planar x[img][N] (times beta) -> interleaved f[N][NB]; and back (divided by beta).
 template <int NB>
@@ -778,6 +815,40 @@ struct Kern {
     static constexpr int GF = 32;                  // lanes per ray row
 };
 
+// A variants (autotuner candidates, one 1024-thread block per SM, a warp
+// per ray): 0 lanes gather 4 images of an entry; 1 lanes gather 8 images
+// (row_dot_w), four rounds of gathers in flight; 2 as 1 with two rounds.
+// Below 16 images only variant 0 exists (the others fall back to it).
+constexpr int kFwdVariants = DECT_FWD_VARIANTS;
+
+template <int NB, int MODE>
+void launch_fwd(const dect_plan *P, int variant, const float *src, float *dst, const float *m,
+                const float *beta, const AdmConst &C, const AdmDev &D, cudaStream_t s,
+                const float *rc = nullptr)
+{
+    constexpr int GF = Kern<NB>::GF;
+    switch (NB >= 16 ? variant : 0) {
+    case 1:
+        k_fwd<NB, GF, MODE, 8, 4, 1024><<<kFwdGrid, 1024, 0, s>>>(P->rowptr, P->ent, src, dst, m, beta, C, D, rc);
+        break;
+    case 2:
+        k_fwd<NB, GF, MODE, 8, 2, 1024><<<kFwdGrid, 1024, 0, s>>>(P->rowptr, P->ent, src, dst, m, beta, C, D, rc);
+        break;
+    default:
+        k_fwd<NB, GF, MODE, 4><<<kFwdGrid, 1024, 0, s>>>(P->rowptr, P->ent, src, dst, m, beta, C, D, rc);
+        break;
+    }
+}
+
+template <int NB>
+void launch_residual_check(const dect_plan *P, int variant, const float *f_cur, float *q, const float *r,
+                           const float *m, const float *beta, const AdmConst &C, const AdmDev &D,
+                           cudaStream_t s)
+{
+    launch_fwd<NB, 3>(P, variant, f_cur, q, m, beta, C, D, s, r);
+    count_launches(1);
+}
+
 struct Work {
     float *f[2], *G, *lam, *z, *p, *r, *q, *beta;
     const float *m;  // measured sinograms, planar [nimg][M]
@@ -789,6 +860,7 @@ struct Work {
     int win_grid;     // > 0: A^T through shared-memory windows with this grid
     size_t win_smem;  // its dynamic shared memory
     int bwd;          // A^T variant in use
+    int fwd;          // A variant in use
 };
 
 constexpr size_t kWinSmemMax = 210 * 1024;
@@ -825,7 +897,9 @@ cudaError_t setup_window(const dect_plan *P, Work &W)
 // 16x16 pixel tiles per 256-thread block; 3 shared-memory sinogram windows;
 // 4-5 L1-cached gather with one 1024-thread block per SM over tiles of two
 // or four block steps (8 x 8 / 16 x 8 pixels at 32 lanes per pixel, 8 x 16 /
-// 16 x 16 at 16), whose lines then stay in one L1.
+// 16 x 16 at 16), whose lines then stay in one L1; 6-7 lanes gather 8
+// images of an entry (row_dot_w, NB >= 16 only): 6 with the lanes and tiles
+// of 4; 7 with 16 lanes per pixel (two pixels per warp) over 8 x 8 tiles.
 constexpr int kBwdVariants = DECT_BWD_VARIANTS;
 
 template <int NB>
@@ -845,6 +919,14 @@ void launch_bwd(const dect_plan *P, const Work &W, const AdmConst &C, int varian
         break;
     case 5:
         k_bwd<NB, GB, 16, RPS1k / 4, 1024><<<kSMs, 1024, 0, s>>>(P->colptr, P->tent, W.r, W.p, W.G, C, W.D);
+        break;
+    case 6:  // 8 images per lane, the lanes and tiles of variant 4
+        if constexpr (NB >= 16)
+            k_bwd<NB, GB, 8, RPS1k / 4, 1024, 8, 4><<<kSMs, 1024, 0, s>>>(P->colptr, P->tent, W.r, W.p, W.G, C, W.D);
+        break;
+    case 7:  // 8 images per lane, 16 lanes per pixel (two pixels per warp), 8 x 8 tiles
+        if constexpr (NB >= 16)
+            k_bwd<NB, 16, 8, 8, 1024, 8, 4><<<kSMs, 1024, 0, s>>>(P->colptr, P->tent, W.r, W.p, W.G, C, W.D);
         break;
     case 3: {
         WinArgs A{P->tmaj, P->tbase, P->tpo, P->wray0, P->wcnt, P->woff, P->wtot, P->nv, P->nvp,
@@ -875,6 +957,7 @@ cudaError_t tune_bwd(const dect_plan *P, Work &W, const AdmConst &C, cudaStream_
     if (P->bwd_choice[idx] >= 0) {
         W.bwd = P->bwd_choice[idx];
         if (W.bwd == 3 && W.win_grid <= 0) W.bwd = 1;
+        if (W.bwd >= 6 && NB < 16) W.bwd = 4;
         return cudaSuccess;
     }
     cudaEvent_t a = nullptr, b = nullptr;
@@ -885,6 +968,7 @@ cudaError_t tune_bwd(const dect_plan *P, Work &W, const AdmConst &C, cudaStream_
     for (int v = 0; v < kBwdVariants && e == cudaSuccess; ++v) {
         P->bwd_us[idx][v] = -1.f;
         if (v == 3 && W.win_grid <= 0) continue;
+        if (v >= 6 && NB < 16) continue;  // wide-lane variants need 16 images
         launch_bwd<NB>(P, W, C, v, s);
         count_launches(1);
         float t[3];
@@ -914,6 +998,55 @@ cudaError_t tune_bwd(const dect_plan *P, Work &W, const AdmConst &C, cudaStream_
     return cudaSuccess;
 }
 
+// Time every A variant on the set-up projection r = A f - beta m (CUDA
+// events, median of three launches after one warm-up) and keep the fastest
+// in the plan.  The caller runs the set-up projection again afterwards with
+// the chosen variant (the variants sum in different orders).
+template <int NB>
+cudaError_t tune_fwd(const dect_plan *P, Work &W, const AdmConst &C, cudaStream_t s)
+{
+    const int idx = nb_index<NB>();
+    if (P->fwd_choice[idx] >= 0) {
+        W.fwd = P->fwd_choice[idx];
+        return cudaSuccess;
+    }
+    cudaEvent_t a = nullptr, b = nullptr;
+    cudaError_t e = cudaEventCreate(&a);
+    if (e == cudaSuccess) e = cudaEventCreate(&b);
+    int best = 0;
+    float best_us = 1e30f;
+    for (int v = 0; v < kFwdVariants && e == cudaSuccess; ++v) {
+        P->fwd_us[idx][v] = -1.f;
+        if (v > 0 && NB < 16) continue;  // only variant 0 below 16 images
+        launch_fwd<NB, 0>(P, v, W.f[0], W.r, W.m, W.beta, C, W.D, s);
+        count_launches(1);
+        float t[3];
+        for (int k = 0; k < 3 && e == cudaSuccess; ++k) {
+            e = cudaEventRecord(a, s);
+            launch_fwd<NB, 0>(P, v, W.f[0], W.r, W.m, W.beta, C, W.D, s);
+            count_launches(1);
+            if (e == cudaSuccess) e = cudaEventRecord(b, s);
+            if (e == cudaSuccess) e = cudaEventSynchronize(b);
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&t[k], a, b);
+        }
+        if (e != cudaSuccess) break;
+        std::sort(t, t + 3);
+        const float us = t[1] * 1e3f;
+        P->fwd_us[idx][v] = us;
+        if (us < best_us) {
+            best_us = us;
+            best = v;
+        }
+    }
+    if (a) cudaEventDestroy(a);
+    if (b) cudaEventDestroy(b);
+    if (e == cudaSuccess) e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    P->fwd_choice[idx] = best;
+    W.fwd = best;
+    return cudaSuccess;
+}
+
 template <int NB>
 void launch_tv(const Work &W, const AdmConst &C, int par, int final_pass, cudaStream_t s)
 {
@@ -939,15 +1072,12 @@ void enqueue_iteration(const dect_plan *P, const Work &W, const AdmConst &C, int
                        const IterEvents *ev)
 {
     launch_tv<NB>(W, C, par, 0, s);
-    if (C.nonneg)
-        k_fwd<NB, Kern<NB>::GF, 2><<<kFwdGrid, kFwdBlock, 0, s>>>(P->rowptr, P->ent, W.f[1 - par], W.r, W.m,
-                                                             W.beta, C, W.D);
+    if (C.nonneg) launch_fwd<NB, 2>(P, W.fwd, W.f[1 - par], W.r, W.m, W.beta, C, W.D, s);
     if (ev) cudaEventRecordWithFlags(ev->b0, s, cudaEventRecordExternal);
     launch_bwd<NB>(P, W, C, W.bwd, s);
     if (ev) cudaEventRecordWithFlags(ev->b1, s, cudaEventRecordExternal);
     if (ev) cudaEventRecordWithFlags(ev->f0, s, cudaEventRecordExternal);
-    k_fwd<NB, Kern<NB>::GF, 1><<<kFwdGrid, kFwdBlock, 0, s>>>(P->rowptr, P->ent, W.G, W.q, nullptr, nullptr,
-                                                         C, W.D);
+    launch_fwd<NB, 1>(P, W.fwd, W.G, W.q, nullptr, nullptr, C, W.D, s);
     if (ev) cudaEventRecordWithFlags(ev->f1, s, cudaEventRecordExternal);
 }
 
@@ -1038,6 +1168,8 @@ inline void fill_report(dect_adm_report &r, int NB, int j, const AdmConst &C, do
         r.objective = hred[R_TV * NB + j] + 0.5 * mu * hred[R_RR * NB + j];
     }
     r.rel_change = hrel[j];
+    r.primal_res = std::sqrt(hred[R_QQ * NB + j]);
+    r.resid_drift = std::sqrt(hred[R_GG * NB + j]);
 }
 
 // The iteration loop at batch width NB from iteration done_iters on, with W
@@ -1136,23 +1268,12 @@ dect_status iterate(const dect_plan *P, const AdmConst &C, Work W, char *base, f
                     const int par = done_iters & 1;
                     std::vector<double> hred(R_COUNT * NB), hrel(NB);
                     std::vector<int> hit(NB), hconv(NB), hslot(NB);
-                    err = cudaMemcpyAsync(hred.data(), D.red, sizeof(double) * R_COUNT * NB, cudaMemcpyDeviceToHost, cs);
-                    if (err == cudaSuccess) err = cudaMemcpyAsync(hrel.data(), D.rel, sizeof(double) * NB, cudaMemcpyDeviceToHost, cs);
-                    if (err == cudaSuccess) err = cudaMemcpyAsync(hit.data(), D.iters, sizeof(int) * NB, cudaMemcpyDeviceToHost, cs);
-                    if (err == cudaSuccess) err = cudaMemcpyAsync(hconv.data(), D.conv, sizeof(int) * NB, cudaMemcpyDeviceToHost, cs);
-                    if (err == cudaSuccess) err = cudaMemcpyAsync(hslot.data(), D.slot, sizeof(int) * NB, cudaMemcpyDeviceToHost, cs);
                     if (err == cudaSuccess) {
                         k_unpack<NB><<<(unsigned)((tn + 255) / 256), 256, 0, cs>>>(W.f[par], x, N, D.slot, D.active, 1,
                                                                                    W.beta);
                         err = cudaGetLastError();
                         count_launches(1);
                     }
-                    if (err == cudaSuccess) err = cudaStreamSynchronize(cs);
-                    if (err != cudaSuccess) break;
-                    if (rep)
-                        for (int j = 0; j < NB; ++j)
-                            if (hslot[j] >= 0 && !h_flags[1 + j])
-                                fill_report(rep[hslot[j]], NB, j, C, prm->mu, K, hred, hrel, hit, hconv);
                     std::vector<int> map(NB2, -1);
                     for (int j = 0, i = 0; j < NB; ++j)
                         if (h_flags[1 + j]) map[i++] = j;  // running channels, in order (pairs stay pairs)
@@ -1160,8 +1281,10 @@ dect_status iterate(const dect_plan *P, const AdmConst &C, Work W, char *base, f
                     err = alloc_work<NB2>(P, W2, &base2, W.m, cs);
                     if (err == cudaSuccess) {
                         W2.bwd = 1;
-                        // time the A^T variants on the empty workspace, before the state arrives
+                        W2.fwd = 0;
+                        // time the A and A^T variants on the empty workspace, before the state arrives
                         err = tune_bwd<NB2>(P, W2, C, cs);
+                        if (err == cudaSuccess) err = tune_fwd<NB2>(P, W2, C, cs);
                     }
                     if (err == cudaSuccess)
                         err = cudaMemcpyAsync(W2.map, map.data(), sizeof(int) * NB2, cudaMemcpyHostToDevice, cs);
@@ -1181,6 +1304,23 @@ dect_status iterate(const dect_plan *P, const AdmConst &C, Work W, char *base, f
                         err = cudaGetLastError();
                         count_launches(8);
                     }
+                    // the state has moved: check the stopped channels' carried
+                    // residual against A f - beta m (q and the QQ / GG slots of
+                    // this workspace are free now), then write their reports
+                    if (err == cudaSuccess) {
+                        launch_residual_check<NB>(P, W.fwd, W.f[par], W.q, W.r, W.m, W.beta, C, D, cs);
+                        err = cudaGetLastError();
+                    }
+                    if (err == cudaSuccess) err = cudaMemcpyAsync(hred.data(), D.red, sizeof(double) * R_COUNT * NB, cudaMemcpyDeviceToHost, cs);
+                    if (err == cudaSuccess) err = cudaMemcpyAsync(hrel.data(), D.rel, sizeof(double) * NB, cudaMemcpyDeviceToHost, cs);
+                    if (err == cudaSuccess) err = cudaMemcpyAsync(hit.data(), D.iters, sizeof(int) * NB, cudaMemcpyDeviceToHost, cs);
+                    if (err == cudaSuccess) err = cudaMemcpyAsync(hconv.data(), D.conv, sizeof(int) * NB, cudaMemcpyDeviceToHost, cs);
+                    if (err == cudaSuccess) err = cudaMemcpyAsync(hslot.data(), D.slot, sizeof(int) * NB, cudaMemcpyDeviceToHost, cs);
+                    if (err == cudaSuccess) err = cudaStreamSynchronize(cs);
+                    if (err == cudaSuccess && rep)
+                        for (int j = 0; j < NB; ++j)
+                            if (hslot[j] >= 0 && !h_flags[1 + j])
+                                fill_report(rep[hslot[j]], NB, j, C, prm->mu, K, hred, hrel, hit, hconv);
                     // the state now lives in the narrowed workspace
                     if (err == cudaSuccess) err = cudaEventRecord(ev, cs);
                     if (err == cudaSuccess) err = cudaStreamWaitEvent(s, ev, 0);
@@ -1222,13 +1362,12 @@ dect_status iterate(const dect_plan *P, const AdmConst &C, Work W, char *base, f
     const int par = done_iters & 1;
     if (err == cudaSuccess) {
         launch_tv<NB>(W, C, par, 1, cs);
-        if (C.nonneg)
-            k_fwd<NB, Kern<NB>::GF, 2><<<kFwdGrid, kFwdBlock, 0, cs>>>(P->rowptr, P->ent, W.f[1 - par], W.r, W.m,
-                                                                  W.beta, C, D);
+        if (C.nonneg) launch_fwd<NB, 2>(P, W.fwd, W.f[1 - par], W.r, W.m, W.beta, C, D, cs);
         k_unpack<NB><<<(unsigned)((tn + 255) / 256), 256, 0, cs>>>(W.f[1 - par], x, N, D.slot, D.active, 0,
                                                                    W.beta);
-        err = cudaGetLastError();
         count_launches(C.nonneg ? 3 : 2);
+        launch_residual_check<NB>(P, W.fwd, W.f[1 - par], W.q, W.r, W.m, W.beta, C, D, cs);
+        err = cudaGetLastError();
     }
     if (err == cudaSuccess) err = cudaEventRecord(ev, cs);
     if (err == cudaSuccess) err = cudaStreamWaitEvent(s, ev, 0);
@@ -1319,8 +1458,10 @@ dect_status run_chunk(const dect_plan *P, const float *m, float *x, int nimg,
         k_pack<NB><<<(unsigned)((tn + 255) / 256), 256, 0, s>>>(x, W.f[0], N, nimg, W.beta);
         count_launches(1);
     }
-    // r^0 = A f^0 - beta m
-    k_fwd<NB, Kern<NB>::GF, 0><<<kFwdGrid, kFwdBlock, 0, s>>>(P->rowptr, P->ent, W.f[0], W.r, m, W.beta, C, D);
+    // r^0 = A f^0 - beta m, with the A variant the autotuner keeps
+    W.fwd = 0;
+    if ((e = tune_fwd<NB>(P, W, C, s)) != cudaSuccess) return fail(e);
+    launch_fwd<NB, 0>(P, W.fwd, W.f[0], W.r, m, W.beta, C, D, s);
     count_launches(1);
     if ((e = cudaGetLastError()) != cudaSuccess) return fail(e);
     W.bwd = 1;

@@ -75,6 +75,9 @@ struct dect_plan {
     // -1 until the first ADM call with that width has timed the candidates.
     mutable int bwd_choice[6];
     mutable float bwd_us[6][DECT_BWD_VARIANTS];
+    // The same for the A variant (k_fwd).
+    mutable int fwd_choice[6];
+    mutable float fwd_us[6][DECT_FWD_VARIANTS];
 };
 
 namespace dect {

@@ -272,6 +272,7 @@ __device__ __forceinline__ Vec<Batch<NB>::VW> row_dot_g(const Entry *__restrict_
             // rounds in groups of R: R entries broadcast, then R independent
             // gathers in flight, then their multiply-adds
             constexpr int NR = G / EG, R = NR < 8 ? NR : 8;
+            static_assert(NR <= 8 || NR % 8 == 0, "rounds must split into groups of 8");
 #pragma unroll
             for (int u = 0; u < U; ++u) {
 #pragma unroll
@@ -302,6 +303,85 @@ __device__ __forceinline__ Vec<Batch<NB>::VW> row_dot_g(const Entry *__restrict_
 #pragma unroll
         for (int c = 0; c < VW; ++c) acc.v[c] += __shfl_xor_sync(0xffffffffu, acc.v[c], off);
     return acc;
+}
+
+// ---------------------------------------------------------------------------
+// Row kernel core, wide-lane form: a lane gathers VWL = 8 or 16 images of an
+// entry (VWL / 4 loads of 16 bytes) instead of 4; NB = 16, 32 or 64.  The
+// time of the table kernels goes into returning loaded data to registers:
+// every entry returns its NB x 4 bytes of image data plus its 8-byte
+// (index, length) to each lane that gathers a part of it, and LPW = NB / VWL
+// lanes share an entry here instead of NB / 4.  Load i of lane vl covers
+// images 4 (i LPW + vl) .. + 3, so the LPW lanes of an entry read 16 LPW
+// contiguous bytes per load (with VWL = 8 at 64 images: one whole 128-byte
+// line of the entry per load, as many lines per warp-wide load as the
+// 4-image form).  Entries are loaded as in row_dot_g (G at a time,
+// coalesced, one batch ahead) and broadcast by shuffles; EG = G / LPW entry
+// groups take the batch's entries in rounds, R rounds' gathers in flight.
+// Groups are summed by a fixed xor-butterfly.  The result is returned in the
+// layout of row_dot_g: lane lr holds images 4 (lr % CPB) .. + 3 (every group
+// holds the full sums, and lane lr's own wide vector covers those images at
+// block (lr % CPB) / LPW).  Every lane of the warp must call it.
+// ---------------------------------------------------------------------------
+template <int NB, int G, int VWL, int R>
+__device__ __forceinline__ Vec<4> row_dot_w(const Entry *__restrict__ ent, int64_t b, int64_t e, int lr,
+                                            const float *__restrict__ src, unsigned long long pol)
+{
+    static_assert((NB == 16 || NB == 32 || NB == 64) && (VWL == 8 || VWL == 16) && VWL <= NB,
+                  "wide row core: 16, 32 or 64 images, 8 or 16 per lane");
+    constexpr int NV = VWL / 4, LPW = NB / VWL, EG = G / LPW, NR = G / EG, CPB = NB / 4;
+    constexpr int RR = NR < R ? NR : R;
+    static_assert(G % LPW == 0 && G <= 32 && NR % RR == 0, "bad row split");
+    const int grp = lr / LPW, vl = lr % LPW;
+    const unsigned lane = threadIdx.x & 31;
+    const unsigned gbase = lane & ~(unsigned)(G - 1);
+    float acc[VWL];
+#pragma unroll
+    for (int k = 0; k < VWL; ++k) acc[k] = 0.f;
+    Entry cur = b + lr < e ? ld_entry(ent + b + lr) : make_int2(0, 0);
+    const unsigned maxlen = __reduce_max_sync(0xffffffffu, (unsigned)(e - b));
+    for (int64_t base = b; base < b + (int64_t)maxlen; base += G) {
+        const int64_t kn = base + G + lr;
+        const Entry nxt = kn < e ? ld_entry(ent + kn) : make_int2(0, 0);
+#pragma unroll
+        for (int j0 = 0; j0 < NR; j0 += RR) {
+            int pix[RR];
+            float w[RR];
+#pragma unroll
+            for (int j = 0; j < RR; ++j) {
+                const unsigned srcl = gbase + (j0 + j) * EG + grp;
+                pix[j] = __shfl_sync(0xffffffffu, cur.x, srcl);
+                w[j] = __int_as_float(__shfl_sync(0xffffffffu, cur.y, srcl));
+            }
+            Vec<4> xv[RR][NV];
+#pragma unroll
+            for (int j = 0; j < RR; ++j)
+#pragma unroll
+                for (int i = 0; i < NV; ++i)
+                    xv[j][i] = ld_gather<4>(src + (int64_t)pix[j] * NB + 4 * (i * LPW + vl), pol);
+#pragma unroll
+            for (int j = 0; j < RR; ++j)
+#pragma unroll
+                for (int i = 0; i < NV; ++i)
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) acc[4 * i + c] = fmaf(w[j], xv[j][i].v[c], acc[4 * i + c]);
+        }
+        cur = nxt;
+    }
+#pragma unroll
+    for (int off = LPW; off < G; off <<= 1)
+#pragma unroll
+        for (int k = 0; k < VWL; ++k) acc[k] += __shfl_xor_sync(0xffffffffu, acc[k], off);
+    const int q = (lr % CPB) / LPW;
+    Vec<4> out;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+        float v = acc[c];
+#pragma unroll
+        for (int i = 1; i < NV; ++i) v = q == i ? acc[4 * i + c] : v;
+        out.v[c] = v;
+    }
+    return out;
 }
 
 // Gathers of one VW-wide vector of the NB images at index `pix`.

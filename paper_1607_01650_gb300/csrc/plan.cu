@@ -470,7 +470,7 @@ extern "C" dect_status dect_plan_create(const dect_geometry *geom, int device, d
     p->nb = geom->n_bins;
     p->N = (int64_t)p->n * p->n;
     p->M = (int64_t)p->nv * p->nb;
-    for (int k = 0; k < 6; ++k) p->bwd_choice[k] = -1;
+    for (int k = 0; k < 6; ++k) p->bwd_choice[k] = p->fwd_choice[k] = -1;
 
     // ray end points on the host, FP64 (see file header)
     std::vector<RayPts> h(p->M);
@@ -689,20 +689,29 @@ extern "C" dect_status dect_plan_copy_table(const dect_plan *p, int64_t *rowptr,
     return DECT_OK;
 }
 
+namespace {
+
+int width_index(int images)
+{
+    switch (images) {
+    case 2: return 0;
+    case 4: return 1;
+    case 8: return 2;
+    case 16: return 3;
+    case 32: return 4;
+    case 64: return 5;
+    default: return -1;
+    }
+}
+
+}  // namespace
+
 extern "C" dect_status dect_plan_get_tuning(const dect_plan *p, int images, int *choice,
                                             float us[DECT_BWD_VARIANTS])
 {
     if (!p || !choice || !us) return DECT_ERR_INVALID_ARG;
-    int idx;
-    switch (images) {
-    case 2: idx = 0; break;
-    case 4: idx = 1; break;
-    case 8: idx = 2; break;
-    case 16: idx = 3; break;
-    case 32: idx = 4; break;
-    case 64: idx = 5; break;
-    default: return DECT_ERR_INVALID_ARG;
-    }
+    const int idx = width_index(images);
+    if (idx < 0) return DECT_ERR_INVALID_ARG;
     *choice = p->bwd_choice[idx];
     for (int v = 0; v < DECT_BWD_VARIANTS; ++v) us[v] = p->bwd_choice[idx] >= 0 ? p->bwd_us[idx][v] : -1.f;
     return DECT_OK;
@@ -711,17 +720,30 @@ extern "C" dect_status dect_plan_get_tuning(const dect_plan *p, int images, int 
 extern "C" dect_status dect_plan_set_tuning(dect_plan *p, int images, int choice)
 {
     if (!p || choice < -1 || choice >= DECT_BWD_VARIANTS) return DECT_ERR_INVALID_ARG;
-    int idx;
-    switch (images) {
-    case 2: idx = 0; break;
-    case 4: idx = 1; break;
-    case 8: idx = 2; break;
-    case 16: idx = 3; break;
-    case 32: idx = 4; break;
-    case 64: idx = 5; break;
-    default: return DECT_ERR_INVALID_ARG;
-    }
+    const int idx = width_index(images);
+    if (idx < 0) return DECT_ERR_INVALID_ARG;
     p->bwd_choice[idx] = choice;
     for (int v = 0; v < DECT_BWD_VARIANTS; ++v) p->bwd_us[idx][v] = -1.f;
+    return DECT_OK;
+}
+
+extern "C" dect_status dect_plan_get_fwd_tuning(const dect_plan *p, int images, int *choice,
+                                                float us[DECT_FWD_VARIANTS])
+{
+    if (!p || !choice || !us) return DECT_ERR_INVALID_ARG;
+    const int idx = width_index(images);
+    if (idx < 0) return DECT_ERR_INVALID_ARG;
+    *choice = p->fwd_choice[idx];
+    for (int v = 0; v < DECT_FWD_VARIANTS; ++v) us[v] = p->fwd_choice[idx] >= 0 ? p->fwd_us[idx][v] : -1.f;
+    return DECT_OK;
+}
+
+extern "C" dect_status dect_plan_set_fwd_tuning(dect_plan *p, int images, int choice)
+{
+    if (!p || choice < -1 || choice >= DECT_FWD_VARIANTS) return DECT_ERR_INVALID_ARG;
+    const int idx = width_index(images);
+    if (idx < 0) return DECT_ERR_INVALID_ARG;
+    p->fwd_choice[idx] = choice;
+    for (int v = 0; v < DECT_FWD_VARIANTS; ++v) p->fwd_us[idx][v] = -1.f;
     return DECT_OK;
 }

@@ -110,3 +110,5 @@ def test_variant_count_matches_the_header():
     import paper_1607_01650_gb300 as dect
     m = re.search(r"#define\s+DECT_BWD_VARIANTS\s+(\d+)", open(HEADER).read())
     assert m and int(m.group(1)) == dect.BWD_VARIANTS
+    m = re.search(r"#define\s+DECT_FWD_VARIANTS\s+(\d+)", open(HEADER).read())
+    assert m and int(m.group(1)) == dect.FWD_VARIANTS

@@ -339,3 +339,31 @@ def test_uneven_geometry_groups():
             for e in range(2):
                 assert rel_l2(x[i, e], xo[e]) <= 1e-4
         assert all(r.iters == 15 for r in reps)
+
+
+@pytest.mark.parametrize("ns", [1, 3, 16, 32])
+def test_every_projector_variant(ns):
+    """Each A variant the autotuner can pick gives the oracle's result, and
+    each one's set-up projection r = A f - beta m (checked through a
+    one-iteration run from a warm start, whose first step depends on it)."""
+    g = synth.tiny_geometry(n=52, nv=24, nb=80, px=1.0, sod=130.0, sdd=260.0)
+    slices = [synth.make_slice(g, seed=400 + i, i0=1e5) for i in range(ns)]
+    plan = dect.Plan(g)
+    t = oracle.table(g)
+    m = np.stack([s.m for s in slices])
+    width = min(64, 1 << (2 * ns - 1).bit_length())
+    prm = dect.AdmParams(mu=MU, rho=RHO, max_iter=12)
+    for v in range(dect.FWD_VARIANTS):
+        plan.set_fwd_tuning(width, v)
+        x, reps = dect.adm_tv(plan, torch.tensor(m, dtype=torch.float32, device="cuda"), prm)
+        x = x.cpu().numpy()
+        for i in range(ns):
+            op = oracle.AdmParams(mu=MU, rho=RHO, max_iter=12, step_rule=oracle.CAUCHY)
+            xo, _ = oracle.adm_dual(t, m[i].astype(np.float32).astype(np.float64), op)
+            for e in range(2):
+                assert rel_l2(x[i, e], xo[e]) <= 1e-4, (v, i, e)
+                assert reps[2 * i + e].resid_drift <= 1e-5 * reps[2 * i + e].primal_res, (v, i, e)
+    plan.set_fwd_tuning(width, -1)
+    dect.adm_tv(plan, torch.tensor(m, dtype=torch.float32, device="cuda"), prm)
+    choice, us = plan.fwd_tuning(width)
+    assert 0 <= choice < dect.FWD_VARIANTS and us[choice] > 0
