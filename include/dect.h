@@ -111,8 +111,13 @@ dect_status dect_plan_copy_table(const dect_plan *plan, int64_t *rowptr, int32_t
 
 /*
  * y = A x, Eq. (1), for `batch` images: x [batch][n][n] -> y [batch][n_views][n_bins].
- * FP32 multiply-add in the table's order; deterministic.
- * Errors: DECT_ERR_INVALID_ARG (NULL plan/pointer, batch < 0).  batch = 0 is a no-op.
+ * The batch runs in passes of up to 64 images: each pass copies its images
+ * into a pixel-major interleaved scratch ([pixel][64]), streams the ray-major
+ * table once, and copies the sums out.  FP32 multiply-add in a fixed order;
+ * deterministic.  The scratch (about 4 (N + M) min(batch, 64) bytes) is
+ * taken from the stream-ordered allocator and returned before the call ends.
+ * Errors: DECT_ERR_INVALID_ARG (NULL plan/pointer, batch < 0), DECT_ERR_OOM,
+ * DECT_ERR_CUDA.  batch = 0 is a no-op.
  */
 dect_status dect_project(const dect_plan *plan, const float *x, float *y, int batch,
                          dect_stream stream);
@@ -120,8 +125,10 @@ dect_status dect_project(const dect_plan *plan, const float *x, float *y, int ba
 /*
  * x = A^T y, the exact transpose used by the gradient G_f of Eq. (9), for
  * `batch` sinograms: y [batch][n_views][n_bins] -> x [batch][n][n].
- * Gather form over the pixel-major table: every pixel sums its rays in
- * increasing ray order; no atomics, bitwise reproducible.
+ * Gather form over the pixel-major table (rays increasing inside a pixel),
+ * in passes of up to 64 sinograms interleaved as for dect_project, pixels
+ * taken in 8 x 8 tiles; every pixel sums its rays in a fixed order; no
+ * atomics, bitwise reproducible.  Scratch and errors as dect_project.
  */
 dect_status dect_backproject(const dect_plan *plan, const float *y, float *x, int batch,
                              dect_stream stream);

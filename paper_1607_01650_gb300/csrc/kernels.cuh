@@ -394,72 +394,12 @@ struct GatherIL {  // interleaved [index][NB] in global memory
         return ld_gather<Batch<NB>::VW>(src + (int64_t)pix * NB + vl * Batch<NB>::VW, pol);
     }
 };
-template <int NB>
-struct GatherPlanar {  // planar [img][stride] in global memory, nimg valid images
-    const float *src;
-    int64_t stride;
-    int nimg;
-    __device__ __forceinline__ Vec<Batch<NB>::VW> operator()(int pix, int vl) const
-    {
-        constexpr int VW = Batch<NB>::VW;
-        Vec<VW> xv;
-#pragma unroll
-        for (int c = 0; c < VW; ++c) {
-            const int img = vl * VW + c;
-            xv.v[c] = img < nimg ? __ldg(src + (int64_t)img * stride + pix) : 0.f;
-        }
-        return xv;
-    }
-};
-template <int NB>
-struct GatherShared {  // interleaved [index][NB] in shared memory
-    const float *win;
-    __device__ __forceinline__ Vec<Batch<NB>::VW> operator()(int idx, int vl) const
-    {
-        return ld_v<Batch<NB>::VW>(win + idx * NB + vl * Batch<NB>::VW);
-    }
-};
-
 template <int NB, int G, bool IL, bool SBC = false>
-__device__ __forceinline__ Vec<Batch<NB>::VW> row_dot(const Entry *__restrict__ ent, int64_t b,
-                                                      int64_t e, const float *__restrict__ src,
-                                                      int64_t src_stride, int lr, int nimg = NB)
+__device__ __forceinline__ Vec<Batch<NB>::VW> row_dot(const Entry *__restrict__ ent, int64_t b, int64_t e,
+                                                      const float *__restrict__ src, int64_t /*unused*/, int lr)
 {
-    if constexpr (IL)
-        return row_dot_g<NB, G, GatherIL<NB>, SBC>(ent, b, e, lr, GatherIL<NB>{src});
-    else
-        return row_dot_g<NB, G>(ent, b, e, lr, GatherPlanar<NB>{src, src_stride, nimg});
-}
-
-// Plain operator kernel: dst[row] = sum over the row's entries of len * src[index].
-// Planar layout: image i of a batch chunk at src + i * src_stride; only the
-// first nimg <= NB images are read or written.
-template <int NB, int G>
-__global__ void __launch_bounds__(256) k_rows_planar(const int64_t *__restrict__ ptr,
-                                                     const Entry *__restrict__ ent, int64_t rows,
-                                                     const float *__restrict__ src, int64_t src_stride,
-                                                     float *__restrict__ dst, int64_t dst_stride,
-                                                     int nimg)
-{
-    constexpr int VW = Batch<NB>::VW, LPE = Batch<NB>::CPB;
-    const int lr = threadIdx.x % G, grp = lr / LPE, vl = lr % LPE;
-    const int64_t rpb = blockDim.x / G;
-    for (int64_t row0 = (int64_t)blockIdx.x * rpb; row0 < rows; row0 += (int64_t)gridDim.x * rpb) {
-        int64_t row = row0 + threadIdx.x / G;
-        int64_t b = 0, e = 0;
-        if (row < rows) {
-            b = ptr[row];
-            e = ptr[row + 1];
-        }
-        Vec<VW> acc = row_dot<NB, G, false>(ent, b, e, src, src_stride, lr, nimg);
-        if (row < rows && grp == 0) {
-#pragma unroll
-            for (int c = 0; c < VW; ++c) {
-                int img = vl * VW + c;
-                if (img < nimg) dst[(int64_t)img * dst_stride + row] = acc.v[c];
-            }
-        }
-    }
+    static_assert(IL, "only the interleaved layout is gathered");
+    return row_dot_g<NB, G, GatherIL<NB>, SBC>(ent, b, e, lr, GatherIL<NB>{src});
 }
 
 }  // namespace dect

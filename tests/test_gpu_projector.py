@@ -52,7 +52,7 @@ def test_table_matches_oracle(plans, name):
 
 
 @pytest.mark.parametrize("name", list(GEOMS))
-@pytest.mark.parametrize("batch", [1, 2, 3, 6])
+@pytest.mark.parametrize("batch", [1, 2, 3, 6, 17, 64, 70])
 def test_project_parity(plans, name, batch):
     plan, t = plans[name]
     g = GEOMS[name]
@@ -65,7 +65,7 @@ def test_project_parity(plans, name, batch):
 
 
 @pytest.mark.parametrize("name", list(GEOMS))
-@pytest.mark.parametrize("batch", [1, 2, 5])
+@pytest.mark.parametrize("batch", [1, 2, 5, 33, 64, 67])
 def test_backproject_parity(plans, name, batch):
     plan, t = plans[name]
     g = GEOMS[name]
@@ -139,3 +139,26 @@ def test_paper_size_mirror_symmetry():
     v = torch.arange(g.nv, device="cuda")
     ym = torch.flip(y[(g.nv - v) % g.nv], dims=[1])
     assert float((yf - ym).norm() / ym.norm()) <= 1e-5
+
+
+def test_paper_size_64_images():
+    """The operators at 512^2 / 60 views / 736 bins on 64 images (one
+    interleaved pass over each table): sampled rays of three images against
+    the oracle's Siddon walks, and the whole A^T y of those images against the
+    oracle's transpose."""
+    g = synth.paper_geometry()
+    plan = dect.Plan(g)
+    rng = np.random.default_rng(11)
+    x = (0.02 * rng.random((64, g.n, g.n))).astype(np.float32)
+    y = dect.project(plan, torch.tensor(x, device="cuda")).cpu().numpy()
+    for b in (0, 31, 63):
+        for r in rng.choice(g.nv * g.nb, 60, replace=False):
+            v, bn = divmod(int(r), g.nb)
+            idx, lens = oracle.siddon_ray(g, v, bn)
+            want = float(np.dot(lens, x[b].reshape(-1)[idx].astype(np.float64)))
+            assert abs(y[b, v, bn] - want) <= 1e-5 * max(abs(want), 1e-3), (b, v, bn)
+    s = rng.random((64, g.nv, g.nb)).astype(np.float32)
+    bp = dect.backproject(plan, torch.tensor(s, device="cuda")).cpu().numpy()
+    t = oracle.table(g)
+    for b in (0, 40, 63):
+        assert rel_l2(bp[b], oracle.backproject(t, s[b].astype(np.float64))) <= 1e-5, b
