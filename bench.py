@@ -64,6 +64,9 @@ def parse():
                     help="fix the A^T variant (0-7, see dect_plan_get_tuning) instead of autotuning")
     ap.add_argument("--fwd-variant", type=int, default=-1,
                     help="fix the A variant (0-3, see dect_plan_get_fwd_tuning) instead of autotuning")
+    ap.add_argument("--batched-otf", action="store_true",
+                    help="batched workload through dect_adm_tv_batch (one launch per ADM phase over all slices, "
+                         "on-the-fly projector) instead of dect_adm_tv_groups")
     ap.add_argument("--train-slices", type=int, default=1024, help="learned workload: training slices")
     ap.add_argument("--epochs", type=int, default=6, help="learned workload: training epochs")
     ap.add_argument("--workload", default="paper", choices=["paper", "batched", "learned", "stress", "fbp"],
@@ -526,7 +529,9 @@ def run_fbp(args, rank, world, local):
 def run_batched(args, rank, world, local):
     """Uneven-slice workload: 64 slices, n in {256..512} at 0.5 mm, 30-180 views,
     bins 368 + round((n - 256) / 256 * 368) x 0.6 mm; one dect_adm_tv_groups
-    call per step (one plan per distinct geometry), then PLS per slice."""
+    call per step (one stored-table ADM per geometry on its own stream;
+    --batched-otf: dect_adm_tv_batch, every slice advanced by the same
+    launches with the on-the-fly projector), then PLS per geometry."""
     import torch
     import paper_1607_01650_gb300 as dect
     torch.cuda.set_device(local)
@@ -551,13 +556,25 @@ def run_batched(args, rank, world, local):
                          rel_obj_tol=TOL, check_every=10)
     pp = dect.PlsParams(**PLS)
     us = [torch.empty_like(x) for _, _, x in groups]
-    iters = []
+    iters, isect = [], []
+
+    adm_ms = []
 
     def step():
-        res = dect.adm_tv_groups(groups, prm)
+        a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a0.record()
+        res = (dect.adm_tv_batch(groups, prm) if args.batched_otf else dect.adm_tv_groups(groups, prm))
+        a1.record()
         iters[:] = [r.iters for _, reps in res for r in reps]
         for (x, _), u in zip(res, us):
             dect.pls_decompose(x, pp, u=u)
+        torch.cuda.synchronize()
+        adm_ms.append(a0.elapsed_time(a1))
+        # intersections visited by the two operators: per slice, nnz x its iterations (the
+        # later of its two channels' stops, up to which the slice stays in the launches)
+        k_sl = [max(r.iters for r in reps[2 * i: 2 * i + 2]) for _, reps in res for i in range(len(reps) // 2)]
+        nnz_sl = [p.nnz for p, m, _ in groups for _ in range(m.shape[0])]
+        isect.append(2.0 * sum(a * b for a, b in zip(nnz_sl, k_sl)))
 
     for _ in range(args.warmup):
         step()
@@ -580,7 +597,12 @@ def run_batched(args, rank, world, local):
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
                 "data": "synthetic",
                 "config": {"workload": "uneven batch: 64 slices, n in {256..512} at 0.5 mm, 30-180 views",
+                           "path": "dect_adm_tv_batch (one launch per ADM phase over all slices, on-the-fly projector)"
+                           if args.batched_otf else "dect_adm_tv_groups (stored tables, a stream per geometry)",
                            "geometries": len(groups), "mean_adm_iterations": float(np.mean(iters)),
+                           "adm_ms_per_step": float(np.mean(adm_ms[-args.steps:])),
+                           "operator_intersections_per_s": float(np.mean(isect[-args.steps:]) /
+                                                                 (np.mean(adm_ms[-args.steps:]) / 1e3)),
                            "l2": "inputs larger than L2"},
                 "gpu_launches": int(dect.kernel_launches() - launches0), "clocks": clk.summary()}
         print(json.dumps(line), flush=True)

@@ -241,6 +241,43 @@ typedef struct {
 dect_status dect_adm_tv_groups(const dect_adm_group *groups, int n_groups,
                                const dect_adm_params *params, int workers, dect_stream stream);
 
+/*
+ * ADM-TV, Eq. (3)-(10), of slices of uneven size and view count, each
+ * group's slices sharing its plan (plans may repeat), all slices of all
+ * groups advanced together: one launch per ADM phase covers every running
+ * slice (per-slice steps, stopping tests and reports as dect_adm_tv; each
+ * slice's two energies interleaved), and slices whose channels have all
+ * stopped leave the launches at the next host check (every check_every
+ * iterations).  The projector is computed on the fly (no stored table):
+ * a_ij is the length of ray i inside pixel j, the overlap of the ray's two
+ * slabs of that pixel, from FP32 crossing parameters measured from the
+ * ray's point nearest the rotation axis; A x walks each ray through its
+ * pixels, A^T y takes each pixel and, per view, the bins whose rays can
+ * cross it, and both evaluate a_ij by the same function, so A^T is the
+ * exact transpose of A (results agree with the stored-table path to FP32
+ * rounding of the lengths).  Plans with rays along a grid line
+ * (dect_plan_info.n_grid_aligned > 0) are rejected (the two paths assign
+ * such rays differently): use dect_adm_tv for them.
+ * Each group: m [n_slices][2][n_views][n_bins], x [n_slices][2][n][n]
+ * (device, as for dect_adm_tv), reports HOST [n_slices * 2] or NULL.
+ * Device scratch from the stream-ordered allocator; synchronises `stream`.
+ * Errors: DECT_ERR_INVALID_ARG, DECT_ERR_OOM, DECT_ERR_CUDA,
+ * DECT_ERR_NONFINITE.
+ */
+dect_status dect_adm_tv_batch(const dect_adm_group *groups, int n_groups, const dect_adm_params *params,
+                              dect_stream stream);
+
+/*
+ * A x and A^T y as dect_project / dect_backproject, with the on-the-fly
+ * projector of dect_adm_tv_batch (no table is read; the plan's ray and view
+ * parameters, 32 bytes per ray, are built on the first call and kept with
+ * the plan).  Images are processed two at a time.  Scratch from the
+ * stream-ordered allocator.  Errors as dect_project.
+ */
+dect_status dect_project_otf(const dect_plan *plan, const float *x, float *y, int batch, dect_stream stream);
+dect_status dect_backproject_otf(const dect_plan *plan, const float *y, float *x, int batch,
+                                 dect_stream stream);
+
 typedef struct {
     double eta[2][2];   /* eta[material][energy]: attenuation (1/mm) of basis material
                            1 / 2 at energy 0 (high) / 1 (low); D of Eq. (12)            */

@@ -18,7 +18,8 @@ from typing import List, Optional, Sequence, Tuple
 from . import _build
 
 __all__ = ["Geometry", "Plan", "AdmParams", "PlsParams", "AdmReport", "AdmProfile", "DectError",
-           "load", "project", "backproject", "adm_tv", "pls_decompose", "pls_edge_mask", "kernel_launches",
+           "load", "project", "backproject", "project_otf", "backproject_otf", "adm_tv", "adm_tv_batch",
+           "pls_decompose", "pls_edge_mask", "kernel_launches",
            "library_path"]
 
 
@@ -88,6 +89,9 @@ _SIGS = {
     "dect_adm_tv_groups": (C.c_int, [C.POINTER(_AdmGroup), C.c_int, C.POINTER(_AdmParams), C.c_int, _P]),
     "dect_pls_decompose_noalloc": (C.c_int, [_P, C.c_int, C.c_int, C.POINTER(_PlsParams), _P, _P, _P]),
     "dect_pls_edge_mask": (C.c_int, [_P, C.c_int, C.c_int, C.c_double, _P, _P]),
+    "dect_adm_tv_batch": (C.c_int, [C.POINTER(_AdmGroup), C.c_int, C.POINTER(_AdmParams), _P]),
+    "dect_project_otf": (C.c_int, [_P, _P, _P, C.c_int, _P]),
+    "dect_backproject_otf": (C.c_int, [_P, _P, _P, C.c_int, _P]),
     "dect_kernel_launches": (C.c_int64, []),
     "dect_cnn_num_params": (C.c_int64, []),
     "dect_cnn_create": (C.c_int, [C.c_int, C.c_int, C.POINTER(_P)]),
@@ -266,6 +270,35 @@ def project(plan: Plan, x, y=None, stream=None):
     return y
 
 
+def project_otf(plan: Plan, x, y=None, stream=None):
+    """y = A x with the on-the-fly projector (no table read; see dect_project_otf)."""
+    import torch
+    g = plan.geom
+    if x.shape[-2:] != (g.n, g.n):
+        raise DectError("x must end in (n, n)")
+    batch = x.numel() // (g.n * g.n)
+    if y is None:
+        y = torch.empty(x.shape[:-2] + (g.nv, g.nb), device=x.device, dtype=torch.float32)
+    _check(load().dect_project_otf(plan.handle, _ptr(x, torch.float32, plan.device),
+                                   _ptr(y, torch.float32, plan.device), batch, _stream(stream)), "dect_project_otf")
+    return y
+
+
+def backproject_otf(plan: Plan, y, x=None, stream=None):
+    """x = A^T y with the on-the-fly projector (see dect_backproject_otf)."""
+    import torch
+    g = plan.geom
+    if y.shape[-2:] != (g.nv, g.nb):
+        raise DectError("y must end in (nv, nb)")
+    batch = y.numel() // (g.nv * g.nb)
+    if x is None:
+        x = torch.empty(y.shape[:-2] + (g.n, g.n), device=y.device, dtype=torch.float32)
+    _check(load().dect_backproject_otf(plan.handle, _ptr(y, torch.float32, plan.device),
+                                       _ptr(x, torch.float32, plan.device), batch, _stream(stream)),
+           "dect_backproject_otf")
+    return x
+
+
 def backproject(plan: Plan, y, x=None, stream=None):
     """x = A^T y for y [..., nv, nb] float32 CUDA -> x [..., n, n] (transpose in G_f, Eq. (9))."""
     import torch
@@ -404,6 +437,32 @@ def adm_tv_groups(groups, params: AdmParams, workers: int = 0, stream=None):
         out.append((x, rep, S))
     _check(load().dect_adm_tv_groups(cg, len(groups), C.byref(params._c()), workers, _stream(stream)),
            "dect_adm_tv_groups")
+    return [(x, [_report(r) for r in rep[:2 * S]]) for x, rep, S in out]
+
+
+def adm_tv_batch(groups, params: AdmParams, stream=None):
+    """ADM-TV (Eq. (3)-(10)) of slices of uneven geometry, all advanced together
+    with one launch per ADM phase and the on-the-fly projector
+    (dect_adm_tv_batch).  groups: list of (plan, m [S, 2, nv, nb], x [S, 2, n, n]
+    or None); plans may repeat.  Returns [(x, reports)] in the order given."""
+    import torch
+    cg = (_AdmGroup * max(len(groups), 1))()
+    keep, out = [], []
+    for i, (plan, m, x) in enumerate(groups):
+        g = plan.geom
+        if m.dim() != 4 or m.shape[1:] != (2, g.nv, g.nb):
+            raise DectError("group %d: m must be [S, 2, nv, nb]" % i)
+        S = m.shape[0]
+        if x is None:
+            x = torch.zeros((S, 2, g.n, g.n), device=m.device, dtype=torch.float32)
+        elif x.shape != (S, 2, g.n, g.n):
+            raise DectError("group %d: x must be [S, 2, n, n]" % i)
+        rep = (_AdmReport * max(2 * S, 1))()
+        keep.append(rep)
+        cg[i] = _AdmGroup(plan.handle.value, _ptr(m, torch.float32, plan.device).value,
+                          _ptr(x, torch.float32, plan.device).value, S, C.cast(rep, C.c_void_p).value)
+        out.append((x, rep, S))
+    _check(load().dect_adm_tv_batch(cg, len(groups), C.byref(params._c()), _stream(stream)), "dect_adm_tv_batch")
     return [(x, [_report(r) for r in rep[:2 * S]]) for x, rep, S in out]
 
 

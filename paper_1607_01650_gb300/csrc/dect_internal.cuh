@@ -78,6 +78,14 @@ struct dect_plan {
     // The same for the A variant (k_fwd).
     mutable int fwd_choice[6];
     mutable float fwd_us[6][DECT_FWD_VARIANTS];
+    // On-the-fly projector geometry (built on first use, see batch.cu): per
+    // ray the point closest to the rotation axis and the unit direction
+    // (otf_ray), the reciprocals of the direction (otf_inv); per view the
+    // source and the detector frame (otf_view, otf_view2).  FP64 computed,
+    // FP32 stored.
+    mutable float4 *otf_ray;
+    mutable float2 *otf_inv;
+    mutable float4 *otf_view, *otf_view2;
 };
 
 namespace dect {
@@ -87,5 +95,9 @@ cudaError_t launch_project_planar(const dect_plan *p, const float *x, float *y, 
                                   cudaStream_t s);
 cudaError_t launch_backproject_planar(const dect_plan *p, const float *y, float *x, int batch,
                                       cudaStream_t s);
+
+// On-the-fly projector geometry of a plan (batch.cu): built and cached on the
+// first call; synchronises `s` then.
+cudaError_t otf_setup(const dect_plan *p, cudaStream_t s);
 
 }  // namespace dect

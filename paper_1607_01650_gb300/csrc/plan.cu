@@ -639,6 +639,10 @@ extern "C" dect_status dect_plan_destroy(dect_plan *p)
     cudaFree(p->ent);
     cudaFree(p->colptr);
     cudaFree(p->tent);
+    cudaFree(p->otf_ray);
+    cudaFree(p->otf_inv);
+    cudaFree(p->otf_view);
+    cudaFree(p->otf_view2);
     cudaFree(p->wray0);
     cudaFree(p->wcnt);
     cudaFree(p->woff);
