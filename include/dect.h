@@ -48,7 +48,8 @@ typedef enum {
     DECT_ERR_OOM = 3,
     DECT_ERR_TIMEOUT = 4,
     DECT_ERR_NONFINITE = 5,
-    DECT_ERR_NOT_CONVERGED = 6
+    DECT_ERR_NOT_CONVERGED = 6,
+    DECT_ERR_INDEX = 7          /* an index check of the checked build failed */
 } dect_status;
 
 /* Opaque CUDA stream (binary-compatible with cudaStream_t). */
@@ -482,6 +483,30 @@ dect_status dect_cnn_loss_grad(dect_cnn *net, const float *x, const float *targe
 /* One Adam step on the last gradient. */
 dect_status dect_cnn_adam_step(dect_cnn *net, float lr, float beta1, float beta2, float eps,
                                dect_stream stream);
+
+/*
+ * Checked build.  libdect_checked.so is the same library compiled with
+ * index checks (DECT_CHECKED): before each table-driven gather, stencil
+ * neighbour, on-the-fly ray or pixel and FBP bin access, the index is
+ * checked against its array; an index outside it is not used (a safe index
+ * is substituted) and the first such failure is recorded on the device.
+ * dect_check_status() synchronises the device, then returns DECT_OK, or
+ * DECT_ERR_INDEX with the site and index in dect_last_error(), clearing
+ * the record.  In the plain library no check is compiled and
+ * dect_check_status() returns DECT_OK.  dect_checked_build() returns 1 in
+ * the checked library, 0 otherwise.
+ */
+int dect_checked_build(void);
+dect_status dect_check_status(void);
+
+/*
+ * Self-test of the index checks: a kernel reads element `index` of an
+ * 8-element device array through a check.  In the checked library an index
+ * outside 0..7 is caught (not read) and the call returns DECT_ERR_INDEX; in
+ * the plain library such an index is refused on the host
+ * (DECT_ERR_INVALID_ARG).  Synchronises `stream`.
+ */
+dect_status dect_selftest_index(int index, dect_stream stream);
 
 /* Text of a status code (static storage). */
 const char *dect_status_string(dect_status s);

@@ -103,6 +103,9 @@ _SIGS = {
                                      C.POINTER(C.c_float), _P, _P]),
     "dect_cnn_adam_step": (C.c_int, [_P, C.c_float, C.c_float, C.c_float, C.c_float, _P]),
     "dect_selftest_bounded_wait": (C.c_int, [C.c_uint, _P]),
+    "dect_selftest_index": (C.c_int, [C.c_int, _P]),
+    "dect_check_status": (C.c_int, []),
+    "dect_checked_build": (C.c_int, []),
     "dect_plan_get_tuning": (C.c_int, [_P, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_float)]),
     "dect_plan_set_tuning": (C.c_int, [_P, C.c_int, C.c_int]),
     "dect_plan_get_fwd_tuning": (C.c_int, [_P, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_float)]),
@@ -114,18 +117,21 @@ _SIGS = {
 
 
 def library_path() -> str:
-    return _build.LIB
+    """libdect.so, or libdect_checked.so (the index-checked build) when the
+    environment variable DECT_CHECKED is 1 at import time."""
+    return _build.LIB_CHECKED if os.environ.get("DECT_CHECKED") == "1" else _build.LIB
 
 
 def load(build_if_missing: bool = True):
     """Load libdect.so (compiling it first when it is missing or stale)."""
     global _lib
     if _lib is None:
+        path = library_path()
         if build_if_missing and not _build.up_to_date():
             _build.build()
-        if not os.path.exists(_build.LIB):
-            raise DectError("libdect.so is not built (run __graft_entry__.build())")
-        lib = C.CDLL(_build.LIB)
+        if not os.path.exists(path):
+            raise DectError("%s is not built (run __graft_entry__.build())" % os.path.basename(path))
+        lib = C.CDLL(path)
         for name, (res, args) in _SIGS.items():
             fn = getattr(lib, name)
             fn.restype = res
@@ -464,6 +470,12 @@ def adm_tv_batch(groups, params: AdmParams, stream=None):
         out.append((x, rep, S))
     _check(load().dect_adm_tv_batch(cg, len(groups), C.byref(params._c()), _stream(stream)), "dect_adm_tv_batch")
     return [(x, [_report(r) for r in rep[:2 * S]]) for x, rep, S in out]
+
+
+def check_status():
+    """Raise DectError if an index check of the checked build has failed
+    since the last call (dect_check_status); no-op in the plain build."""
+    _check(load().dect_check_status(), "dect_check_status")
 
 
 def kernel_launches() -> int:

@@ -401,9 +401,9 @@ __global__ void __launch_bounds__(BLK) k_bwd(const int64_t *__restrict__ colptr,
             }
             Vec<VW> acc;
             if constexpr (VWL > 4 && NB >= 16)
-                acc = row_dot_w<NB, G_, VWL, R>(tent, b, e, lr, r, pol);
+                acc = row_dot_w<NB, G_, VWL, R>(tent, b, e, lr, r, pol, C.M, CHK_GATHER_AT);
             else
-                acc = row_dot<NB, G_, true, true>(tent, b, e, r, 0, lr);
+                acc = row_dot<NB, G_, true, true>(tent, b, e, r, C.M, lr, CHK_GATHER_AT);
             if (ok && grp == 0) {
                 const int64_t o = pix * NB + vl * VW;
                 Vec<VW> p0 = ld_v<VW>(p + o), p1 = ld_v<VW>(p + sN + o), pd, pr;
@@ -696,9 +696,9 @@ __global__ void __launch_bounds__(BLK) k_fwd(const int64_t *__restrict__ rowptr,
         }
         Vec<VW> acc;
         if constexpr (VWL > 4 && NB >= 16)
-            acc = row_dot_w<NB, G_, VWL, R>(ent, b, e, lr, src, pol);
+            acc = row_dot_w<NB, G_, VWL, R>(ent, b, e, lr, src, pol, C.N, CHK_GATHER_A);
         else
-            acc = row_dot<NB, G_, true>(ent, b, e, src, 0, lr);
+            acc = row_dot<NB, G_, true>(ent, b, e, src, C.N, lr, CHK_GATHER_A);
         if (ray < C.M && grp == 0) {
             if (MODE != 1) {
 #pragma unroll

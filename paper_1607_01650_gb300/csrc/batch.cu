@@ -122,7 +122,10 @@ __device__ float2 ray_sum(const OtfGrid &g, const float4 &R, const float2 &I, co
         }
         float2 v[W];
 #pragma unroll
-        for (int w = 0; w < W; ++w) v[w] = __ldg(img + idx[w]);
+        for (int w = 0; w < W; ++w) {
+            if (!DECT_IDX_OK(idx[w], (int64_t)n * n, CHK_OTF_WALK)) idx[w] = 0;
+            v[w] = __ldg(img + idx[w]);
+        }
 #pragma unroll
         for (int w = 0; w < W; ++w) {
             acc.x = fmaf(len[w], v[w].x, acc.x);
@@ -164,9 +167,11 @@ __device__ float2 pixel_sum(const OtfGeom &G, int i, int j, const float2 *__rest
         // candidates two at a time, the second one's loads from a valid ray
         // (b0) and its length zeroed when it is past b1
         for (int b = b0; b <= b1; b += 2) {
-            const int64_t r0 = (int64_t)v * G.nb + b;
+            int64_t r0 = (int64_t)v * G.nb + b;
             const bool two = b + 1 <= b1;
-            const int64_t r1 = two ? r0 + 1 : r0;
+            int64_t r1 = two ? r0 + 1 : r0;
+            if (!DECT_IDX_OK(r0, (int64_t)G.nv * G.nb, CHK_OTF_RAY)) r0 = 0;
+            if (!DECT_IDX_OK(r1, (int64_t)G.nv * G.nb, CHK_OTF_RAY)) r1 = 0;
             const float4 R0 = __ldg(G.ray + r0), R1 = __ldg(G.ray + r1);
             const float2 I0 = __ldg(G.inv + r0), I1 = __ldg(G.inv + r1);
             const float2 y0 = __ldg(sino + r0), y1 = __ldg(sino + r1);

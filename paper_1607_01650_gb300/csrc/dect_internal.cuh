@@ -40,6 +40,51 @@ void count_launches(int64_t k);
 // Packed table entry: .x = pixel (or ray) index, .y = __float_as_int(length in mm).
 typedef int2 Entry;
 
+// ---------------------------------------------------------------------------
+// Index checks of the checked build (compiled with -DDECT_CHECKED).  A
+// checked access whose index falls outside [0, bound) is not made: the
+// caller substitutes a safe index, and the first such failure of the
+// process (site code << 48 | index) is recorded in this translation unit's
+// device word, which dect_check_status() reads and clears.  Without
+// DECT_CHECKED the checks compile to nothing.
+// ---------------------------------------------------------------------------
+enum CheckSite : unsigned {
+    CHK_GATHER_A = 1,     // A x: image index from the ray-major table
+    CHK_GATHER_AT = 2,    // A^T y: ray index from the pixel-major table
+    CHK_OTF_WALK = 3,     // on-the-fly A: pixel of the walk
+    CHK_OTF_RAY = 4,      // on-the-fly A^T: candidate ray
+    CHK_PLS_STENCIL = 5,  // PLS: neighbour of the 5-point stencil
+    CHK_FBP_BIN = 6,      // FBP: interpolation bin
+    CHK_SELFTEST = 7      // dect_selftest_index
+};
+
+typedef cudaError_t (*CheckReader)(unsigned long long *word);
+// register a translation unit's reader (called by static initialisers)
+int register_check_reader(CheckReader r);
+
+#ifdef DECT_CHECKED
+static __device__ unsigned long long g_check_word;
+
+static cudaError_t read_check_word(unsigned long long *w)
+{
+    cudaError_t e = cudaMemcpyFromSymbol(w, g_check_word, sizeof(*w));
+    const unsigned long long zero = 0ull;
+    if (e == cudaSuccess && *w) e = cudaMemcpyToSymbol(g_check_word, &zero, sizeof(zero));
+    return e;
+}
+static const int g_check_reader_registered = register_check_reader(read_check_word);
+
+__device__ __forceinline__ bool check_index(int64_t i, int64_t bound, unsigned site)
+{
+    if (i >= 0 && i < bound) return true;
+    atomicCAS(&g_check_word, 0ull, ((unsigned long long)site << 48) | ((unsigned long long)i & 0xffffffffffffull));
+    return false;
+}
+#define DECT_IDX_OK(i, bound, site) ::dect::check_index((int64_t)(i), (int64_t)(bound), (site))
+#else
+#define DECT_IDX_OK(i, bound, site) true
+#endif
+
 }  // namespace dect
 
 struct dect_plan {

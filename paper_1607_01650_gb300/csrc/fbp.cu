@@ -115,6 +115,7 @@ __global__ void __launch_bounds__(kFbpBlock) k_fbp_bp(const float *__restrict__ 
         if (!(t >= 0.0 && t <= tmax)) continue;
         int b0 = (int)floor(t);
         if (b0 > nb - 2) b0 = nb - 2;
+        if (!DECT_IDX_OK(b0, nb - 1, CHK_FBP_BIN)) b0 = 0;
         const float w = (float)(t - (double)b0);
         const float wt = (float)(half_dth * r * r);
 #pragma unroll

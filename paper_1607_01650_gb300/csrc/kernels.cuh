@@ -325,7 +325,8 @@ __device__ __forceinline__ Vec<Batch<NB>::VW> row_dot_g(const Entry *__restrict_
 // ---------------------------------------------------------------------------
 template <int NB, int G, int VWL, int R>
 __device__ __forceinline__ Vec<4> row_dot_w(const Entry *__restrict__ ent, int64_t b, int64_t e, int lr,
-                                            const float *__restrict__ src, unsigned long long pol)
+                                            const float *__restrict__ src, unsigned long long pol,
+                                            int64_t rows, unsigned site)
 {
     static_assert((NB == 16 || NB == 32 || NB == 64) && (VWL == 8 || VWL == 16) && VWL <= NB,
                   "wide row core: 16, 32 or 64 images, 8 or 16 per lane");
@@ -352,6 +353,7 @@ __device__ __forceinline__ Vec<4> row_dot_w(const Entry *__restrict__ ent, int64
                 const unsigned srcl = gbase + (j0 + j) * EG + grp;
                 pix[j] = __shfl_sync(0xffffffffu, cur.x, srcl);
                 w[j] = __int_as_float(__shfl_sync(0xffffffffu, cur.y, srcl));
+                if (!DECT_IDX_OK(pix[j], rows, site)) pix[j] = 0;
             }
             Vec<4> xv[RR][NV];
 #pragma unroll
@@ -386,20 +388,25 @@ __device__ __forceinline__ Vec<4> row_dot_w(const Entry *__restrict__ ent, int64
 
 // Gathers of one VW-wide vector of the NB images at index `pix`.
 template <int NB>
-struct GatherIL {  // interleaved [index][NB] in global memory
+struct GatherIL {  // interleaved [index][NB] in global memory, `rows` indices
     const float *src;
+    int64_t rows;
+    unsigned site;
     unsigned long long pol = l2_evict_last_policy();
     __device__ __forceinline__ Vec<Batch<NB>::VW> operator()(int pix, int vl) const
     {
+        if (!DECT_IDX_OK(pix, rows, site)) pix = 0;
         return ld_gather<Batch<NB>::VW>(src + (int64_t)pix * NB + vl * Batch<NB>::VW, pol);
     }
 };
+// src holds `rows` interleaved rows; site: the check site of its gathers.
 template <int NB, int G, bool IL, bool SBC = false>
 __device__ __forceinline__ Vec<Batch<NB>::VW> row_dot(const Entry *__restrict__ ent, int64_t b, int64_t e,
-                                                      const float *__restrict__ src, int64_t /*unused*/, int lr)
+                                                      const float *__restrict__ src, int64_t rows, int lr,
+                                                      unsigned site)
 {
     static_assert(IL, "only the interleaved layout is gathered");
-    return row_dot_g<NB, G, GatherIL<NB>, SBC>(ent, b, e, lr, GatherIL<NB>{src});
+    return row_dot_g<NB, G, GatherIL<NB>, SBC>(ent, b, e, lr, GatherIL<NB>{src, rows, site});
 }
 
 }  // namespace dect
@@ -407,8 +414,7 @@ __device__ __forceinline__ Vec<Batch<NB>::VW> row_dot(const Entry *__restrict__ 
 namespace dect {
 
 // ---------------------------------------------------------------------------
-// Bulk asynchronous copies (TMA, non-tensor form) into shared memory with
-// mbarrier completion.  Every wait is bounded: after `limit` failed polls the
+// mbarrier helpers.  Every wait is bounded: after `limit` failed polls the
 // caller gets false and records the timeout instead of spinning forever.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ unsigned smem_u32(const void *p)
@@ -445,24 +451,6 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, unsigned parity
     for (unsigned i = 0; i < limit; ++i)
         if (mbar_try_wait(bar, parity)) return true;
     return false;
-}
-
-// Order this thread's earlier generic-proxy accesses to shared memory before
-// later async-proxy (bulk copy) writes to it.
-__device__ __forceinline__ void fence_proxy_async_smem()
-{
-    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
-}
-
-// Copy `bytes` (a multiple of 16; both addresses 16-byte aligned) from global
-// to shared memory; completion is counted on `bar` as transaction bytes.
-__device__ __forceinline__ void bulk_copy_g2s(void *dst, const void *src, unsigned bytes, uint64_t *bar)
-{
-    asm volatile(
-        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
-            smem_u32(dst)),
-        "l"(src), "r"(bytes), "r"(smem_u32(bar))
-        : "memory");
 }
 
 }  // namespace dect

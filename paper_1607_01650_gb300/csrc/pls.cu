@@ -182,10 +182,13 @@ __device__ __forceinline__ float apply_op(const Stencil &S, int i, int j, int64_
 {
     const float c = val(p);
     float acc = 0.f, wsum = 0.f;
-    if (i > 0) { float w = S.w(p, p - S.n); acc += w * (c - val(p - S.n)); wsum += w; }
-    if (i + 1 < S.n) { float w = S.w(p, p + S.n); acc += w * (c - val(p + S.n)); wsum += w; }
-    if (j > 0) { float w = S.w(p, p - 1); acc += w * (c - val(p - 1)); wsum += w; }
-    if (j + 1 < S.n) { float w = S.w(p, p + 1); acc += w * (c - val(p + 1)); wsum += w; }
+    const int64_t N = (int64_t)S.n * S.n;
+    // neighbours inside the image only (out-of-image links are omitted, Eq. (14))
+    auto nb = [&](int64_t q) { return DECT_IDX_OK(q, N, CHK_PLS_STENCIL) ? q : p; };
+    if (i > 0) { const int64_t q = nb(p - S.n); float w = S.w(p, q); acc += w * (c - val(q)); wsum += w; }
+    if (i + 1 < S.n) { const int64_t q = nb(p + S.n); float w = S.w(p, q); acc += w * (c - val(q)); wsum += w; }
+    if (j > 0) { const int64_t q = nb(p - 1); float w = S.w(p, q); acc += w * (c - val(q)); wsum += w; }
+    if (j + 1 < S.n) { const int64_t q = nb(p + 1); float w = S.w(p, q); acc += w * (c - val(q)); wsum += w; }
     diag = 1.f + S.gamma * wsum;
     return c + S.gamma * acc;
 }

@@ -48,7 +48,7 @@ __global__ void k_from_il(const float *__restrict__ src, float *__restrict__ dst
 template <int NB, bool TILED>
 __global__ void __launch_bounds__(kOpBlock) k_rows_il(const int64_t *__restrict__ ptr, const Entry *__restrict__ ent,
                                                       int64_t rows, int n, const float *__restrict__ src,
-                                                      float *__restrict__ dst)
+                                                      int64_t src_rows, float *__restrict__ dst)
 {
     constexpr int G = 32, VW = Batch<NB>::VW, LPE = Batch<NB>::CPB;
     const int lr = threadIdx.x % G, grp = lr / LPE, vl = lr % LPE;
@@ -74,9 +74,9 @@ __global__ void __launch_bounds__(kOpBlock) k_rows_il(const int64_t *__restrict_
         }
         Vec<VW> acc;
         if constexpr (NB >= 16)
-            acc = row_dot_w<NB, G, 8, 2>(ent, b, e, lr, src, pol);
+            acc = row_dot_w<NB, G, 8, 2>(ent, b, e, lr, src, pol, src_rows, TILED ? CHK_GATHER_AT : CHK_GATHER_A);
         else
-            acc = row_dot<NB, G, true>(ent, b, e, src, 0, lr);
+            acc = row_dot<NB, G, true>(ent, b, e, src, src_rows, lr, TILED ? CHK_GATHER_AT : CHK_GATHER_A);
         if (ok && grp == 0) st_v<VW>(dst + row * NB + vl * VW, acc);
     }
 }
@@ -89,9 +89,9 @@ cudaError_t pass(const int64_t *ptr, const Entry *ent, int64_t rows_in, int64_t 
     const unsigned bi = (unsigned)((rows_in * NB + 255) / 256), bo = (unsigned)((rows_out * NB + 255) / 256);
     k_to_il<NB><<<bi, 256, 0, s>>>(src, in_il, rows_in, nimg);
     if (tiled)
-        k_rows_il<NB, true><<<kSMs, kOpBlock, 0, s>>>(ptr, ent, rows_out, n, in_il, out_il);
+        k_rows_il<NB, true><<<kSMs, kOpBlock, 0, s>>>(ptr, ent, rows_out, n, in_il, rows_in, out_il);
     else
-        k_rows_il<NB, false><<<kSMs, kOpBlock, 0, s>>>(ptr, ent, rows_out, n, in_il, out_il);
+        k_rows_il<NB, false><<<kSMs, kOpBlock, 0, s>>>(ptr, ent, rows_out, n, in_il, rows_in, out_il);
     k_from_il<NB><<<bo, 256, 0, s>>>(out_il, dst, rows_out, nimg);
     count_launches(3);
     return cudaGetLastError();

@@ -112,3 +112,18 @@ def test_variant_count_matches_the_header():
     assert m and int(m.group(1)) == dect.BWD_VARIANTS
     m = re.search(r"#define\s+DECT_FWD_VARIANTS\s+(\d+)", open(HEADER).read())
     assert m and int(m.group(1)) == dect.FWD_VARIANTS
+
+
+def test_checked_library_exports_and_host_checks(lib):
+    """The checked build exports every entry point; the plain build refuses an
+    out-of-range self-test index on the host (its kernel has no check)."""
+    from paper_1607_01650_gb300 import _build
+    chk = C.CDLL(_build.LIB_CHECKED)
+    missing = [n for n in declared_functions() if not hasattr(chk, n)]
+    assert not missing, missing
+    assert chk.dect_checked_build() == 1
+    cdll, _ = lib
+    assert cdll.dect_checked_build() == 0
+    cdll.dect_selftest_index.argtypes = [C.c_int, C.c_void_p]
+    assert cdll.dect_selftest_index(8, None) == 1   # DECT_ERR_INVALID_ARG, nothing enqueued
+    assert cdll.dect_selftest_index(-1, None) == 1
