@@ -67,8 +67,9 @@ def parse():
     ap.add_argument("--batched-otf", action="store_true",
                     help="batched workload through dect_adm_tv_batch (one launch per ADM phase over all slices, "
                          "on-the-fly projector) instead of dect_adm_tv_groups")
-    ap.add_argument("--train-slices", type=int, default=1024, help="learned workload: training slices")
-    ap.add_argument("--epochs", type=int, default=6, help="learned workload: training epochs")
+    ap.add_argument("--train-slices", type=int, default=2048,
+                    help="learned workload: training slices (x 2 energies = training pairs)")
+    ap.add_argument("--epochs", type=int, default=8, help="learned workload: training epochs")
     ap.add_argument("--workload", default="paper", choices=["paper", "batched", "learned", "stress", "fbp"],
                     help="paper: 32 slices of 512^2/60 views per step (the headline); batched: "
                          "64 slices of uneven size (256^2-512^2) and view count (30-180) per step; "
