@@ -49,6 +49,13 @@ class _Geom(C.Structure):
                 ("start", C.c_double), ("arc", C.c_double), ("det_offset", C.c_double)]
 
 
+class _Geom3(C.Structure):
+    _fields_ = [("n", C.c_int), ("nz", C.c_int), ("px", C.c_double), ("pz", C.c_double),
+                ("nv", C.c_int), ("nr", C.c_int), ("nc", C.c_int), ("pu", C.c_double), ("pv", C.c_double),
+                ("sod", C.c_double), ("sdd", C.c_double), ("start", C.c_double), ("arc", C.c_double),
+                ("off_u", C.c_double), ("off_v", C.c_double)]
+
+
 class _AdmParams(C.Structure):
     _fields_ = [("mu", C.c_double), ("rho", C.c_double), ("xi", C.c_double),
                 ("step_rule", C.c_int), ("max_iter", C.c_int), ("tol", C.c_double),
@@ -104,6 +111,16 @@ def _load():
             "orc_pls_diag": (None, [C.c_int, u8, C.c_double, C.c_double, d]),
             "orc_pls_pcg": (C.c_int, [C.c_int, u8, C.c_double, C.c_double, d, d,
                                       C.c_int, C.c_double, d]),
+            "orc3_ray": (None, [C.POINTER(_Geom3), C.c_int, C.c_int, C.c_int, d, d]),
+            "orc3_siddon_ray": (C.c_int, [C.POINTER(_Geom3), C.c_int, C.c_int, C.c_int, i32, d, C.c_int]),
+            "orc3_table_nnz": (C.c_int64, [C.POINTER(_Geom3)]),
+            "orc3_table_build": (None, [C.POINTER(_Geom3), i64, i32, d]),
+            "orc3_prewitt": (None, [C.c_int, C.c_int, d, d]),
+            "orc3_edge_mask": (None, [C.c_int, C.c_int, d, d, C.c_double, u8]),
+            "orc3_pls_apply": (None, [C.c_int, C.c_int, u8, C.c_double, C.c_double, d, d]),
+            "orc3_pls_diag": (None, [C.c_int, C.c_int, u8, C.c_double, C.c_double, d]),
+            "orc3_pls_pcg": (C.c_int, [C.c_int, C.c_int, u8, C.c_double, C.c_double, d, d,
+                                       C.c_int, C.c_double, d]),
             "orc_cnn_num_params": (C.c_int64, []),
             "orc_cnn_run": (None, [d, C.c_double, d, C.c_int, C.c_int, d, d, d, d]),
         }
@@ -547,3 +564,139 @@ def cnn_loss_grad(params, x, target, scale: float):
     _load().orc_cnn_run(_d(params), scale, _d(x), x.shape[0], x.shape[1], None, _d(target), _d(grad),
                         C.byref(loss))
     return float(loss.value), grad
+
+
+
+# ---------------------------------------------------------------------------
+# Cone-beam geometry and 3-D decomposition (Sec. 2.1, Fig. 1; Sec. 2.3,
+# Eq. (14) with 6 neighbours; Sec. 3)
+# ---------------------------------------------------------------------------
+
+def _geom3(g) -> _Geom3:
+    return _Geom3(g.n, g.nz, g.px, g.pz, g.nv, g.nr, g.nc, g.pu, g.pv, g.sod, g.sdd, g.start, g.arc,
+                  g.off_u, g.off_v)
+
+
+def ray3(geom, v: int, r: int, c: int):
+    """(S, D): source and detector-cell centre of ray (v, r, c), mm."""
+    S = np.zeros(3)
+    D = np.zeros(3)
+    _load().orc3_ray(C.byref(_geom3(geom)), v, r, c, _d(S), _d(D))
+    return S, D
+
+
+def siddon_ray3(geom, v: int, r: int, c: int):
+    """(voxel indices, lengths in mm) of ray (v, r, c), in walk order."""
+    cap = 2 * geom.n + geom.nz + 8
+    idx = np.zeros(cap, np.int32)
+    ln = np.zeros(cap)
+    k = _load().orc3_siddon_ray(C.byref(_geom3(geom)), v, r, c, idx.ctypes.data_as(C.POINTER(C.c_int32)),
+                                _d(ln), cap)
+    return idx[:k].copy(), ln[:k].copy()
+
+
+@dataclasses.dataclass
+class Table3:
+    """Ray-major table of the cone-beam A: row (v nr + r) nc + c."""
+    geom: object
+    rowptr: np.ndarray
+    idx: np.ndarray
+    len: np.ndarray
+
+    @property
+    def m(self) -> int:
+        return self.geom.nv * self.geom.nr * self.geom.nc
+
+    @property
+    def npix(self) -> int:
+        return self.geom.n * self.geom.n * self.geom.nz
+
+    @property
+    def nnz(self) -> int:
+        return int(self.rowptr[-1])
+
+    def _args(self):
+        return (C.c_int64(self.m), self.rowptr.ctypes.data_as(C.POINTER(C.c_int64)),
+                self.idx.ctypes.data_as(C.POINTER(C.c_int32)), _d(self.len))
+
+
+def table3(geom) -> Table3:
+    lib = _load()
+    g = _geom3(geom)
+    nnz = lib.orc3_table_nnz(C.byref(g))
+    M = geom.nv * geom.nr * geom.nc
+    rowptr = np.zeros(M + 1, np.int64)
+    idx = np.zeros(max(nnz, 1), np.int32)
+    ln = np.zeros(max(nnz, 1))
+    lib.orc3_table_build(C.byref(g), rowptr.ctypes.data_as(C.POINTER(C.c_int64)),
+                         idx.ctypes.data_as(C.POINTER(C.c_int32)), _d(ln))
+    return Table3(geom, rowptr, idx[:nnz], ln[:nnz])
+
+
+def project3(t: Table3, x) -> np.ndarray:
+    """y = A x: volume [nz][n][n] -> projections [nv][nr][nc]."""
+    x = _f64(x).reshape(-1)
+    y = np.zeros(t.m)
+    _load().orc_project(*t._args(), _d(x), _d(y))
+    return y.reshape(t.geom.nv, t.geom.nr, t.geom.nc)
+
+
+def backproject3(t: Table3, y) -> np.ndarray:
+    """x = A^T y: [nv][nr][nc] -> [nz][n][n]."""
+    y = _f64(y).reshape(-1)
+    x = np.zeros(t.npix)
+    m, rp, ix, ln = t._args()
+    _load().orc_backproject(m, C.c_int64(t.npix), rp, ix, ln, _d(y), _d(x))
+    return x.reshape(t.geom.nz, t.geom.n, t.geom.n)
+
+
+def prewitt3(x) -> np.ndarray:
+    """3-D Prewitt magnitude, replicate padding: x [nz][n][n]."""
+    x = _f64(x)
+    out = np.zeros_like(x)
+    _load().orc3_prewitt(x.shape[-1], x.shape[0], _d(x), _d(out))
+    return out
+
+
+def edge_mask3(xh, xl, tau: float) -> np.ndarray:
+    xh, xl = _f64(xh), _f64(xl)
+    mask = np.zeros(xh.shape, np.uint8)
+    _load().orc3_edge_mask(xh.shape[-1], xh.shape[0], _d(xh), _d(xl), tau,
+                           mask.ctypes.data_as(C.POINTER(C.c_uint8)))
+    return mask
+
+
+def pls_apply3(mask, gamma: float, eps: float, u) -> np.ndarray:
+    u = _f64(u)
+    mask = np.ascontiguousarray(mask, np.uint8)
+    out = np.zeros_like(u)
+    _load().orc3_pls_apply(u.shape[-1], u.shape[0], mask.ctypes.data_as(C.POINTER(C.c_uint8)), gamma, eps,
+                           _d(u), _d(out))
+    return out
+
+
+def pls_diag3(mask, gamma: float, eps: float) -> np.ndarray:
+    mask = np.ascontiguousarray(mask, np.uint8)
+    out = np.zeros(mask.shape, np.float64)
+    _load().orc3_pls_diag(mask.shape[-1], mask.shape[0], mask.ctypes.data_as(C.POINTER(C.c_uint8)), gamma, eps,
+                          _d(out))
+    return out
+
+
+def pls_pcg3(mask, gamma: float, eps: float, d, max_iter: int, tol: float):
+    d = _f64(d)
+    mask = np.ascontiguousarray(mask, np.uint8)
+    u = np.zeros_like(d)
+    rr = C.c_double(0.0)
+    it = _load().orc3_pls_pcg(d.shape[-1], d.shape[0], mask.ctypes.data_as(C.POINTER(C.c_uint8)), gamma, eps,
+                              _d(d), _d(u), max_iter, tol, C.byref(rr))
+    return u, int(it), float(rr.value)
+
+
+def pls_decompose3(xh, xl, prm: PlsParams):
+    """3-D PLS decomposition (Eq. (13)-(15), 6 neighbours): volumes [nz][n][n]."""
+    d1, d2 = direct_decompose(prm.eta, xh, xl)
+    mask = edge_mask3(xh, xl, prm.tau)
+    u1, i1, _ = pls_pcg3(mask, prm.gamma, prm.eps, d1, prm.max_iter, prm.tol)
+    u2, i2, _ = pls_pcg3(mask, prm.gamma, prm.eps, d2, prm.max_iter, prm.tol)
+    return u1, u2, mask, (i1, i2)

@@ -49,6 +49,14 @@
  *      e_ik = eps if pixel i or k is an edge, else 1.  Magnitudes, maxima
  *      and the comparison with tau are FP64.
  *   R16 PCG: Jacobi preconditioner, initial guess D^{-1} x.
+ *   R19 cone-beam geometry (Sec. 2.1, Fig. 1, Sec. 3): circular orbit in the
+ *      plane z = 0, flat 2-D detector (rows along z), one ray per detector
+ *      cell from the source point to the cell centre; Siddon in 3-D with the
+ *      rule of R10 (a ray on a slice boundary goes to the +z voxel).
+ *   R20 3-D edge weights: Prewitt in 3-D (each component the difference of
+ *      the two neighbours along its axis summed over the 3 x 3 neighbourhood
+ *      of the other two axes, replicate padding); N_i of Eq. (14) is the 6
+ *      face neighbours of a voxel inside the volume.
  */
 #include <math.h>
 #include <stdint.h>
@@ -1044,4 +1052,263 @@ void orc_cnn_run(const double *prm, double s, const double *x, int H, int W, dou
     }
     free(xin); free(a1); free(e1); free(p1); free(a3); free(e2); free(p2); free(a5); free(bt);
     free(c2); free(a7); free(d2); free(c1); free(a9); free(d1); free(o);
+}
+
+/* ======================================================================== */
+/* Cone-beam geometry and 3-D decomposition (Sec. 2.1, Fig. 1: circular    */
+/* source orbit, flat 2-D detector; Sec. 2.3, Eq. (14) with the 6          */
+/* neighbours of a voxel; Sec. 3)                                           */
+/* ======================================================================== */
+
+/*
+ * Geometry.  The source turns in the plane z = 0: view v at angle
+ * th_v = start + v arc / nv, source S = SOD (cos th, sin th, 0); the flat
+ * detector is centred at (SOD - SDD)(cos th, sin th, 0) with axes
+ * e_u = (-sin th, cos th, 0) (columns) and e_z = (0, 0, 1) (rows); cell
+ * (row r, column c) is centred at u_c = (c - (nc - 1) / 2) pu + off_u,
+ * z_r = (r - (nr - 1) / 2) pv + off_v.  One ray per cell, from the source
+ * point to the cell centre; ray index (v nr + r) nc + c.  The volume is
+ * n x n x nz voxels of px x px x pz, centred on the origin; voxel index
+ * (k n + i) n + j with k along z, i along y (row), j along x (column).
+ */
+typedef struct {
+    int n, nz;
+    double px, pz;
+    int nv, nr, nc;
+    double pu, pv;
+    double sod, sdd, start, arc, off_u, off_v;
+} orc_geom3;
+
+void orc3_ray(const orc_geom3 *g, int v, int r, int c, double S[3], double D[3])
+{
+    double th = g->start + (double)v * (g->arc / (double)g->nv);
+    double ct = cos(th), st = sin(th);
+    S[0] = g->sod * ct;
+    S[1] = g->sod * st;
+    S[2] = 0.0;
+    double cx = (g->sod - g->sdd) * ct, cy = (g->sod - g->sdd) * st;
+    double u = ((double)c - 0.5 * (double)(g->nc - 1)) * g->pu + g->off_u;
+    double z = ((double)r - 0.5 * (double)(g->nr - 1)) * g->pv + g->off_v;
+    D[0] = cx - u * st;
+    D[1] = cy + u * ct;
+    D[2] = z;
+}
+
+/*
+ * Siddon's method in 3-D (ref. [42]), the same rule as in 2-D (R10): the
+ * crossing parameters of the x, y and z grid planes inside the volume box
+ * are collected, sorted and de-duplicated; the piece between consecutive
+ * parameters goes to the voxel holding its midpoint; consecutive pieces in
+ * one voxel are summed.  Writes up to `cap` (voxel, length in mm) pairs;
+ * returns the count.
+ */
+int orc3_siddon_ray(const orc_geom3 *g, int v, int r, int c, int32_t *idx, double *len, int cap)
+{
+    double S[3], D[3];
+    orc3_ray(g, v, r, c, S, D);
+    const int n = g->n, nz = g->nz;
+    const double d[3] = {D[0] - S[0], D[1] - S[1], D[2] - S[2]};
+    const double L = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+    const double lo[3] = {-0.5 * (double)n * g->px, -0.5 * (double)n * g->px, -0.5 * (double)nz * g->pz};
+    const double sz[3] = {g->px, g->px, g->pz};
+    const int cnt_ax[3] = {n, n, nz};
+    double amin = 0.0, amax = 1.0;
+    for (int a = 0; a < 3; ++a) {
+        const double hi = lo[a] + (double)cnt_ax[a] * sz[a];
+        if (d[a] != 0.0) {
+            double t0 = (lo[a] - S[a]) / d[a], t1 = (hi - S[a]) / d[a];
+            amin = fmax(amin, fmin(t0, t1));
+            amax = fmin(amax, fmax(t0, t1));
+        } else if (!(S[a] >= lo[a] && S[a] < hi)) {
+            return 0;
+        }
+    }
+    if (!(amin < amax)) return 0;
+    double *al = (double *)malloc(sizeof(double) * (size_t)(2 * n + nz + 8));
+    int na = 0;
+    al[na++] = amin;
+    al[na++] = amax;
+    for (int a = 0; a < 3; ++a) {
+        if (d[a] == 0.0) continue;
+        for (int k = 0; k <= cnt_ax[a]; ++k) {
+            double t = (lo[a] + (double)k * sz[a] - S[a]) / d[a];
+            if (t > amin && t < amax) al[na++] = t;
+        }
+    }
+    qsort(al, (size_t)na, sizeof(double), cmp_double);
+    int cnt = 0, last = -1;
+    for (int k = 0; k + 1 < na; ++k) {
+        double a0 = al[k], a1 = al[k + 1];
+        if (!(a1 > a0)) continue;
+        double mid = 0.5 * (a0 + a1);
+        int jj = (int)floor((S[0] + mid * d[0] - lo[0]) / sz[0]);
+        int ii = (int)floor((S[1] + mid * d[1] - lo[1]) / sz[1]);
+        int kk = (int)floor((S[2] + mid * d[2] - lo[2]) / sz[2]);
+        if (jj < 0 || jj >= n || ii < 0 || ii >= n || kk < 0 || kk >= nz) continue;
+        int vox = (kk * n + ii) * n + jj;
+        double seg = (a1 - a0) * L;
+        if (cnt > 0 && last == vox) {
+            if (cnt - 1 < cap) len[cnt - 1] += seg;
+            continue;
+        }
+        if (cnt < cap) {
+            idx[cnt] = vox;
+            len[cnt] = seg;
+        }
+        last = vox;
+        ++cnt;
+    }
+    free(al);
+    return cnt;
+}
+
+int64_t orc3_table_nnz(const orc_geom3 *g)
+{
+    int cap = 2 * g->n + g->nz + 8;
+    int32_t *ti = (int32_t *)malloc(sizeof(int32_t) * (size_t)cap);
+    double *tl = (double *)malloc(sizeof(double) * (size_t)cap);
+    int64_t total = 0;
+    for (int v = 0; v < g->nv; ++v)
+        for (int r = 0; r < g->nr; ++r)
+            for (int c = 0; c < g->nc; ++c) total += orc3_siddon_ray(g, v, r, c, ti, tl, cap);
+    free(ti);
+    free(tl);
+    return total;
+}
+
+/* Ray-major table of the cone-beam A: rowptr[M + 1], idx[nnz], len[nnz]. */
+void orc3_table_build(const orc_geom3 *g, int64_t *rowptr, int32_t *idx, double *len)
+{
+    int cap = 2 * g->n + g->nz + 8;
+    int64_t pos = 0, row = 0;
+    rowptr[0] = 0;
+    for (int v = 0; v < g->nv; ++v)
+        for (int r = 0; r < g->nr; ++r)
+            for (int c = 0; c < g->nc; ++c) {
+                pos += orc3_siddon_ray(g, v, r, c, idx + pos, len + pos, cap);
+                rowptr[++row] = pos;
+            }
+}
+
+/*
+ * 3-D Prewitt magnitude (reading R14 in 3-D): along each axis the
+ * difference of the two neighbours along it, summed over the 3 x 3
+ * neighbourhood of the other two axes, indices clamped to the volume;
+ * |g| = sqrt(gx^2 + gy^2 + gz^2), FP64.
+ */
+void orc3_prewitt(int n, int nz, const double *x, double *mag)
+{
+#define CL(a, m) ((a) < 0 ? 0 : ((a) >= (m) ? (m) - 1 : (a)))
+#define X3(k, i, j) x[((int64_t)CL(k, nz) * n + CL(i, n)) * n + CL(j, n)]
+    for (int k = 0; k < nz; ++k)
+        for (int i = 0; i < n; ++i)
+            for (int j = 0; j < n; ++j) {
+                double gx = 0.0, gy = 0.0, gz = 0.0;
+                for (int s = -1; s <= 1; ++s)
+                    for (int t = -1; t <= 1; ++t) {
+                        gx += X3(k + s, i + t, j + 1) - X3(k + s, i + t, j - 1);
+                        gy += X3(k + s, i + 1, j + t) - X3(k + s, i - 1, j + t);
+                        gz += X3(k + 1, i + s, j + t) - X3(k - 1, i + s, j + t);
+                    }
+                mag[((int64_t)k * n + i) * n + j] = sqrt(gx * gx + gy * gy + gz * gz);
+            }
+#undef X3
+#undef CL
+}
+
+/* Edge mask of the two energy volumes (R14 in 3-D), decided in FP64. */
+void orc3_edge_mask(int n, int nz, const double *xh, const double *xl, double tau, uint8_t *mask)
+{
+    int64_t N = (int64_t)n * n * nz;
+    double *mh = (double *)malloc(sizeof(double) * (size_t)N);
+    double *ml = (double *)malloc(sizeof(double) * (size_t)N);
+    orc3_prewitt(n, nz, xh, mh);
+    orc3_prewitt(n, nz, xl, ml);
+    double Mh = 0.0, Ml = 0.0;
+    for (int64_t p = 0; p < N; ++p) {
+        if (mh[p] > Mh) Mh = mh[p];
+        if (ml[p] > Ml) Ml = ml[p];
+    }
+    for (int64_t p = 0; p < N; ++p)
+        mask[p] = (uint8_t)((Mh > 0.0 && mh[p] / Mh > tau) || (Ml > 0.0 && ml[p] / Ml > tau));
+    free(mh);
+    free(ml);
+}
+
+/* out = (I + gamma L_e) u over the 6 neighbours of each voxel inside the
+   volume (R13 with N_i of Eq. (14) in 3-D); e_ik as in 2-D. */
+void orc3_pls_apply(int n, int nz, const uint8_t *mask, double gamma, double eps, const double *u, double *out)
+{
+    const int64_t plane = (int64_t)n * n;
+    for (int k = 0; k < nz; ++k)
+        for (int i = 0; i < n; ++i)
+            for (int j = 0; j < n; ++j) {
+                int64_t p = k * plane + (int64_t)i * n + j;
+                double s = 0.0;
+                if (k > 0) s += edge_w(mask, p, p - plane, eps) * (u[p] - u[p - plane]);
+                if (k + 1 < nz) s += edge_w(mask, p, p + plane, eps) * (u[p] - u[p + plane]);
+                if (i > 0) s += edge_w(mask, p, p - n, eps) * (u[p] - u[p - n]);
+                if (i + 1 < n) s += edge_w(mask, p, p + n, eps) * (u[p] - u[p + n]);
+                if (j > 0) s += edge_w(mask, p, p - 1, eps) * (u[p] - u[p - 1]);
+                if (j + 1 < n) s += edge_w(mask, p, p + 1, eps) * (u[p] - u[p + 1]);
+                out[p] = u[p] + gamma * s;
+            }
+}
+
+/* Jacobi diagonal 1 + gamma sum_k e_ik over the 6 neighbours. */
+void orc3_pls_diag(int n, int nz, const uint8_t *mask, double gamma, double eps, double *diag)
+{
+    const int64_t plane = (int64_t)n * n;
+    for (int k = 0; k < nz; ++k)
+        for (int i = 0; i < n; ++i)
+            for (int j = 0; j < n; ++j) {
+                int64_t p = k * plane + (int64_t)i * n + j;
+                double s = 0.0;
+                if (k > 0) s += edge_w(mask, p, p - plane, eps);
+                if (k + 1 < nz) s += edge_w(mask, p, p + plane, eps);
+                if (i > 0) s += edge_w(mask, p, p - n, eps);
+                if (i + 1 < n) s += edge_w(mask, p, p + n, eps);
+                if (j > 0) s += edge_w(mask, p, p - 1, eps);
+                if (j + 1 < n) s += edge_w(mask, p, p + 1, eps);
+                diag[p] = 1.0 + gamma * s;
+            }
+}
+
+/* Jacobi PCG for the 3-D system from u = d (as orc_pls_pcg). */
+int orc3_pls_pcg(int n, int nz, const uint8_t *mask, double gamma, double eps, const double *d,
+                 double *u, int max_iter, double tol, double *relres)
+{
+    int64_t N = (int64_t)n * n * nz;
+    double *r = (double *)malloc(sizeof(double) * (size_t)N);
+    double *z = (double *)malloc(sizeof(double) * (size_t)N);
+    double *p = (double *)malloc(sizeof(double) * (size_t)N);
+    double *Ap = (double *)malloc(sizeof(double) * (size_t)N);
+    double *M = (double *)malloc(sizeof(double) * (size_t)N);
+    orc3_pls_diag(n, nz, mask, gamma, eps, M);
+    memcpy(u, d, sizeof(double) * (size_t)N);
+    orc3_pls_apply(n, nz, mask, gamma, eps, u, Ap);
+    for (int64_t i = 0; i < N; ++i) r[i] = d[i] - Ap[i];
+    double bn = sqrt(dot(N, d, d));
+    for (int64_t i = 0; i < N; ++i) { z[i] = r[i] / M[i]; p[i] = z[i]; }
+    double rz = dot(N, r, z);
+    int it = 0;
+    double rn = sqrt(dot(N, r, r));
+    while (it < max_iter) {
+        if (tol > 0.0 && (bn == 0.0 || rn / bn < tol)) break;
+        orc3_pls_apply(n, nz, mask, gamma, eps, p, Ap);
+        double pAp = dot(N, p, Ap);
+        if (pAp <= 0.0) break;
+        double a = rz / pAp;
+        for (int64_t i = 0; i < N; ++i) { u[i] += a * p[i]; r[i] -= a * Ap[i]; }
+        ++it;
+        rn = sqrt(dot(N, r, r));
+        for (int64_t i = 0; i < N; ++i) z[i] = r[i] / M[i];
+        double rz_new = dot(N, r, z);
+        double beta = (rz != 0.0) ? rz_new / rz : 0.0;
+        rz = rz_new;
+        for (int64_t i = 0; i < N; ++i) p[i] = z[i] + beta * p[i];
+    }
+    if (relres) *relres = (bn > 0.0) ? rn / bn : 0.0;
+    free(r); free(z); free(p); free(Ap); free(M);
+    return it;
 }

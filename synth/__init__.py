@@ -109,6 +109,57 @@ def tiny_geometry(n: int = 8, nv: int = 12, nb: int = 12, px: float = 1.0,
                     start=start, arc=arc, det_offset=det_offset)
 
 
+@dataclasses.dataclass(frozen=True)
+class ConeGeometry:
+    """Circular cone-beam geometry with a flat 2-D detector (Sec. 2.1, Fig. 1;
+    Sec. 3): source orbit in the plane z = 0; detector cell (row r, column c)
+    at u_c = (c - (nc - 1) / 2) pu + off_u, z_r = (r - (nr - 1) / 2) pv + off_v;
+    an n x n x nz volume of px x px x pz voxels centred on the origin."""
+    n: int
+    nz: int
+    px: float
+    pz: float
+    nv: int
+    nr: int
+    nc: int
+    pu: float
+    pv: float
+    sod: float
+    sdd: float
+    start: float = 0.0
+    arc: float = 2.0 * math.pi
+    off_u: float = 0.0
+    off_v: float = 0.0
+
+    @property
+    def n_vox(self) -> int:
+        return self.n * self.n * self.nz
+
+    @property
+    def n_rays(self) -> int:
+        return self.nv * self.nr * self.nc
+
+
+def tiny_cone(n: int = 4, nz: int = 3, nv: int = 6, nr: int = 3, nc: int = 5, px: float = 1.0,
+              pz: float = 1.0, sod: float = 20.0, sdd: float = 40.0, start: float = 0.2,
+              off_u: float = 0.0, off_v: float = 0.0) -> ConeGeometry:
+    """Small cone geometry for oracle pins and quick parity cases: the
+    detector covers the volume's footprint with some margin."""
+    mag = sdd / (sod - 0.75 * n * px)
+    pu = 1.6 * n * px * mag / nc
+    pv = 1.4 * nz * pz * mag / nr
+    return ConeGeometry(n=n, nz=nz, px=px, pz=pz, nv=nv, nr=nr, nc=nc, pu=pu, pv=pv, sod=sod, sdd=sdd,
+                        start=start, off_u=off_u, off_v=off_v)
+
+
+def cone_geometry() -> ConeGeometry:
+    """A cone-beam stand-in for the paper's scan (Sec. 3) at the benchmark's
+    scale: 256^2 x 64 voxels of 0.5 mm, 60 views over 360 deg, 64 rows x 368
+    columns of 0.6 mm at SOD 500 / SDD 1000."""
+    return ConeGeometry(n=256, nz=64, px=0.5, pz=0.5, nv=60, nr=64, nc=368, pu=0.6, pv=0.6,
+                        sod=500.0, sdd=1000.0)
+
+
 # --------------------------------------------------------------------------
 # Phantoms
 # --------------------------------------------------------------------------

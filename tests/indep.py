@@ -239,3 +239,80 @@ def chambolle_pock_joint(A, g, n, mu, iters=20000):
         fb = 2.0 * f_new - f
         f = f_new
     return f.reshape(2, n, n)
+
+
+# ---------------------------------------------------------------------------
+# Cone-beam (3-D) counterparts
+# ---------------------------------------------------------------------------
+
+def rays3_np(geom):
+    """Source and detector-cell points [M, 3], ray order (v, r, c) (Fig. 1 with a 2-D detector)."""
+    v = np.arange(geom.nv, dtype=np.float64)
+    th = geom.start + v * (geom.arc / geom.nv)
+    c, s = np.cos(th), np.sin(th)
+    u = (np.arange(geom.nc) - 0.5 * (geom.nc - 1)) * geom.pu + geom.off_u
+    z = (np.arange(geom.nr) - 0.5 * (geom.nr - 1)) * geom.pv + geom.off_v
+    S = np.stack([geom.sod * c, geom.sod * s, np.zeros_like(c)], -1)                  # [nv, 3]
+    Cd = np.stack([(geom.sod - geom.sdd) * c, (geom.sod - geom.sdd) * s, np.zeros_like(c)], -1)
+    eu = np.stack([-s, c, np.zeros_like(c)], -1)
+    D = (Cd[:, None, None, :] + u[None, None, :, None] * eu[:, None, None, :]
+         + z[None, :, None, None] * np.array([0.0, 0.0, 1.0])[None, None, None, :])    # [nv, nr, nc, 3]
+    S = np.broadcast_to(S[:, None, None, :], D.shape)
+    return S.reshape(-1, 3), D.reshape(-1, 3)
+
+
+def clip_matrix3(geom) -> np.ndarray:
+    """Dense A[M, N]: length of each ray inside each voxel box (mm), by slab clipping."""
+    S, D = rays3_np(geom)
+    d = D - S
+    L = np.sqrt((d * d).sum(-1))
+    n, nz = geom.n, geom.nz
+    ex = -0.5 * n * geom.px + np.arange(n) * geom.px
+    ez = -0.5 * nz * geom.pz + np.arange(nz) * geom.pz
+    ax_lo, ax_hi = _clip_interval(S[:, 0:1], d[:, 0:1], ex[None, :], ex[None, :] + geom.px)   # [M, n] cols
+    ay_lo, ay_hi = _clip_interval(S[:, 1:2], d[:, 1:2], ex[None, :], ex[None, :] + geom.px)   # [M, n] rows
+    az_lo, az_hi = _clip_interval(S[:, 2:3], d[:, 2:3], ez[None, :], ez[None, :] + geom.pz)   # [M, nz]
+    a_lo = np.maximum(np.maximum(np.maximum(az_lo[:, :, None, None], ay_lo[:, None, :, None]),
+                                 ax_lo[:, None, None, :]), 0.0)
+    a_hi = np.minimum(np.minimum(np.minimum(az_hi[:, :, None, None], ay_hi[:, None, :, None]),
+                                 ax_hi[:, None, None, :]), 1.0)
+    A = np.clip(a_hi - a_lo, 0.0, None) * L[:, None, None, None]
+    return A.reshape(S.shape[0], nz * n * n)
+
+
+def box_chord3(geom) -> np.ndarray:
+    """Length of each ray inside the volume box [M]."""
+    S, D = rays3_np(geom)
+    d = D - S
+    L = np.sqrt((d * d).sum(-1))
+    lo = np.array([-0.5 * geom.n * geom.px] * 2 + [-0.5 * geom.nz * geom.pz])
+    hi = -lo
+    a_lo, a_hi = np.zeros(len(S)), np.ones(len(S))
+    for a in range(3):
+        l, h = _clip_interval(S[:, a], d[:, a], lo[a], hi[a])
+        a_lo = np.maximum(a_lo, l)
+        a_hi = np.minimum(a_hi, h)
+    return np.clip(a_hi - a_lo, 0.0, None) * L
+
+
+def pls_matrix3(mask: np.ndarray, gamma: float, eps: float) -> np.ndarray:
+    """Half the Hessian of |u - d|^2 + gamma R(u) with R of Eq. (14) over the 6
+    neighbours of each voxel, assembled pair by pair (as pls_matrix)."""
+    nz, n, _ = mask.shape
+    N = nz * n * n
+    H = 2.0 * np.eye(N)
+    for k in range(nz):
+        for i in range(n):
+            for j in range(n):
+                p = (k * n + i) * n + j
+                for dk, di, dj in ((-1, 0, 0), (1, 0, 0), (0, -1, 0), (0, 1, 0), (0, 0, -1), (0, 0, 1)):
+                    kk, ii, jj = k + dk, i + di, j + dj
+                    if 0 <= kk < nz and 0 <= ii < n and 0 <= jj < n:
+                        q = (kk * n + ii) * n + jj
+                        e = eps if (mask[k, i, j] or mask[kk, ii, jj]) else 1.0
+                        w = gamma * e
+                        H[p, p] += w
+                        H[q, q] += w
+                        H[p, q] -= w
+                        H[q, p] -= w
+    return 0.5 * H
