@@ -70,12 +70,13 @@ def parse():
     ap.add_argument("--train-slices", type=int, default=2048,
                     help="learned workload: training slices (x 2 energies = training pairs)")
     ap.add_argument("--epochs", type=int, default=8, help="learned workload: training epochs")
-    ap.add_argument("--workload", default="paper", choices=["paper", "batched", "learned", "stress", "fbp"],
+    ap.add_argument("--workload", default="paper", choices=["paper", "batched", "learned", "stress", "fbp", "cone"],
                     help="paper: 32 slices of 512^2/60 views per step (the headline); batched: "
                          "64 slices of uneven size (256^2-512^2) and view count (30-180) per step; "
                          "learned: CNN warm start trained on 256^2 pairs, evaluated at 512^2; "
                          "stress: 16 slices of 1024^2/360 views/1472 bins, 300 ADM iterations; "
-                         "fbp: the paper workload warm-started from dect_fbp, beside the cold run")
+                         "fbp: the paper workload warm-started from dect_fbp, beside the cold run; "
+                         "cone: cone-beam operators and 3-D decomposition at 256^2 x 64")
     return ap.parse_args()
 
 
@@ -473,6 +474,64 @@ def run_learned(args, rank, world, local):
     return 0
 
 
+def run_cone(args, rank, world, local):
+    """Cone-beam operators and 3-D decomposition (the paper's scan geometry at
+    the benchmark's scale): A x and A^T y of the 3-D Siddon table on 16
+    volumes (one interleaved pass over each table) and the 6-neighbour PLS
+    of 4 volume pairs, timed with CUDA events."""
+    import torch
+    import paper_1607_01650_gb300 as dect
+    torch.cuda.set_device(local)
+    g = synth.cone_geometry()
+    t0 = time.perf_counter()
+    plan = dect.ConePlan(g, device=local)
+    plan_s = time.perf_counter() - t0
+    V = 16
+    x = torch.rand((V, g.nz, g.n, g.n), device="cuda") * 0.02
+    y = torch.empty((V, g.nv, g.nr, g.nc), device="cuda")
+    peak, peak_src = measured_peaks()
+
+    def timed(fn, reps):
+        for _ in range(max(1, args.warmup)):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    ops = {}
+    launches0 = dect.kernel_launches()
+    with ClockSampler(local) as clk:
+        for name, fn, rows_ptr in (("project", lambda: dect.project_cone(plan, x, y=y), g.n_rays),
+                                   ("backproject", lambda: dect.backproject_cone(plan, y, x=x), g.n_vox)):
+            ms = timed(fn, args.steps)
+            alg = 8 * plan.nnz + 8 * (rows_ptr + 1) + 4 * V * (g.n_vox + g.n_rays)
+            ops[name] = {"ms_per_call": round(ms, 3), "gbs": round(alg / (ms / 1e3) / 1e9, 1),
+                         "frac_of_hbm_peak": round(alg / (ms / 1e3) / 1e9 / peak, 4),
+                         "intersections_per_s": plan.nnz * V / (ms / 1e3)}
+        xv = (torch.rand((4, 2, g.nz, g.n, g.n), device="cuda") * 0.02)
+        pp = dect.PlsParams(**PLS)
+        pls_ms = timed(lambda: dect.pls_decompose_cone(xv, pp), args.steps)
+    launches = dect.kernel_launches() - launches0
+    line = {"metric": "cone-beam A x and A^T y, 256^2 x 64 voxels, 60 views x 64 x 368 cells (16 volumes)",
+            "value": ops["project"]["intersections_per_s"], "unit": "intersections/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ops["project"]["ms_per_call"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "cone-beam 256x256x64 at 0.5 mm, 60 views over 360 deg, 64 rows x 368 columns "
+                                   "x 0.6 mm, SOD 500 / SDD 1000",
+                       "volumes": V, "nnz": plan.nnz, "plan_seconds": round(plan_s, 2),
+                       "table_bytes": plan.table_bytes, "operators": ops, "peak_source": peak_src,
+                       "pls_volume_pairs": 4, "pls_ms_per_call": round(pls_ms, 2),
+                       "l2": "inputs larger than L2"},
+            "gpu_launches": int(launches), "clocks": clk.summary()}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_fbp(args, rank, world, local):
     """FBP warm start: the headline's slices (512^2 / 60 views, 32 per step),
     each step FBP of both energies (dect_fbp), ADM from it to the 1e-4 stop,
@@ -629,6 +688,8 @@ def main():
         return run_learned(args, rank, world, local)
     if args.workload == "fbp":
         return run_fbp(args, rank, world, local)
+    if args.workload == "cone":
+        return run_cone(args, rank, world, local)
     torch.cuda.set_device(local)
     dist = None
     if world > 1:

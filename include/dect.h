@@ -95,6 +95,41 @@ typedef struct {
 dect_status dect_plan_create(const dect_geometry *geom, int device, dect_stream stream,
                              dect_plan **out);
 
+/*
+ * Cone-beam geometry (Sec. 2.1, Fig. 1 with a flat 2-D detector; the
+ * paper's scan, Sec. 3): the source turns in the plane z = 0; view v at
+ * t_v = start + v * (arc / n_views), source SOD (cos t, sin t, 0); detector
+ * centred at (SOD - SDD)(cos t, sin t, 0) with axes (-sin t, cos t, 0)
+ * (columns) and (0, 0, 1) (rows); cell (row r, column c) at
+ * u_c = (c - (n_cols - 1) / 2) pitch_u + offset_u,
+ * z_r = (r - (n_rows - 1) / 2) pitch_v + offset_v.  Volume of n x n x nz
+ * voxels of pixel_mm x pixel_mm x slice_mm centred on the origin, index
+ * (k n + i) n + j (k along z, i = row = y, j = column = x); projections
+ * [view][row][column].
+ */
+typedef struct {
+    int n, nz;
+    double pixel_mm, slice_mm;
+    int n_views, n_rows, n_cols;
+    double pitch_u_mm, pitch_v_mm;
+    double sod_mm, sdd_mm, start_rad, arc_rad, offset_u_mm, offset_v_mm;
+} dect_cone_geometry;
+
+/*
+ * Build the plan of a cone-beam geometry: the Siddon system matrix in 3-D
+ * (crossings of the x, y and z grid planes, each piece given to the voxel
+ * holding its midpoint, FP64 crossing parameters, FP32 lengths), ray-major
+ * and voxel-major, as dect_plan_create does in 2-D.  The plan serves
+ * dect_project, dect_backproject, dect_plan_get_info (n_pixels = voxels,
+ * n_rays = cells x views) and dect_plan_copy_table; the fan-beam solvers
+ * and the on-the-fly projector refuse it (DECT_ERR_INVALID_ARG).
+ * Errors: DECT_ERR_INVALID_ARG (bad geometry: sizes < 1, non-positive
+ * sizes or pitches, SOD not beyond the volume's half diagonal, SDD <= SOD,
+ * more than 2^30 rays or voxels), DECT_ERR_OOM, DECT_ERR_CUDA.
+ */
+dect_status dect_plan_create_cone(const dect_cone_geometry *geom, int device, dect_stream stream,
+                                  dect_plan **out);
+
 /* Free a plan and its device tables (NULL is a no-op). Synchronises the device. */
 dect_status dect_plan_destroy(dect_plan *plan);
 
@@ -330,6 +365,23 @@ dect_status dect_pls_decompose(const float *x, int n, int batch, const dect_pls_
  */
 dect_status dect_pls_edge_mask(const float *x, int n, int batch, double edge_tau, uint8_t *mask,
                                dect_stream stream);
+
+/*
+ * PLS decomposition of `batch` cone-beam volumes of nz slices of n x n
+ * voxels (x: [batch][2][nz][n][n], u the same), Eq. (11)-(15) with the
+ * 6 face neighbours of a voxel inside the volume as N_i of Eq. (14) and the
+ * 3-D Prewitt magnitude for the edge map (each component the difference of
+ * the two neighbours along its axis summed over the 3 x 3 neighbourhood of
+ * the other two axes, replicate padding, FP32).  Otherwise as
+ * dect_pls_decompose (which is this call with nz = 1 and the 2-D Prewitt).
+ * Errors: as dect_pls_decompose; nz outside 1..4096 is DECT_ERR_INVALID_ARG.
+ */
+dect_status dect_pls_decompose_cone(const float *x, int n, int nz, int batch, const dect_pls_params *params,
+                                    float *u, dect_pls_report *reports, dect_stream stream);
+
+/* The edge map of dect_pls_decompose_cone: mask [batch][nz][n][n]. */
+dect_status dect_pls_edge_mask_cone(const float *x, int n, int nz, int batch, double edge_tau, uint8_t *mask,
+                                    dect_stream stream);
 
 /*
  * dect_pls_decompose without any device allocation.  (The paper has no

@@ -17,7 +17,8 @@ from typing import List, Optional, Sequence, Tuple
 
 from . import _build
 
-__all__ = ["Geometry", "Plan", "AdmParams", "PlsParams", "AdmReport", "AdmProfile", "DectError",
+__all__ = ["Geometry", "Plan", "ConePlan", "project_cone", "backproject_cone", "pls_decompose_cone",
+           "pls_edge_mask_cone", "AdmParams", "PlsParams", "AdmReport", "AdmProfile", "DectError",
            "load", "project", "backproject", "project_otf", "backproject_otf", "adm_tv", "adm_tv_batch",
            "pls_decompose", "pls_edge_mask", "kernel_launches",
            "library_path"]
@@ -37,6 +38,14 @@ class _Geometry(C.Structure):
 class _PlanInfo(C.Structure):
     _fields_ = [("n_pixels", C.c_int64), ("n_rays", C.c_int64), ("nnz", C.c_int64),
                 ("table_bytes", C.c_int64), ("n_grid_aligned", C.c_int64)]
+
+
+class _ConeGeometry(C.Structure):
+    _fields_ = [("n", C.c_int), ("nz", C.c_int), ("pixel_mm", C.c_double), ("slice_mm", C.c_double),
+                ("n_views", C.c_int), ("n_rows", C.c_int), ("n_cols", C.c_int),
+                ("pitch_u_mm", C.c_double), ("pitch_v_mm", C.c_double), ("sod_mm", C.c_double),
+                ("sdd_mm", C.c_double), ("start_rad", C.c_double), ("arc_rad", C.c_double),
+                ("offset_u_mm", C.c_double), ("offset_v_mm", C.c_double)]
 
 
 class _AdmParams(C.Structure):
@@ -78,6 +87,9 @@ _P = C.c_void_p
 _SIGS = {
     "dect_plan_create": (C.c_int, [C.POINTER(_Geometry), C.c_int, _P, C.POINTER(_P)]),
     "dect_plan_destroy": (C.c_int, [_P]),
+    "dect_plan_create_cone": (C.c_int, [C.POINTER(_ConeGeometry), C.c_int, _P, C.POINTER(_P)]),
+    "dect_pls_decompose_cone": (C.c_int, [_P, C.c_int, C.c_int, C.c_int, C.POINTER(_PlsParams), _P, _P, _P]),
+    "dect_pls_edge_mask_cone": (C.c_int, [_P, C.c_int, C.c_int, C.c_int, C.c_double, _P, _P]),
     "dect_plan_get_info": (C.c_int, [_P, C.POINTER(_PlanInfo)]),
     "dect_plan_copy_table": (C.c_int, [_P, _P, _P, _P, _P]),
     "dect_project": (C.c_int, [_P, _P, _P, C.c_int, _P]),
@@ -259,6 +271,71 @@ class Plan:
         _check(load().dect_plan_copy_table(self._h, rowptr.ctypes.data, pix.ctypes.data,
                                            ln.ctypes.data, _stream()), "dect_plan_copy_table")
         return rowptr, pix[:self.nnz], ln[:self.nnz]
+
+
+class ConePlan(Plan):
+    """Cone-beam plan (dect_plan_create_cone): 3-D Siddon table of a
+    circular orbit with a flat 2-D detector.  geom: an object with n, nz,
+    px, pz, nv, nr, nc, pu, pv, sod, sdd, start, arc, off_u, off_v (mm, rad)."""
+
+    def __init__(self, geom, device: int = 0, stream=None):  # noqa: super-init replaced
+        import torch
+        self.geom = geom
+        self.device = device
+        lib = load()
+        h = C.c_void_p()
+        cg = _ConeGeometry(geom.n, geom.nz, geom.px, geom.pz, geom.nv, geom.nr, geom.nc, geom.pu, geom.pv,
+                           geom.sod, geom.sdd, geom.start, geom.arc, geom.off_u, geom.off_v)
+        with torch.cuda.device(device):
+            _check(lib.dect_plan_create_cone(C.byref(cg), device, _stream(stream), C.byref(h)),
+                   "dect_plan_create_cone")
+        self._h = h
+        info = _PlanInfo()
+        _check(lib.dect_plan_get_info(h, C.byref(info)), "dect_plan_get_info")
+        self.nnz = int(info.nnz)
+        self.n_pixels = int(info.n_pixels)
+        self.n_rays = int(info.n_rays)
+        self.table_bytes = int(info.table_bytes)
+        self.n_grid_aligned = int(info.n_grid_aligned)
+
+    def table(self):
+        """(rowptr int64 [M+1], voxel int32 [nnz], len float32 [nnz]) as numpy arrays."""
+        import numpy as np
+        rowptr = np.zeros(self.n_rays + 1, np.int64)
+        pix = np.zeros(max(self.nnz, 1), np.int32)
+        ln = np.zeros(max(self.nnz, 1), np.float32)
+        _check(load().dect_plan_copy_table(self._h, rowptr.ctypes.data_as(C.c_void_p),
+                                           pix.ctypes.data_as(C.c_void_p), ln.ctypes.data_as(C.c_void_p),
+                                           _stream()), "dect_plan_copy_table")
+        return rowptr, pix[:self.nnz], ln[:self.nnz]
+
+
+def project_cone(plan: ConePlan, x, y=None, stream=None):
+    """y = A x for volumes x [..., nz, n, n] -> y [..., nv, nr, nc] (cone-beam plan)."""
+    import torch
+    g = plan.geom
+    if x.shape[-3:] != (g.nz, g.n, g.n):
+        raise DectError("x must end in (nz, n, n)")
+    batch = x.numel() // (g.nz * g.n * g.n)
+    if y is None:
+        y = torch.empty(x.shape[:-3] + (g.nv, g.nr, g.nc), device=x.device, dtype=torch.float32)
+    _check(load().dect_project(plan.handle, _ptr(x, torch.float32, plan.device), _ptr(y, torch.float32, plan.device),
+                               batch, _stream(stream)), "dect_project")
+    return y
+
+
+def backproject_cone(plan: ConePlan, y, x=None, stream=None):
+    """x = A^T y for projections y [..., nv, nr, nc] -> x [..., nz, n, n] (cone-beam plan)."""
+    import torch
+    g = plan.geom
+    if y.shape[-3:] != (g.nv, g.nr, g.nc):
+        raise DectError("y must end in (nv, nr, nc)")
+    batch = y.numel() // (g.nv * g.nr * g.nc)
+    if x is None:
+        x = torch.empty(y.shape[:-3] + (g.nz, g.n, g.n), device=y.device, dtype=torch.float32)
+    _check(load().dect_backproject(plan.handle, _ptr(y, torch.float32, plan.device),
+                                   _ptr(x, torch.float32, plan.device), batch, _stream(stream)), "dect_backproject")
+    return x
 
 
 def project(plan: Plan, x, y=None, stream=None):
@@ -534,6 +611,36 @@ def pls_edge_mask(x, tau: float, mask=None, stream=None):
         mask = torch.empty((batch, n, n), dtype=torch.uint8, device=x.device)
     _check(load().dect_pls_edge_mask(_ptr(x, torch.float32, dev), n, batch, float(tau),
                                      _ptr(mask, torch.uint8, dev), _stream(stream)), "dect_pls_edge_mask")
+    return mask
+
+
+def pls_decompose_cone(x, params: PlsParams, u=None, stream=None):
+    """3-D PLS decomposition (6 neighbours): x [B, 2, nz, n, n] -> u [B, 2, nz, n, n]."""
+    import torch
+    if x.dim() != 5 or x.shape[1] != 2 or x.shape[3] != x.shape[4]:
+        raise DectError("x must be [B, 2, nz, n, n]")
+    batch, nz, n = x.shape[0], x.shape[2], x.shape[-1]
+    if u is None:
+        u = torch.empty_like(x)
+    dev = x.device.index
+    rep = (_PlsReport * max(batch, 1))()
+    _check(load().dect_pls_decompose_cone(_ptr(x, torch.float32, dev), n, nz, batch, C.byref(params._c()),
+                                          _ptr(u, torch.float32, dev), C.cast(rep, C.c_void_p), _stream(stream)),
+           "dect_pls_decompose_cone")
+    return u, [(tuple(r.iters), tuple(r.relres)) for r in rep[:batch]]
+
+
+def pls_edge_mask_cone(x, tau: float, mask=None, stream=None):
+    """Edge map of the 3-D decomposition: x [B, 2, nz, n, n] -> uint8 [B, nz, n, n]."""
+    import torch
+    if x.dim() != 5 or x.shape[1] != 2:
+        raise DectError("x must be [B, 2, nz, n, n]")
+    batch, nz, n = x.shape[0], x.shape[2], x.shape[-1]
+    if mask is None:
+        mask = torch.empty((batch, nz, n, n), dtype=torch.uint8, device=x.device)
+    _check(load().dect_pls_edge_mask_cone(_ptr(x, torch.float32, x.device.index), n, nz, batch, float(tau),
+                                          _ptr(mask, torch.uint8, x.device.index), _stream(stream)),
+           "dect_pls_edge_mask_cone")
     return mask
 
 

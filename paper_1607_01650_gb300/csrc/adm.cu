@@ -1479,7 +1479,7 @@ extern "C" dect_status dect_adm_tv_ex(const dect_plan *plan, const float *m, flo
                                       const dect_adm_params *prm, dect_adm_report *reports,
                                       dect_adm_profile *prof, dect_stream stream)
 {
-    if (!plan || !prm || n_slices < 0) return DECT_ERR_INVALID_ARG;
+    if (!plan || !prm || n_slices < 0 || plan->nz > 0) return DECT_ERR_INVALID_ARG;  // fan-beam plans only
     if (n_slices == 0) return DECT_OK;
     if (!m || !x) return DECT_ERR_INVALID_ARG;
     if (!(prm->mu > 0) || !(prm->rho > 0) || !(prm->beta[0] > 0) || !(prm->beta[1] > 0) ||
@@ -1536,7 +1536,7 @@ extern "C" dect_status dect_adm_tv_groups(const dect_adm_group *groups, int n_gr
     if (!groups || n_groups < 0 || !prm || workers < 0) return DECT_ERR_INVALID_ARG;
     if (n_groups == 0) return DECT_OK;
     for (int i = 0; i < n_groups; ++i) {
-        if (!groups[i].plan || groups[i].n_slices < 0) return DECT_ERR_INVALID_ARG;
+        if (!groups[i].plan || groups[i].n_slices < 0 || groups[i].plan->nz > 0) return DECT_ERR_INVALID_ARG;
         for (int j = 0; j < i; ++j)
             if (groups[j].plan == groups[i].plan) return DECT_ERR_INVALID_ARG;  // plans must differ
     }

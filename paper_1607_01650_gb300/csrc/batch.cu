@@ -742,7 +742,7 @@ using namespace dect;
 
 extern "C" dect_status dect_project_otf(const dect_plan *plan, const float *x, float *y, int batch, dect_stream stream)
 {
-    if (!plan || batch < 0) return DECT_ERR_INVALID_ARG;
+    if (!plan || batch < 0 || plan->nz > 0) return DECT_ERR_INVALID_ARG;
     if (batch == 0) return DECT_OK;
     if (!x || !y) return DECT_ERR_INVALID_ARG;
     DECT_CUDA(cudaSetDevice(plan->device));
@@ -753,7 +753,7 @@ extern "C" dect_status dect_project_otf(const dect_plan *plan, const float *x, f
 extern "C" dect_status dect_backproject_otf(const dect_plan *plan, const float *y, float *x, int batch,
                                             dect_stream stream)
 {
-    if (!plan || batch < 0) return DECT_ERR_INVALID_ARG;
+    if (!plan || batch < 0 || plan->nz > 0) return DECT_ERR_INVALID_ARG;
     if (batch == 0) return DECT_OK;
     if (!x || !y) return DECT_ERR_INVALID_ARG;
     DECT_CUDA(cudaSetDevice(plan->device));
@@ -775,7 +775,7 @@ extern "C" dect_status dect_adm_tv_batch(const dect_adm_group *groups, int n_gro
     int device = -1;
     for (int gi = 0; gi < n_groups; ++gi) {
         const dect_adm_group &G = groups[gi];
-        if (!G.plan || G.n_slices < 0) return DECT_ERR_INVALID_ARG;
+        if (!G.plan || G.n_slices < 0 || G.plan->nz > 0) return DECT_ERR_INVALID_ARG;  // fan-beam plans only
         if (G.n_slices > 0 && (!G.m || !G.x)) return DECT_ERR_INVALID_ARG;
         if (device >= 0 && G.plan->device != device) return DECT_ERR_INVALID_ARG;
         device = G.plan->device;

@@ -89,8 +89,10 @@ __device__ __forceinline__ bool check_index(int64_t i, int64_t bound, unsigned s
 
 struct dect_plan {
     dect_geometry g;
+    dect_cone_geometry cone;  // cone-beam plans (nz > 1 or nr > 1; zero otherwise)
     int device;
     int n, nv, nb;
+    int nz, nr;               // cone-beam: slices and detector rows (0 for fan-beam plans)
     int64_t N, M, nnz;
     int64_t n_grid_aligned;
     int64_t *rowptr;   // [M + 1], ray-major table (CSR of A)

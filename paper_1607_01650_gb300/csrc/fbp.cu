@@ -140,7 +140,7 @@ using namespace dect;
 
 extern "C" dect_status dect_fbp(const dect_plan *plan, const float *m, float *x, int batch, dect_stream stream)
 {
-    if (!plan || batch < 0) return DECT_ERR_INVALID_ARG;
+    if (!plan || batch < 0 || plan->nz > 0) return DECT_ERR_INVALID_ARG;  // fan-beam plans only
     if (batch == 0) return DECT_OK;
     if (!m || !x) return DECT_ERR_INVALID_ARG;
     const dect_geometry &g = plan->g;

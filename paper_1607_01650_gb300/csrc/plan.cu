@@ -204,6 +204,89 @@ __global__ void k_siddon_fill(const RayPts *__restrict__ rays, int64_t M, Grid g
 }
 
 // ---------------------------------------------------------------------------
+// Cone-beam walk (3-D Siddon): the same rule with a third axis.  The volume
+// is n x n x nz voxels, index (kz n + row) n + col; gxy is the grid of x and
+// y, gz the grid of z.
+// ---------------------------------------------------------------------------
+struct RayPts3 {
+    double sx, sy, sz, dx_, dy_, dz_;
+};
+
+__device__ int siddon_walk3(const RayPts3 &r, const Grid &gxy, const Grid &gz, Entry *out)
+{
+    const double dx = __dsub_rn(r.dx_, r.sx), dy = __dsub_rn(r.dy_, r.sy), dz = __dsub_rn(r.dz_, r.sz);
+    const double L = __dsqrt_rn(__dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz)));
+    const double s[3] = {r.sx, r.sy, r.sz}, d[3] = {dx, dy, dz};
+    const Grid *gs[3] = {&gxy, &gxy, &gz};
+    double amin = 0.0, amax = 1.0;
+    for (int a = 0; a < 3; ++a) {
+        const Grid &g = *gs[a];
+        const double hi = __dadd_rn(g.lo, __dmul_rn((double)g.n, g.px));
+        if (d[a] != 0.0) {
+            const double t0 = cross_param(g.lo, s[a], d[a]), t1 = cross_param(hi, s[a], d[a]);
+            amin = fmax(amin, fmin(t0, t1));
+            amax = fmin(amax, fmax(t0, t1));
+        } else if (!(s[a] >= g.lo && s[a] < hi)) {
+            return 0;
+        }
+    }
+    if (!(amin < amax)) return 0;
+    AxisWalk w[3];
+    for (int a = 0; a < 3; ++a) axis_init(w[a], *gs[a], s[a], d[a], amin, amax);
+    const int n = gxy.n, nz = gz.n;
+    int cnt = 0, pend = -1;
+    double pend_len = 0.0, cur = amin;
+    for (int guard = 0; guard < 2 * n + nz + 6; ++guard) {
+        const double a1 = fmin(fmin(fmin(w[0].next, w[1].next), w[2].next), amax);
+        if (a1 > cur) {
+            const double mid = __dmul_rn(0.5, __dadd_rn(cur, a1));
+            int idx[3];
+            for (int a = 0; a < 3; ++a) {
+                const double pos = __dadd_rn(s[a], __dmul_rn(mid, d[a]));
+                idx[a] = (int)floor(__ddiv_rn(__dsub_rn(pos, gs[a]->lo), gs[a]->px));
+            }
+            if (idx[0] >= 0 && idx[0] < n && idx[1] >= 0 && idx[1] < n && idx[2] >= 0 && idx[2] < nz) {
+                const int vox = (idx[2] * n + idx[1]) * n + idx[0];
+                const double seg = __dmul_rn(__dsub_rn(a1, cur), L);
+                if (vox == pend) {
+                    pend_len = __dadd_rn(pend_len, seg);
+                } else {
+                    if (pend >= 0) {
+                        if (out) out[cnt] = make_int2(pend, __float_as_int(__double2float_rn(pend_len)));
+                        ++cnt;
+                    }
+                    pend = vox;
+                    pend_len = seg;
+                }
+            }
+        }
+        if (a1 >= amax) break;
+        for (int a = 0; a < 3; ++a)
+            if (w[a].next == a1) axis_advance(w[a], *gs[a], s[a], d[a], amax);
+        cur = a1;
+    }
+    if (pend >= 0) {
+        if (out) out[cnt] = make_int2(pend, __float_as_int(__double2float_rn(pend_len)));
+        ++cnt;
+    }
+    return cnt;
+}
+
+__global__ void k_siddon3_count(const RayPts3 *__restrict__ rays, int64_t M, Grid gxy, Grid gz,
+                                int64_t *__restrict__ counts)
+{
+    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r < M) counts[r] = siddon_walk3(rays[r], gxy, gz, nullptr);
+}
+
+__global__ void k_siddon3_fill(const RayPts3 *__restrict__ rays, int64_t M, Grid gxy, Grid gz,
+                               const int64_t *__restrict__ rowptr, Entry *__restrict__ ent)
+{
+    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r < M) siddon_walk3(rays[r], gxy, gz, ent + rowptr[r]);
+}
+
+// ---------------------------------------------------------------------------
 // Exclusive scan of int64 counts (in place into out[0..n], out[n] = total).
 // ---------------------------------------------------------------------------
 constexpr int kScanBlock = 1024;
@@ -624,6 +707,180 @@ extern "C" dect_status dect_plan_create(const dect_geometry *geom, int device, d
     cudaFree(d_cursor); cudaFree(d_ccnt64); cudaFree(d_tmp);
 #undef PLAN_CUDA
     (void)st;
+    *out = p;
+    return DECT_OK;
+}
+
+namespace {
+
+bool cone_ok(const dect_cone_geometry *g)
+{
+    if (!g) return false;
+    if (g->n < 1 || g->n > 4096 || g->nz < 1 || g->nz > 4096 || g->n_views < 1 || g->n_rows < 1 ||
+        g->n_cols < 1)
+        return false;
+    const double vals[] = {g->pixel_mm, g->slice_mm, g->pitch_u_mm, g->pitch_v_mm, g->sod_mm, g->sdd_mm,
+                           g->start_rad, g->arc_rad, g->offset_u_mm, g->offset_v_mm};
+    for (double v : vals)
+        if (!std::isfinite(v)) return false;
+    if (!(g->pixel_mm > 0) || !(g->slice_mm > 0) || !(g->pitch_u_mm > 0) || !(g->pitch_v_mm > 0) ||
+        !(g->arc_rad > 0))
+        return false;
+    const double half_diag = 0.5 * g->n * g->pixel_mm * std::sqrt(2.0);
+    if (!(g->sod_mm > half_diag) || !(g->sdd_mm > g->sod_mm)) return false;
+    if ((int64_t)g->n_views * g->n_rows * g->n_cols > (int64_t)1 << 30) return false;
+    if ((int64_t)g->n * g->n * g->nz > (int64_t)1 << 30) return false;
+    return true;
+}
+
+}  // namespace
+
+extern "C" dect_status dect_plan_create_cone(const dect_cone_geometry *geom, int device, dect_stream stream,
+                                             dect_plan **out)
+{
+    if (!out || !cone_ok(geom)) return DECT_ERR_INVALID_ARG;
+    *out = nullptr;
+    int ndev = 0;
+    DECT_CUDA(cudaGetDeviceCount(&ndev));
+    if (device < 0 || device >= ndev) return DECT_ERR_INVALID_ARG;
+    DECT_CUDA(cudaSetDevice(device));
+    cudaStream_t s = (cudaStream_t)stream;
+
+    dect_plan *p = new dect_plan();
+    std::memset(p, 0, sizeof(*p));
+    // the fan-beam fields that describe the in-plane geometry
+    p->g.n = geom->n;
+    p->g.pixel_mm = geom->pixel_mm;
+    p->g.n_views = geom->n_views;
+    p->g.n_bins = geom->n_cols;
+    p->g.pitch_mm = geom->pitch_u_mm;
+    p->g.sod_mm = geom->sod_mm;
+    p->g.sdd_mm = geom->sdd_mm;
+    p->g.start_rad = geom->start_rad;
+    p->g.arc_rad = geom->arc_rad;
+    p->g.det_offset_mm = geom->offset_u_mm;
+    p->cone = *geom;
+    p->device = device;
+    p->n = geom->n;
+    p->nz = geom->nz;
+    p->nv = geom->n_views;
+    p->nr = geom->n_rows;
+    p->nb = geom->n_cols;
+    p->N = (int64_t)geom->n * geom->n * geom->nz;
+    p->M = (int64_t)geom->n_views * geom->n_rows * geom->n_cols;
+    for (int k = 0; k < 6; ++k) p->bwd_choice[k] = p->fwd_choice[k] = -1;
+
+    // ray end points on the host, FP64 (ray (v, r, c) -> (v nr + r) nc + c)
+    std::vector<RayPts3> h(p->M);
+    for (int v = 0; v < p->nv; ++v) {
+        const double th = geom->start_rad + (double)v * (geom->arc_rad / (double)p->nv);
+        const double c = std::cos(th), sn = std::sin(th);
+        const double sx = geom->sod_mm * c, sy = geom->sod_mm * sn;
+        const double cx = (geom->sod_mm - geom->sdd_mm) * c, cy = (geom->sod_mm - geom->sdd_mm) * sn;
+        for (int r = 0; r < p->nr; ++r) {
+            const double z = ((double)r - 0.5 * (double)(p->nr - 1)) * geom->pitch_v_mm + geom->offset_v_mm;
+            for (int b = 0; b < p->nb; ++b) {
+                const double u = ((double)b - 0.5 * (double)(p->nb - 1)) * geom->pitch_u_mm + geom->offset_u_mm;
+                RayPts3 q;
+                q.sx = sx;
+                q.sy = sy;
+                q.sz = 0.0;
+                q.dx_ = cx - u * sn;
+                q.dy_ = cy + u * c;
+                q.dz_ = z;
+                h[((size_t)v * p->nr + r) * p->nb + b] = q;
+            }
+        }
+    }
+    Grid gxy, gz;
+    gxy.n = p->n;
+    gxy.px = geom->pixel_mm;
+    gxy.lo = -0.5 * (double)p->n * geom->pixel_mm;
+    gz.n = p->nz;
+    gz.px = geom->slice_mm;
+    gz.lo = -0.5 * (double)p->nz * geom->slice_mm;
+
+    RayPts3 *d_rays = nullptr;
+    int64_t *d_cnt = nullptr, *d_ccnt64 = nullptr;
+    int *d_ccnt = nullptr, *d_cursor = nullptr;
+    Entry *d_tmp = nullptr;
+    auto fail = [&](dect_status code) {
+        cudaStreamSynchronize(s);
+        cudaFree(d_rays); cudaFree(d_cnt); cudaFree(d_ccnt); cudaFree(d_cursor); cudaFree(d_ccnt64); cudaFree(d_tmp);
+        cudaFree(p->rowptr); cudaFree(p->ent); cudaFree(p->colptr); cudaFree(p->tent);
+        delete p;
+        return code;
+    };
+#define PLAN_CUDA(call)                                                            \
+    do {                                                                           \
+        cudaError_t e_ = (call);                                                   \
+        if (e_ != cudaSuccess) {                                                   \
+            set_error(#call, e_);                                                  \
+            return fail(e_ == cudaErrorMemoryAllocation ? DECT_ERR_OOM : DECT_ERR_CUDA); \
+        }                                                                          \
+    } while (0)
+    // rays within 1e-9 mm of running along a grid plane (the midpoint rule
+    // then gives them to the + side)
+    for (size_t k = 0; k < h.size(); ++k) {
+        const RayPts3 &q = h[k];
+        const double d[3] = {q.dx_ - q.sx, q.dy_ - q.sy, q.dz_ - q.sz}, o[3] = {q.sx, q.sy, q.sz};
+        const double L = std::sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+        const Grid *gg[3] = {&gxy, &gxy, &gz};
+        for (int a = 0; a < 3; ++a)
+            if (std::fabs(d[a]) <= 1e-12 * L) {
+                const double f = (o[a] - gg[a]->lo) / gg[a]->px;
+                if (std::fabs(f - std::rint(f)) * gg[a]->px < 1e-9) {
+                    ++p->n_grid_aligned;
+                    break;
+                }
+            }
+    }
+    PLAN_CUDA(cudaMalloc(&d_rays, sizeof(RayPts3) * p->M));
+    PLAN_CUDA(cudaMemcpyAsync(d_rays, h.data(), sizeof(RayPts3) * p->M, cudaMemcpyHostToDevice, s));
+    PLAN_CUDA(cudaMalloc(&d_cnt, sizeof(int64_t) * p->M));
+    PLAN_CUDA(cudaMalloc(&p->rowptr, sizeof(int64_t) * (p->M + 1)));
+    const int T = 128;
+    k_siddon3_count<<<(unsigned)((p->M + T - 1) / T), T, 0, s>>>(d_rays, p->M, gxy, gz, d_cnt);
+    PLAN_CUDA(cudaGetLastError());
+    PLAN_CUDA(scan_exclusive(d_cnt, p->M, p->rowptr, s));
+    int64_t nnz = 0;
+    PLAN_CUDA(cudaMemcpyAsync(&nnz, p->rowptr + p->M, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    PLAN_CUDA(cudaStreamSynchronize(s));
+    p->nnz = nnz;
+    if (nnz >= ((int64_t)1 << 31)) return fail(DECT_ERR_INVALID_ARG);
+    const size_t ne = (size_t)(nnz > 0 ? nnz : 1) + kTablePad;
+    PLAN_CUDA(cudaMalloc(&p->ent, sizeof(Entry) * ne));
+    PLAN_CUDA(cudaMemsetAsync(p->ent, 0, sizeof(Entry) * ne, s));
+    k_siddon3_fill<<<(unsigned)((p->M + T - 1) / T), T, 0, s>>>(d_rays, p->M, gxy, gz, p->rowptr, p->ent);
+    PLAN_CUDA(cudaGetLastError());
+    // voxel-major transpose (rays increasing inside a voxel)
+    PLAN_CUDA(cudaMalloc(&d_ccnt, sizeof(int) * p->N));
+    PLAN_CUDA(cudaMalloc(&d_cursor, sizeof(int) * p->N));
+    PLAN_CUDA(cudaMalloc(&d_ccnt64, sizeof(int64_t) * p->N));
+    PLAN_CUDA(cudaMalloc(&p->colptr, sizeof(int64_t) * (p->N + 1)));
+    PLAN_CUDA(cudaMalloc(&d_tmp, sizeof(Entry) * ne));
+    PLAN_CUDA(cudaMalloc(&p->tent, sizeof(Entry) * ne));
+    PLAN_CUDA(cudaMemsetAsync(p->tent, 0, sizeof(Entry) * ne, s));
+    PLAN_CUDA(cudaMemsetAsync(d_ccnt, 0, sizeof(int) * p->N, s));
+    PLAN_CUDA(cudaMemsetAsync(d_cursor, 0, sizeof(int) * p->N, s));
+    if (nnz > 0) {
+        k_col_count<<<kSMs * 8, 256, 0, s>>>(p->ent, nnz, d_ccnt);
+        PLAN_CUDA(cudaGetLastError());
+    }
+    k_int_to_i64<<<(unsigned)((p->N + 255) / 256), 256, 0, s>>>(d_ccnt, p->N, d_ccnt64);
+    PLAN_CUDA(cudaGetLastError());
+    PLAN_CUDA(scan_exclusive(d_ccnt64, p->N, p->colptr, s));
+    if (nnz > 0) {
+        k_col_scatter<<<(unsigned)((p->M + T - 1) / T), T, 0, s>>>(p->rowptr, p->ent, p->M, p->colptr, d_cursor,
+                                                                   d_tmp);
+        PLAN_CUDA(cudaGetLastError());
+        const int64_t threads = p->N * 32;
+        k_col_sort<<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(p->colptr, p->N, d_tmp, p->tent);
+        PLAN_CUDA(cudaGetLastError());
+    }
+    PLAN_CUDA(cudaStreamSynchronize(s));
+    cudaFree(d_rays); cudaFree(d_cnt); cudaFree(d_ccnt); cudaFree(d_cursor); cudaFree(d_ccnt64); cudaFree(d_tmp);
+#undef PLAN_CUDA
     *out = p;
     return DECT_OK;
 }

@@ -42,7 +42,7 @@ struct PlsDev {
 };
 
 struct PlsConst {
-    int n;
+    int n, nz;   // nz = 1: 2-D images (4 neighbours); nz > 1: volumes (6 neighbours)
     int64_t N;
     int nvec;
     float gamma, eps;
@@ -116,9 +116,26 @@ __device__ __forceinline__ float prewitt_at(const float *__restrict__ x, int n, 
     return __fsqrt_rn(__fadd_rn(__fmul_rn(gx, gx), __fmul_rn(gy, gy)));
 }
 
+// 3-D Prewitt magnitude (volumes of nz > 1 slices), FP32, each component
+// summed in the order of the two outer offsets s, t = -1, 0, 1.
+__device__ __forceinline__ float prewitt3_at(const float *__restrict__ x, int n, int nz, int k, int i, int j)
+{
+    auto X = [&](int kk, int ii, int jj) {
+        return x[((int64_t)clampi(kk, 0, nz - 1) * n + clampi(ii, 0, n - 1)) * n + clampi(jj, 0, n - 1)];
+    };
+    float gx = 0.f, gy = 0.f, gz = 0.f;
+    for (int a = -1; a <= 1; ++a)
+        for (int b = -1; b <= 1; ++b) {
+            gx = __fadd_rn(gx, __fsub_rn(X(k + a, i + b, j + 1), X(k + a, i + b, j - 1)));
+            gy = __fadd_rn(gy, __fsub_rn(X(k + a, i + 1, j + b), X(k + a, i - 1, j + b)));
+            gz = __fadd_rn(gz, __fsub_rn(X(k + 1, i + a, j + b), X(k - 1, i + a, j + b)));
+        }
+    return __fsqrt_rn(__fadd_rn(__fadd_rn(__fmul_rn(gx, gx), __fmul_rn(gy, gy)), __fmul_rn(gz, gz)));
+}
+
 // d = D^{-1} x (FP64), written as the initial u (skipped when u is null);
 // Prewitt magnitudes and their maxima.
-__global__ void k_prep(const float *__restrict__ x, int n, int64_t N, double a, double b, double c,
+__global__ void k_prep(const float *__restrict__ x, int n, int nz, int64_t N, double a, double b, double c,
                        double e, float *__restrict__ u, float *__restrict__ mh,
                        float *__restrict__ ml, int *__restrict__ maxbits)
 {
@@ -135,8 +152,10 @@ __global__ void k_prep(const float *__restrict__ x, int n, int64_t N, double a, 
             u[(int64_t)(2 * s) * N + p] = (float)d1;
             u[(int64_t)(2 * s + 1) * N + p] = (float)d2;
         }
-        const int i = (int)(p / n), j = (int)(p % n);
-        const float g1 = prewitt_at(xs, n, i, j), g2 = prewitt_at(ls, n, i, j);
+        const int64_t plane = (int64_t)n * n;
+        const int k = (int)(p / plane), i = (int)((p % plane) / n), j = (int)(p % n);
+        const float g1 = nz > 1 ? prewitt3_at(xs, n, nz, k, i, j) : prewitt_at(xs, n, i, j);
+        const float g2 = nz > 1 ? prewitt3_at(ls, n, nz, k, i, j) : prewitt_at(ls, n, i, j);
         mh[(int64_t)s * N + p] = g1;
         ml[(int64_t)s * N + p] = g2;
         lmax_h = fmaxf(lmax_h, g1);
@@ -172,19 +191,26 @@ __global__ void k_mask(const float *__restrict__ mh, const float *__restrict__ m
 // also returns the Jacobi diagonal.
 struct Stencil {
     const unsigned char *mk;
-    int n;
+    int n, nz;
     float gamma, eps;
     __device__ __forceinline__ float w(int64_t p, int64_t q) const { return (mk[p] | mk[q]) ? eps : 1.f; }
 };
 
+// (I + gamma L_e) applied at element p (slice k, row i, column j) of vector
+// `val`; also returns the Jacobi diagonal.  Volumes (nz > 1) add the two
+// neighbours along z.
 template <typename F>
-__device__ __forceinline__ float apply_op(const Stencil &S, int i, int j, int64_t p, F val, float &diag)
+__device__ __forceinline__ float apply_op(const Stencil &S, int64_t p, F val, float &diag)
 {
+    const int64_t plane = (int64_t)S.n * S.n;
+    const int k = (int)(p / plane), i = (int)((p % plane) / S.n), j = (int)(p % S.n);
     const float c = val(p);
     float acc = 0.f, wsum = 0.f;
-    const int64_t N = (int64_t)S.n * S.n;
+    const int64_t N = plane * S.nz;
     // neighbours inside the image only (out-of-image links are omitted, Eq. (14))
     auto nb = [&](int64_t q) { return DECT_IDX_OK(q, N, CHK_PLS_STENCIL) ? q : p; };
+    if (k > 0) { const int64_t q = nb(p - plane); float w = S.w(p, q); acc += w * (c - val(q)); wsum += w; }
+    if (k + 1 < S.nz) { const int64_t q = nb(p + plane); float w = S.w(p, q); acc += w * (c - val(q)); wsum += w; }
     if (i > 0) { const int64_t q = nb(p - S.n); float w = S.w(p, q); acc += w * (c - val(q)); wsum += w; }
     if (i + 1 < S.n) { const int64_t q = nb(p + S.n); float w = S.w(p, q); acc += w * (c - val(q)); wsum += w; }
     if (j > 0) { const int64_t q = nb(p - 1); float w = S.w(p, q); acc += w * (c - val(q)); wsum += w; }
@@ -201,13 +227,12 @@ __global__ void k_init(float *__restrict__ uall, const unsigned char *__restrict
 {
     const int v = blockIdx.y;
     const float *u = uall + (int64_t)v * C.N;
-    Stencil S{mask + (int64_t)(v >> 1) * C.N, C.n, C.gamma, C.eps};
+    Stencil S{mask + (int64_t)(v >> 1) * C.N, C.n, C.nz, C.gamma, C.eps};
     float acc[3] = {0.f, 0.f, 0.f};
     for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < C.N;
          q += (int64_t)gridDim.x * blockDim.x) {
-        const int i = (int)(q / C.n), j = (int)(q % C.n);
         float diag;
-        const float Ad = apply_op(S, i, j, q, [&](int64_t k) { return u[k]; }, diag);
+        const float Ad = apply_op(S, q, [&](int64_t k) { return u[k]; }, diag);
         const float d = u[q];
         const float rr = d - Ad, zz = rr / diag;
         const int64_t o = (int64_t)v * C.N + q;
@@ -246,14 +271,13 @@ __global__ void k_cg_a(const float *__restrict__ z, const float *__restrict__ p_
     const int v = blockIdx.y;
     const float beta = (float)D.beta[v];
     const float *zv = z + (int64_t)v * C.N, *pv = p_old + (int64_t)v * C.N;
-    Stencil S{mask + (int64_t)(v >> 1) * C.N, C.n, C.gamma, C.eps};
+    Stencil S{mask + (int64_t)(v >> 1) * C.N, C.n, C.nz, C.gamma, C.eps};
     float acc[1] = {0.f};
     for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < C.N;
          q += (int64_t)gridDim.x * blockDim.x) {
-        const int i = (int)(q / C.n), j = (int)(q % C.n);
         float diag;
         auto pn = [&](int64_t k) { return fmaf(beta, pv[k], zv[k]); };
-        const float a = apply_op(S, i, j, q, pn, diag);
+        const float a = apply_op(S, q, pn, diag);
         const float pc = pn(q);
         p_new[(int64_t)v * C.N + q] = pc;
         Ap[(int64_t)v * C.N + q] = a;
@@ -275,13 +299,16 @@ __global__ void k_cg_b(float *__restrict__ uall, const float *__restrict__ p,
     const int v = blockIdx.y;
     const float alpha = (float)D.alpha[v];
     float *u = uall + (int64_t)v * C.N;
-    Stencil S{mask + (int64_t)(v >> 1) * C.N, C.n, C.gamma, C.eps};
+    Stencil S{mask + (int64_t)(v >> 1) * C.N, C.n, C.nz, C.gamma, C.eps};
     float acc[2] = {0.f, 0.f};
     for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < C.N;
          q += (int64_t)gridDim.x * blockDim.x) {
-        const int i = (int)(q / C.n), j = (int)(q % C.n);
+        const int64_t plane = (int64_t)C.n * C.n;
+        const int k = (int)(q / plane), i = (int)((q % plane) / C.n), j = (int)(q % C.n);
         const int64_t o = (int64_t)v * C.N + q;
         float wsum = 0.f;
+        if (k > 0) wsum += S.w(q, q - plane);
+        if (k + 1 < C.nz) wsum += S.w(q, q + plane);
         if (i > 0) wsum += S.w(q, q - C.n);
         if (i + 1 < C.n) wsum += S.w(q, q + C.n);
         if (j > 0) wsum += S.w(q, q - 1);
@@ -324,14 +351,18 @@ __global__ void k_cg_b(float *__restrict__ uall, const float *__restrict__ p,
 
 using namespace dect;
 
-extern "C" dect_status dect_pls_decompose(const float *x, int n, int batch, const dect_pls_params *prm,
-                                          float *u, dect_pls_report *reports, dect_stream stream)
+namespace dect {
+namespace {
+
+// The decomposition of `batch` images (nz = 1) or volumes (nz slices).
+dect_status pls_run(const float *x, int n, int nz, int batch, const dect_pls_params *prm, float *u,
+                    dect_pls_report *reports, dect_stream stream)
 {
-    if (!prm || n < 1 || batch < 0 || n > 16384) return DECT_ERR_INVALID_ARG;
+    if (!prm || n < 1 || batch < 0 || n > 16384 || nz < 1 || nz > 4096) return DECT_ERR_INVALID_ARG;
     if (batch == 0) return DECT_OK;
     if (!x || !u) return DECT_ERR_INVALID_ARG;
     {
-        const size_t span = (size_t)batch * 2 * n * n * sizeof(float);
+        const size_t span = (size_t)batch * 2 * n * n * nz * sizeof(float);
         const char *xa = (const char *)x, *ua = (const char *)u;
         if (xa < ua + span && ua < xa + span) return DECT_ERR_INVALID_ARG;
     }
@@ -345,7 +376,7 @@ extern "C" dect_status dect_pls_decompose(const float *x, int n, int batch, cons
     int dev = 0;
     DECT_CUDA(cudaGetDevice(&dev));
 
-    const int64_t N = (int64_t)n * n;
+    const int64_t N = (int64_t)n * n * nz;
     const int nvec = 2 * batch;
     const int64_t want = (N + kBlock - 1) / kBlock;
     const int gx = (int)std::max<int64_t>(1, std::min<int64_t>(want, std::max(1, (kSMs * 8) / nvec)));
@@ -391,6 +422,7 @@ extern "C" dect_status dect_pls_decompose(const float *x, int n, int batch, cons
 
     PlsConst C;
     C.n = n;
+    C.nz = nz;
     C.N = N;
     C.nvec = nvec;
     C.gamma = (float)prm->gamma;
@@ -398,7 +430,7 @@ extern "C" dect_status dect_pls_decompose(const float *x, int n, int batch, cons
     C.tol = prm->tol;
 
     dim3 gs((unsigned)gx, (unsigned)batch), gv((unsigned)gx, (unsigned)nvec);
-    k_prep<<<gs, kBlock, 0, s>>>(x, n, N, a, b, c, e, u, mh, ml, D.maxbits);
+    k_prep<<<gs, kBlock, 0, s>>>(x, n, nz, N, a, b, c, e, u, mh, ml, D.maxbits);
     DECT_LAUNCH_CHECK();
     k_mask<<<gs, kBlock, 0, s>>>(mh, ml, N, D.maxbits, (float)prm->edge_tau, mask);
     DECT_LAUNCH_CHECK();
@@ -490,14 +522,33 @@ extern "C" dect_status dect_pls_decompose(const float *x, int n, int batch, cons
     return DECT_OK;
 }
 
-extern "C" dect_status dect_pls_edge_mask(const float *x, int n, int batch, double edge_tau,
-                                          uint8_t *mask, dect_stream stream)
+}  // namespace
+}  // namespace dect
+
+extern "C" dect_status dect_pls_decompose(const float *x, int n, int batch, const dect_pls_params *prm,
+                                          float *u, dect_pls_report *reports, dect_stream stream)
 {
-    if (n < 1 || batch < 0 || n > 16384 || !std::isfinite(edge_tau)) return DECT_ERR_INVALID_ARG;
+    return dect::pls_run(x, n, 1, batch, prm, u, reports, stream);
+}
+
+extern "C" dect_status dect_pls_decompose_cone(const float *x, int n, int nz, int batch, const dect_pls_params *prm,
+                                               float *u, dect_pls_report *reports, dect_stream stream)
+{
+    return dect::pls_run(x, n, nz, batch, prm, u, reports, stream);
+}
+
+namespace dect {
+namespace {
+
+dect_status edge_mask_run(const float *x, int n, int nz, int batch, double edge_tau, uint8_t *mask,
+                          dect_stream stream)
+{
+    if (n < 1 || batch < 0 || n > 16384 || nz < 1 || nz > 4096 || !std::isfinite(edge_tau))
+        return DECT_ERR_INVALID_ARG;
     if (batch == 0) return DECT_OK;
     if (!x || !mask || batch > 65535) return DECT_ERR_INVALID_ARG;
     cudaStream_t s = (cudaStream_t)stream;
-    const int64_t N = (int64_t)n * n;
+    const int64_t N = (int64_t)n * n * nz;
     const int64_t want = (N + kBlock - 1) / kBlock;
     const int gx = (int)std::max<int64_t>(1, std::min<int64_t>(want, std::max(1, (kSMs * 8) / batch)));
     const size_t mag_bytes = ((size_t)batch * N * 4 + 255) & ~(size_t)255;
@@ -508,7 +559,7 @@ extern "C" dect_status dect_pls_edge_mask(const float *x, int n, int batch, doub
     cudaError_t err = cudaMemsetAsync(maxbits, 0, (size_t)2 * batch * 4, s);
     if (err == cudaSuccess) {
         dim3 gs((unsigned)gx, (unsigned)batch);
-        k_prep<<<gs, kBlock, 0, s>>>(x, n, N, 1.0, 0.0, 0.0, 1.0, nullptr, mh, ml, maxbits);
+        k_prep<<<gs, kBlock, 0, s>>>(x, n, nz, N, 1.0, 0.0, 0.0, 1.0, nullptr, mh, ml, maxbits);
         k_mask<<<gs, kBlock, 0, s>>>(mh, ml, N, maxbits, (float)edge_tau, mask);
         count_launches(2);
         err = cudaGetLastError();
@@ -519,6 +570,21 @@ extern "C" dect_status dect_pls_edge_mask(const float *x, int n, int batch, doub
         return DECT_ERR_CUDA;
     }
     return DECT_OK;
+}
+
+}  // namespace
+}  // namespace dect
+
+extern "C" dect_status dect_pls_edge_mask(const float *x, int n, int batch, double edge_tau, uint8_t *mask,
+                                          dect_stream stream)
+{
+    return dect::edge_mask_run(x, n, 1, batch, edge_tau, mask, stream);
+}
+
+extern "C" dect_status dect_pls_edge_mask_cone(const float *x, int n, int nz, int batch, double edge_tau,
+                                               uint8_t *mask, dect_stream stream)
+{
+    return dect::edge_mask_run(x, n, nz, batch, edge_tau, mask, stream);
 }
 
 // ---------------------------------------------------------------------------
@@ -636,6 +702,7 @@ extern "C" dect_status dect_pls_decompose_noalloc(const float *x, int n, int bat
 
     PlsConst C;
     C.n = n;
+    C.nz = 1;
     C.N = N;
     C.nvec = nvec;
     C.gamma = (float)prm->gamma;
@@ -643,7 +710,7 @@ extern "C" dect_status dect_pls_decompose_noalloc(const float *x, int n, int bat
     C.tol = prm->tol;
 
     dim3 gs((unsigned)gx, (unsigned)batch), gv((unsigned)gx, (unsigned)nvec);
-    k_prep<<<gs, kBlock, 0, s>>>(x, n, N, a, b, c, e, u, mh, ml, D.maxbits);
+    k_prep<<<gs, kBlock, 0, s>>>(x, n, 1, N, a, b, c, e, u, mh, ml, D.maxbits);
     DECT_LAUNCH_CHECK();
     k_mask<<<gs, kBlock, 0, s>>>(mh, ml, N, D.maxbits, (float)prm->edge_tau, mask);
     DECT_LAUNCH_CHECK();

@@ -47,25 +47,27 @@ __global__ void k_from_il(const float *__restrict__ src, float *__restrict__ dst
 // images (row_dot_w), 4 below (row_dot_g).
 template <int NB, bool TILED>
 __global__ void __launch_bounds__(kOpBlock) k_rows_il(const int64_t *__restrict__ ptr, const Entry *__restrict__ ent,
-                                                      int64_t rows, int n, const float *__restrict__ src,
+                                                      int64_t rows, int n, int nz, const float *__restrict__ src,
                                                       int64_t src_rows, float *__restrict__ dst)
 {
     constexpr int G = 32, VW = Batch<NB>::VW, LPE = Batch<NB>::CPB;
     const int lr = threadIdx.x % G, grp = lr / LPE, vl = lr % LPE;
     const int64_t rpb = kOpBlock / G;
     const int tiles_x = (n + kTile - 1) / kTile;
-    const int64_t vrows = TILED ? (int64_t)tiles_x * tiles_x * kTile * kTile : rows;
+    const int64_t per_slice = (int64_t)tiles_x * tiles_x * kTile * kTile;
+    const int64_t vrows = TILED ? per_slice * nz : rows;
     const unsigned long long pol = l2_evict_last_policy();
     for (int64_t v0 = (int64_t)blockIdx.x * rpb; v0 < vrows; v0 += (int64_t)gridDim.x * rpb) {
         const int64_t v = v0 + threadIdx.x / G;
         int64_t row = v;
         bool ok = v < vrows;
-        if (TILED && ok) {
-            const int64_t tile = v / (kTile * kTile);
-            const int w = (int)(v % (kTile * kTile));
+        if (TILED && ok) {  // slice k, tile of the slice, pixel of the tile
+            const int64_t k = v / per_slice, vs = v % per_slice;
+            const int64_t tile = vs / (kTile * kTile);
+            const int w = (int)(vs % (kTile * kTile));
             const int i = (int)(tile / tiles_x) * kTile + w / kTile, j = (int)(tile % tiles_x) * kTile + w % kTile;
             ok = i < n && j < n;
-            row = (int64_t)i * n + j;
+            row = (k * n + i) * n + j;
         }
         int64_t b = 0, e = 0;
         if (ok) {
@@ -82,16 +84,16 @@ __global__ void __launch_bounds__(kOpBlock) k_rows_il(const int64_t *__restrict_
 }
 
 template <int NB>
-cudaError_t pass(const int64_t *ptr, const Entry *ent, int64_t rows_in, int64_t rows_out, int n, bool tiled,
+cudaError_t pass(const int64_t *ptr, const Entry *ent, int64_t rows_in, int64_t rows_out, int n, int nz, bool tiled,
                  const float *src, float *dst, int nimg, float *buf, cudaStream_t s)
 {
     float *in_il = buf, *out_il = buf + rows_in * NB;
     const unsigned bi = (unsigned)((rows_in * NB + 255) / 256), bo = (unsigned)((rows_out * NB + 255) / 256);
     k_to_il<NB><<<bi, 256, 0, s>>>(src, in_il, rows_in, nimg);
     if (tiled)
-        k_rows_il<NB, true><<<kSMs, kOpBlock, 0, s>>>(ptr, ent, rows_out, n, in_il, rows_in, out_il);
+        k_rows_il<NB, true><<<kSMs, kOpBlock, 0, s>>>(ptr, ent, rows_out, n, nz, in_il, rows_in, out_il);
     else
-        k_rows_il<NB, false><<<kSMs, kOpBlock, 0, s>>>(ptr, ent, rows_out, n, in_il, rows_in, out_il);
+        k_rows_il<NB, false><<<kSMs, kOpBlock, 0, s>>>(ptr, ent, rows_out, n, nz, in_il, rows_in, out_il);
     k_from_il<NB><<<bo, 256, 0, s>>>(out_il, dst, rows_out, nimg);
     count_launches(3);
     return cudaGetLastError();
@@ -99,7 +101,7 @@ cudaError_t pass(const int64_t *ptr, const Entry *ent, int64_t rows_in, int64_t 
 
 // Passes of up to 64 images over the table (ptr, ent) mapping src rows
 // (rows_in per image) to dst rows (rows_out per image).
-cudaError_t run_batched(const int64_t *ptr, const Entry *ent, int64_t rows_in, int64_t rows_out, int n,
+cudaError_t run_batched(const int64_t *ptr, const Entry *ent, int64_t rows_in, int64_t rows_out, int n, int nz,
                         bool tiled, const float *src, float *dst, int batch, cudaStream_t s)
 {
     int width0 = 2;  // widest pass: the next power of two >= min(batch, 64), at least 2
@@ -111,12 +113,12 @@ cudaError_t run_batched(const int64_t *ptr, const Entry *ent, int64_t rows_in, i
         const int k = std::min(kMaxBatchImages, batch - done);
         const float *sp = src + (int64_t)done * rows_in;
         float *dp = dst + (int64_t)done * rows_out;
-        if (k <= 2) e = pass<2>(ptr, ent, rows_in, rows_out, n, tiled, sp, dp, k, buf, s);
-        else if (k <= 4) e = pass<4>(ptr, ent, rows_in, rows_out, n, tiled, sp, dp, k, buf, s);
-        else if (k <= 8) e = pass<8>(ptr, ent, rows_in, rows_out, n, tiled, sp, dp, k, buf, s);
-        else if (k <= 16) e = pass<16>(ptr, ent, rows_in, rows_out, n, tiled, sp, dp, k, buf, s);
-        else if (k <= 32) e = pass<32>(ptr, ent, rows_in, rows_out, n, tiled, sp, dp, k, buf, s);
-        else e = pass<64>(ptr, ent, rows_in, rows_out, n, tiled, sp, dp, k, buf, s);
+        if (k <= 2) e = pass<2>(ptr, ent, rows_in, rows_out, n, nz, tiled, sp, dp, k, buf, s);
+        else if (k <= 4) e = pass<4>(ptr, ent, rows_in, rows_out, n, nz, tiled, sp, dp, k, buf, s);
+        else if (k <= 8) e = pass<8>(ptr, ent, rows_in, rows_out, n, nz, tiled, sp, dp, k, buf, s);
+        else if (k <= 16) e = pass<16>(ptr, ent, rows_in, rows_out, n, nz, tiled, sp, dp, k, buf, s);
+        else if (k <= 32) e = pass<32>(ptr, ent, rows_in, rows_out, n, nz, tiled, sp, dp, k, buf, s);
+        else e = pass<64>(ptr, ent, rows_in, rows_out, n, nz, tiled, sp, dp, k, buf, s);
         done += k;
     }
     cudaError_t f = cudaFreeAsync(buf, s);
@@ -127,12 +129,12 @@ cudaError_t run_batched(const int64_t *ptr, const Entry *ent, int64_t rows_in, i
 
 cudaError_t launch_project_planar(const dect_plan *p, const float *x, float *y, int batch, cudaStream_t s)
 {
-    return run_batched(p->rowptr, p->ent, p->N, p->M, p->n, false, x, y, batch, s);
+    return run_batched(p->rowptr, p->ent, p->N, p->M, p->n, std::max(p->nz, 1), false, x, y, batch, s);
 }
 
 cudaError_t launch_backproject_planar(const dect_plan *p, const float *y, float *x, int batch, cudaStream_t s)
 {
-    return run_batched(p->colptr, p->tent, p->M, p->N, p->n, true, y, x, batch, s);
+    return run_batched(p->colptr, p->tent, p->M, p->N, p->n, std::max(p->nz, 1), true, y, x, batch, s);
 }
 
 }  // namespace dect

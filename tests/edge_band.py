@@ -53,3 +53,33 @@ def band(x: np.ndarray, tau: float) -> np.ndarray:
 def mask_band(xh: np.ndarray, xl: np.ndarray, tau: float) -> np.ndarray:
     """Pixels whose edge/non-edge decision from either image is within rounding of tau."""
     return band(xh, tau) | band(xl, tau)
+
+
+def _abs_terms3(x: np.ndarray) -> np.ndarray:
+    """3-D counterpart of _abs_terms: x [nz][n][n], nine differences per component."""
+    nz, n = x.shape[0], x.shape[1]
+    ci = lambda a: np.clip(a, 0, n - 1)  # noqa: E731
+    ck = lambda a: np.clip(a, 0, nz - 1)  # noqa: E731
+    ii, kk = np.arange(n), np.arange(nz)
+    sx = np.zeros_like(x)
+    sy = np.zeros_like(x)
+    sz = np.zeros_like(x)
+    for a in (-1, 0, 1):
+        for b in (-1, 0, 1):
+            sx += np.abs(x[ck(kk + a)][:, ci(ii + b)][:, :, ci(ii + 1)] - x[ck(kk + a)][:, ci(ii + b)][:, :, ci(ii - 1)])
+            sy += np.abs(x[ck(kk + a)][:, ci(ii + 1)][:, :, ci(ii + b)] - x[ck(kk + a)][:, ci(ii - 1)][:, :, ci(ii + b)])
+            sz += np.abs(x[ck(kk + 1)][:, ci(ii + a)][:, :, ci(ii + b)] - x[ck(kk - 1)][:, ci(ii + a)][:, :, ci(ii + b)])
+    return np.sqrt(sx * sx + sy * sy + sz * sz)
+
+
+def band3(x: np.ndarray, tau: float) -> np.ndarray:
+    """band() for volumes [nz][n][n] and the 3-D Prewitt of nine terms per component."""
+    x = np.asarray(x, np.float64)
+    m = oracle.prewitt3(x)
+    big = m.max()
+    if big == 0.0:
+        return np.zeros(x.shape, bool)
+    err = 10 * U32 * _abs_terms3(x) + 4 * U32 * m
+    r = m / big
+    width = 2 * ((err + r * err.max()) / big + 2 * U32 * r)
+    return np.abs(r - tau) <= width
