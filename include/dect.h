@@ -537,6 +537,36 @@ dect_status dect_cnn_adam_step(dect_cnn *net, float lr, float beta1, float beta2
                                dect_stream stream);
 
 /*
+ * Kernel of the 3x3 convolutions (forward and input gradient).
+ * DECT_CNN_CONV_TCGEN05 (the default): a persistent implicit GEMM on the
+ * 5th-generation tensor cores, accumulating in tensor memory; TMA copies the
+ * weights once per block and, per 32 input channels, three column-shifted
+ * halo patches of each 8 x 16 pixel tile.  DECT_CNN_CONV_MMA_SYNC: the
+ * warp-level mma.sync implicit GEMM, kept for comparison.  Both compute the
+ * same sums (BF16 products, FP32 accumulation) in different orders.
+ * Returns DECT_ERR_INVALID_ARG for any other value.
+ */
+#define DECT_CNN_CONV_TCGEN05 0
+#define DECT_CNN_CONV_MMA_SYNC 1
+dect_status dect_cnn_set_conv_path(dect_cnn *net, int path);
+int dect_cnn_get_conv_path(const dect_cnn *net); /* -1 for a NULL net */
+/* Resident blocks per SM of the tensor-memory convolution: 2 (the default;
+ * each block keeps the deepest operand ring that fits in half the SM's
+ * shared memory, where that is at least two stages, else one block) or 1
+ * (one block per SM with the deepest ring).  Any other value:
+ * DECT_ERR_INVALID_ARG.  Changes speed only, not results. */
+dect_status dect_cnn_set_conv_tuning(dect_cnn *net, int blocks_per_sm);
+
+/*
+ * Synchronises the device and reads the network's error word.  Returns
+ * DECT_ERR_TIMEOUT (and clears the word) when a bounded wait inside a
+ * tensor-memory convolution ran out since the last check: the outputs of
+ * the calls since then are not valid.  dect_cnn_loss_grad runs this check
+ * itself before it returns; after dect_cnn_forward the caller runs it.
+ */
+dect_status dect_cnn_check(dect_cnn *net);
+
+/*
  * Checked build.  libdect_checked.so is the same library compiled with
  * index checks (DECT_CHECKED): before each table-driven gather, stencil
  * neighbour, on-the-fly ray or pixel and FBP bin access, the index is

@@ -114,6 +114,10 @@ _SIGS = {
     "dect_cnn_loss_grad": (C.c_int, [_P, _P, _P, C.c_int, C.c_int, C.c_int, C.c_float,
                                      C.POINTER(C.c_float), _P, _P]),
     "dect_cnn_adam_step": (C.c_int, [_P, C.c_float, C.c_float, C.c_float, C.c_float, _P]),
+    "dect_cnn_set_conv_path": (C.c_int, [_P, C.c_int]),
+    "dect_cnn_get_conv_path": (C.c_int, [_P]),
+    "dect_cnn_check": (C.c_int, [_P]),
+    "dect_cnn_set_conv_tuning": (C.c_int, [_P, C.c_int]),
     "dect_selftest_bounded_wait": (C.c_int, [C.c_uint, _P]),
     "dect_selftest_index": (C.c_int, [C.c_int, _P]),
     "dect_check_status": (C.c_int, []),
@@ -710,8 +714,29 @@ class Cnn:
         _check(load().dect_cnn_get_params(self._h, p.ctypes.data), "dect_cnn_get_params")
         return p
 
-    def forward(self, x, scale: float, out=None, stream=None):
-        """x: [B, H, W] float32 CUDA (H, W multiples of 4)."""
+    # kernels of the 3x3 convolutions (dect_cnn_set_conv_path)
+    CONV_TCGEN05 = 0
+    CONV_MMA_SYNC = 1
+
+    @property
+    def conv_path(self) -> int:
+        return int(load().dect_cnn_get_conv_path(self._h))
+
+    @conv_path.setter
+    def conv_path(self, path: int):
+        _check(load().dect_cnn_set_conv_path(self._h, int(path)), "dect_cnn_set_conv_path")
+
+    def set_conv_tuning(self, blocks_per_sm: int):
+        """Resident blocks per SM of the tensor-memory convolution (1 or 2)."""
+        _check(load().dect_cnn_set_conv_tuning(self._h, int(blocks_per_sm)), "dect_cnn_set_conv_tuning")
+
+    def check(self):
+        """Synchronise and raise if a bounded device wait ran out (dect_cnn_check)."""
+        _check(load().dect_cnn_check(self._h), "dect_cnn_check")
+
+    def forward(self, x, scale: float, out=None, stream=None, check: bool = True):
+        """x: [B, H, W] float32 CUDA (H, W multiples of 4).  With check (the
+        default) the call synchronises and raises if a device wait ran out."""
         import torch
         B, H, W = x.shape
         if out is None:
@@ -719,6 +744,8 @@ class Cnn:
         _check(load().dect_cnn_forward(self._h, _ptr(x, torch.float32, self.device),
                                        _ptr(out, torch.float32, self.device), B, H, W, scale,
                                        _stream(stream)), "dect_cnn_forward")
+        if check:
+            self.check()
         return out
 
     def loss_grad(self, x, target, scale: float, want_grad: bool = False, stream=None):

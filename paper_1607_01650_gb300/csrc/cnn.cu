@@ -18,15 +18,20 @@
 // implicit GEMM reduced in a fixed order.  Master weights, gradients and the
 // Adam state are FP32.  Parameter vector layout (shared with the host):
 // per layer W[Cout][Cin][3][3] then b[Cout]; then the head Wh[32], bh.
+#include <cuda.h>  // CUtensorMap and its enums (the encoder is fetched from the driver at run time)
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
+
+#include <cudaTypedefs.h>  // PFN_cuTensorMapEncodeTiled_v12000
 
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <mutex>
 #include <vector>
 
 #include "dect_internal.cuh"
+#include "kernels.cuh"
 
 typedef __nv_bfloat16 bf16;
 
@@ -49,11 +54,9 @@ int64_t num_params()
 // ---------------------------------------------------------------------------
 // PTX helpers
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ unsigned su32(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
-
 __device__ __forceinline__ void cp16_zfill(void *smem, const void *gmem, bool valid)
 {
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(su32(smem)), "l"(gmem),
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(smem_u32(smem)), "l"(gmem),
                  "r"(valid ? 16 : 0)
                  : "memory");
 }
@@ -65,13 +68,13 @@ __device__ __forceinline__ void ldsm_x4(unsigned (&r)[4], const void *p)
 {
     asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
                  : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
-                 : "r"(su32(p)));
+                 : "r"(smem_u32(p)));
 }
 __device__ __forceinline__ void ldsm_x4_t(unsigned (&r)[4], const void *p)
 {
     asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];\n"
                  : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
-                 : "r"(su32(p)));
+                 : "r"(smem_u32(p)));
 }
 
 __device__ __forceinline__ void mma_bf16(float (&d)[4], const unsigned (&a)[4], unsigned b0, unsigned b1)
@@ -243,6 +246,408 @@ __global__ void __launch_bounds__(128) k_conv(ConvArgs a)
                 }
                 *reinterpret_cast<__nv_bfloat162 *>(a.Y + (int64_t)p * a.ldy + co) = __floats2bfloat162_rn(v0, v1);
             }
+}
+
+// ---------------------------------------------------------------------------
+// 3x3 convolution on the 5th-generation tensor cores (tcgen05), the same
+// implicit GEMM as k_conv.  Persistent and warp-specialised: one block per
+// SM (two where shared memory allows) walks output tiles of 128 pixels (an
+// 8 x 16 patch of one image) x BN output channels.
+//   * The block's BN x 9 x Cin weights are loaded once by TMA and stay in
+//     shared memory when they fit (STREAM = false); otherwise each stage of
+//     the ring carries its chunk's BN x 9 x 32 weights with the pixels
+//     (STREAM = true), so that BN can be the whole layer: a tcgen05.mma of
+//     M = 128 costs about as much at N = 32 or 64 as at N = 128.
+//   * For each chunk of 32 input channels the tensor-memory accelerator (TMA)
+//     copies three column-shifted halo patches (10 x 16 pixels at x offsets
+//     -1, 0, +1, rows -1 .. +8, zero-filled outside the image).  The A
+//     operand of tap (dy, dx) is then the shifted copy dx started dy + 1
+//     rows in: 8 contiguous rows of 16 pixels, so each of the 9 taps is two
+//     tcgen05.mma (K = 16 each) with no data movement of its own.
+//   * The FP32 accumulator lives in tensor memory (TMEM, lane = pixel,
+//     column = channel), double-buffered so that the epilogue of one tile
+//     overlaps the MMAs of the next.
+// Warp 0 issues the TMA copies, warp 1 the MMAs, warps 2-5 run the
+// epilogue (tcgen05.ld of 16 columns, bias, ReLU, mask, BF16 store); warp
+// w reads TMEM lanes 32 (w % 4) .. + 31.  mbarriers hand over the stages:
+// a_full (TMA -> MMA), a_empty (MMA done reading -> TMA), acc_full (last
+// MMA of a tile -> epilogue), acc_empty (epilogue -> MMA).  Operands are
+// K-major with 64-byte rows in the 64-byte swizzle.  Every wait is bounded:
+// a role whose wait runs out raises a shared flag that ends the others'
+// loops; the block then records the timeout in *err, lets its copies and
+// MMAs in flight complete (bounded waits), frees its TMEM and returns.
+// Requires Cin % 32 == 0 and Cout % BN == 0.
+// ---------------------------------------------------------------------------
+constexpr int kTcTH = 8, kTcTW = 16;                    // output pixels per tile: 8 rows x 16
+constexpr int kTcBK = 32;                               // input channels per chunk (64-byte rows)
+constexpr int kTcRowBytes = kTcTW * kTcBK * 2;          // one image row of a copy: 1 KB
+constexpr int kTcCopy = (kTcTH + 2) * kTcRowBytes;      // one shifted halo copy: 10 KB
+constexpr int kTcAStage = 3 * kTcCopy;                  // the three copies of a chunk
+constexpr int kTcMaxStages = 8;                        // depth of the A ring: as deep as shared memory allows
+constexpr int kTcThreads = 320;                         // producer, MMA issuer, 8 epilogue warps
+constexpr int kTcSmemMax = 227 * 1024;                  // opt-in shared memory per block
+constexpr int kTcWeightMax = 108 * 1024;                // leaves room for at least 3 A stages
+constexpr unsigned kTcPolls = 1u << 22;
+
+// shared memory of k_conv_tc: resident weights, ring, barriers, bias
+__host__ __device__ constexpr int tc_weight_bytes(int Cin, int BN) { return (Cin / kTcBK) * 9 * BN * kTcBK * 2; }
+__host__ __device__ constexpr int tc_wslice_bytes(int BN) { return 9 * BN * kTcBK * 2; }  // one chunk's weights
+__host__ __device__ constexpr int tc_stage_bytes(int BN, bool stream, bool dxn)
+{
+    return (dxn ? kTcCopy : kTcAStage) + (stream ? tc_wslice_bytes(BN) : 0);
+}
+// tensor-memory columns of a block: two accumulators of BN (or 3 BN) columns,
+// rounded up to a power of two
+__host__ __device__ constexpr unsigned tc_tmem_cols(int BN, bool dxn)
+{
+    return (dxn ? 6 : 2) * BN <= 64 ? 64u : (dxn ? 6 : 2) * BN <= 128 ? 128u : (dxn ? 6 : 2) * BN <= 256 ? 256u : 512u;
+}
+__host__ __device__ constexpr int tc_fixed_bytes(int Cin, int BN, bool stream)
+{
+    return 1024 /* alignment slack */ + (stream ? 0 : tc_weight_bytes(Cin, BN)) + 32 * 8 /* barriers */ +
+           BN * 4 /* bias */;
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(smem_u32(bar)) : "memory");
+}
+
+// wait for phase `parity`, giving up after kTcPolls polls or once *fail is set
+__device__ __forceinline__ bool tc_wait(uint64_t *bar, unsigned parity, volatile int *fail)
+{
+    for (unsigned i = 0; i < kTcPolls; ++i) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if ((i & 255u) == 255u && *fail) return false;
+    }
+    return false;
+}
+
+__device__ __forceinline__ void tma_load_4d(void *dst, const CUtensorMap *map, int c0, int c1, int c2, int c3,
+                                            uint64_t *bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, "
+        "%5}], [%6];\n" ::"r"(smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(smem_u32(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *map, int c0, int c1, int c2, uint64_t *bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
+        "[%5];\n" ::"r"(smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(smem_u32(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, int c0, int c1, uint64_t *bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], "
+        "[%4];\n" ::"r"(smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(smem_u32(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ void tc_alloc(uint32_t *slot, uint32_t ncols)
+{
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(slot)),
+                 "r"(ncols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
+}
+__device__ __forceinline__ void tc_dealloc(uint32_t taddr, uint32_t ncols)
+{
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(taddr), "r"(ncols) : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory"); }
+
+// D (TMEM) (+)= A (smem) x B (smem)^T with K = 16; accumulate = 0 overwrites D.
+__device__ __forceinline__ void tc_mma(uint32_t taddr, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                       uint32_t accumulate)
+{
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(taddr),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
+// arrive on `bar` once every tcgen05 operation this thread issued has completed
+__device__ __forceinline__ void tc_commit(uint64_t *bar)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
+                     smem_u32(bar))
+                 : "memory");
+}
+
+// 16 consecutive FP32 columns of this thread's TMEM lane (no wait)
+__device__ __forceinline__ void tc_ld16_nowait(uint32_t taddr, uint32_t (&r)[16])
+{
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+        "%15}, [%16];\n"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+}
+__device__ __forceinline__ void tc_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory"); }
+
+// Shared-memory matrix descriptor of a K-major operand with 64-byte rows in
+// the 64-byte swizzle (the layout TMA writes with CU_TENSOR_MAP_SWIZZLE_64B):
+// start address >> 4 (bits 0-13), leading offset 16 B (unused by this
+// layout, bits 16-29), 512 B between 8-row groups (bits 32-45), descriptor
+// version 1 (bit 46), base offset 0, swizzle mode 4 = 64 B (bits 61-63).
+// The tile must start on a 512-byte boundary; +2 in the low word moves the
+// start 32 bytes along K (the second K = 16 step of a 64-byte row).
+__device__ __forceinline__ uint64_t sw64_desc(const void *tile)
+{
+    const uint32_t a = smem_u32(tile);
+    return (uint64_t)((a >> 4) & 0x3FFFu) | ((uint64_t)1 << 16) | ((uint64_t)(512 >> 4) << 32) |
+           ((uint64_t)1 << 46) | ((uint64_t)4 << 61);
+}
+
+// Instruction descriptor of kind::f16: D FP32 (bits 4-5 = 1), A and B BF16
+// (bits 7-9 = 1, 10-12 = 1), both K-major (bits 15, 16 = 0), N >> 3 (bits
+// 17-22), M >> 4 (bits 24-28).
+__host__ __device__ constexpr uint32_t tc_idesc(int m, int n)
+{
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(m >> 4) << 24);
+}
+
+template <int BN, bool STREAM, bool DXN>
+__global__ void __launch_bounds__(kTcThreads, 1)
+    k_conv_tc(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmW, ConvArgs a,
+              int tiles_x, int tiles_y, int nstage, int w3d, unsigned *err)
+{
+    static_assert(BN % 32 == 0 && BN >= 32 && BN <= 128, "output channels per block: 32 .. 128, a multiple of 32");
+    static_assert(!DXN || BN <= 64, "with the taps folded into N, N = 3 BN <= 192");
+    constexpr int AW = DXN ? 3 * BN : BN;  // accumulator columns of one tile
+    constexpr uint32_t TM_COLS = tc_tmem_cols(BN, DXN);  // two accumulators
+    constexpr uint32_t idesc = tc_idesc(kTcTH * kTcTW, AW);
+    constexpr int OW = DXN ? kTcTW - 2 : kTcTW;  // output columns per tile
+    extern __shared__ unsigned char smraw[];
+    unsigned char *sm =
+        reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smraw) + 1023) & ~(uintptr_t)1023);
+    constexpr int STAGE = tc_stage_bytes(BN, STREAM, DXN);
+    constexpr int ACOPY = DXN ? kTcCopy : kTcAStage;  // the pixel part of a stage
+    const int nck = a.Cin / kTcBK;
+    const int wbytes = STREAM ? 0 : tc_weight_bytes(a.Cin, BN);
+    unsigned char *sW = sm, *sA = sm + wbytes;
+    uint64_t *bars = reinterpret_cast<uint64_t *>(sA + nstage * STAGE);
+    uint64_t *wbar = bars, *a_full = bars + 1, *a_empty = bars + 1 + kTcMaxStages;
+    uint64_t *acc_full = bars + 1 + 2 * kTcMaxStages, *acc_empty = acc_full + 2, *mma_done = acc_empty + 2;
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(mma_done + 1);
+    float *s_bias = reinterpret_cast<float *>(bars + 32);
+    __shared__ volatile int s_fail;
+    __shared__ int s_consumed;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int per_img = tiles_x * tiles_y, ntiles = a.B * per_img;
+    const int n0 = blockIdx.y * BN;
+
+    if (threadIdx.x == 0) {
+        mbar_init(wbar, 1);
+        for (int s = 0; s < nstage; ++s) {
+            mbar_init(a_full + s, 1);
+            mbar_init(a_empty + s, 1);
+        }
+        for (int s = 0; s < 2; ++s) {
+            mbar_init(acc_full + s, 1);
+            mbar_init(acc_empty + s, 8);
+        }
+        mbar_init(mma_done, 1);
+        s_fail = 0;
+        s_consumed = 0;
+    }
+    if (threadIdx.x < BN) s_bias[threadIdx.x] = a.bias ? a.bias[n0 + threadIdx.x] : 0.f;
+    if (warp == 0) tc_alloc(tmem_slot, TM_COLS);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+
+    int issued = 0;  // A chunks issued (producer thread)
+    if (warp == 0) {
+        if (lane == 0) {
+            // resident weights (none when they stream: the barrier's phase
+            // then completes at once)
+            mbar_arrive_expect_tx(wbar, (unsigned)wbytes);
+            if (!STREAM)
+                for (int c = 0; c < nck; ++c)
+                    for (int tap = 0; tap < 9; ++tap)
+                        tma_load_2d(sW + (c * 9 + tap) * BN * kTcBK * 2, &tmW, tap * a.Cin + c * kTcBK, n0, wbar);
+            int n = 0, s = 0, u = 0;  // chunk count, its stage and the stage's use
+            for (int t = blockIdx.x; t < ntiles && !s_fail; t += gridDim.x) {
+                const int b = t / per_img, r = t % per_img;
+                const int y0 = (r / tiles_x) * kTcTH, x0 = (r % tiles_x) * OW - (DXN ? 1 : 0);
+                for (int c = 0; c < nck; ++c, ++n, s = (s + 1 == nstage) ? 0 : s + 1, u += (s == 0)) {
+                    if (u > 0 && !tc_wait(a_empty + s, (u - 1) & 1, &s_fail)) {
+                        s_fail = 1;
+                        break;
+                    }
+                    mbar_arrive_expect_tx(a_full + s, (unsigned)STAGE);
+                    unsigned char *dst = sA + s * STAGE;
+                    if (DXN) {
+                        tma_load_4d(dst, &tmX, c * kTcBK, x0, y0 - 1, b, a_full + s);
+                    } else {
+#pragma unroll
+                        for (int d = 0; d < 3; ++d)
+                            tma_load_4d(dst + d * kTcCopy, &tmX, c * kTcBK, x0 + d - 1, y0 - 1, b, a_full + s);
+                    }
+                    if (STREAM) {
+                        if (w3d) {  // one box {32 channels, BN rows, 9 taps}
+                            tma_load_3d(dst + ACOPY, &tmW, c * kTcBK, n0, 0, a_full + s);
+                        } else {
+#pragma unroll
+                            for (int tap = 0; tap < 9; ++tap)
+                                tma_load_2d(dst + ACOPY + tap * BN * kTcBK * 2, &tmW, tap * a.Cin + c * kTcBK, n0,
+                                            a_full + s);
+                        }
+                    }
+                    issued = n + 1;
+                }
+            }
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            // descriptors of the ring's first stage and of the first weight
+            // slice; every other operand is a constant offset from these
+            const uint64_t a_desc0 = sw64_desc(sA), w_desc0 = sw64_desc(sW);
+            int n = 0, j = 0, s = 0, u = 0;  // chunk count, its stage and the stage's use
+            bool ok = tc_wait(wbar, 0, &s_fail);
+            for (int t = blockIdx.x; ok && t < ntiles; t += gridDim.x, ++j) {
+                const int acc = j & 1, ua = j >> 1;
+                if (ua > 0 && !tc_wait(acc_empty + acc, (ua - 1) & 1, &s_fail)) {
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t d = tmem + (uint32_t)(acc * AW);
+                for (int c = 0; c < nck; ++c, ++n, s = (s + 1 == nstage) ? 0 : s + 1, u += (s == 0)) {
+                    if (!tc_wait(a_full + s, u & 1, &s_fail)) {
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    // (start address >> 4) sits in the low bits and never carries
+                    const uint64_t ad0 = a_desc0 + (uint64_t)((s * STAGE) >> 4);
+                    const uint64_t bd0 = STREAM ? ad0 + (uint64_t)(ACOPY >> 4)
+                                                : w_desc0 + (uint64_t)((c * tc_wslice_bytes(BN)) >> 4);
+                    if (DXN) {
+                        // row shift dy: the copy dy rows in; B = the three taps
+                        // (dy, -1 .. +1), 3 BN consecutive weight rows
+#pragma unroll
+                        for (int dy = 0; dy < 3; ++dy) {
+                            const uint64_t ad = ad0 + (uint64_t)((dy * kTcRowBytes) >> 4);
+                            const uint64_t bd = bd0 + (uint64_t)((dy * 3 * BN * kTcBK * 2) >> 4);
+                            tc_mma(d, ad, bd, idesc, (c | dy) ? 1u : 0u);
+                            tc_mma(d, ad + 2, bd + 2, idesc, 1u);
+                        }
+                    } else {
+#pragma unroll
+                        for (int tap = 0; tap < 9; ++tap) {
+                            const uint64_t ad =
+                                ad0 + (uint64_t)(((tap % 3) * kTcCopy + (tap / 3) * kTcRowBytes) >> 4);
+                            const uint64_t bd = bd0 + (uint64_t)((tap * BN * kTcBK * 2) >> 4);
+                            tc_mma(d, ad, bd, idesc, (c | tap) ? 1u : 0u);
+                            tc_mma(d, ad + 2, bd + 2, idesc, 1u);
+                        }
+                    }
+                    tc_commit(a_empty + s);
+                    s_consumed = n + 1;
+                }
+                if (!ok) break;
+                tc_commit(acc_full + acc);
+            }
+            if (!ok) s_fail = 1;
+            tc_commit(mma_done);
+        }
+    } else {
+        // epilogue warps 2 .. 9: warp w reads TMEM lanes 32 (w % 4) .. + 31 and
+        // takes half (w - 2) / 4 of the block's BN channels
+        const int q = warp & 3;
+        const int m = q * 32 + lane;
+        constexpr int HALF = BN / 2;
+        const int cbeg = ((warp - 2) >> 2) * HALF;
+        int j = 0;
+        for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++j) {
+            const int acc = j & 1, ua = j >> 1;
+            const bool ok = tc_wait(acc_full + acc, ua & 1, &s_fail);
+            if (!__all_sync(0xffffffffu, ok)) {
+                s_fail = 1;
+                break;
+            }
+            tc_fence_after();
+            const int b = t / per_img, r = t % per_img;
+            const int xm = m % kTcTW;
+            const int y = (r / tiles_x) * kTcTH + m / kTcTW, x = (r % tiles_x) * OW - (DXN ? 1 : 0) + xm;
+            // with folded taps the first and last column of the patch are halo
+            const bool in = y < a.H && x < a.W && (!DXN || (xm >= 1 && xm <= kTcTW - 2));
+            const int64_t p = ((int64_t)b * a.H + y) * a.W + x;
+            const uint32_t trow = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * AW);
+#pragma unroll 1
+            for (int c0 = cbeg; c0 < cbeg + HALF; c0 += 16) {
+                float v[16];
+                if (DXN) {
+                    // Y[x] = D[x - 1][tap dx = -1] + D[x][dx = 0] + D[x + 1][dx = +1]:
+                    // the neighbours are lanes m -+ 1 of the same 16-pixel row
+                    uint32_t l[16], c[16], rr[16];
+                    tc_ld16_nowait(trow + (uint32_t)c0, l);
+                    tc_ld16_nowait(trow + (uint32_t)(BN + c0), c);
+                    tc_ld16_nowait(trow + (uint32_t)(2 * BN + c0), rr);
+                    tc_wait_ld();
+#pragma unroll
+                    for (int i = 0; i < 16; ++i)
+                        v[i] = __shfl_up_sync(0xffffffffu, __uint_as_float(l[i]), 1) + __uint_as_float(c[i]) +
+                               __shfl_down_sync(0xffffffffu, __uint_as_float(rr[i]), 1);
+                } else {
+                    uint32_t c[16];
+                    tc_ld16_nowait(trow + (uint32_t)c0, c);
+                    tc_wait_ld();
+#pragma unroll
+                    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(c[i]);
+                }
+                if (!in) continue;
+                const int co = n0 + c0;
+#pragma unroll
+                for (int g = 0; g < 2; ++g) {
+                    B8 mk, o;
+                    if (a.mask) mk = ld8(a.mask + p * a.ldm + co + 8 * g);
+#pragma unroll
+                    for (int i = 0; i < 8; ++i) {
+                        float rv = v[8 * g + i] + s_bias[c0 + 8 * g + i];
+                        if (a.relu) rv = fmaxf(rv, 0.f);
+                        if (a.mask && !(mk.v[i] > 0.f)) rv = 0.f;
+                        o.v[i] = rv;
+                    }
+                    st8(a.Y + p * a.ldy + co + 8 * g, o);
+                }
+            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(acc_empty + acc);
+        }
+    }
+    __syncwarp();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        // the MMAs issued have completed once mma_done fires; copies still in
+        // flight after a failure land before the block's shared memory goes
+        const bool mma_ok = mbar_wait_bounded(mma_done, 0, kTcPolls);
+        if (s_fail || !mma_ok) {
+            atomicOr(err, 1u);
+            mbar_wait_bounded(wbar, 0, kTcPolls);
+            for (int n = s_consumed; n < issued; ++n)
+                mbar_wait_bounded(a_full + n % nstage, (n / nstage) & 1, kTcPolls);
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == 0) tc_dealloc(tmem, TM_COLS);
 }
 
 // ---------------------------------------------------------------------------
@@ -589,18 +994,144 @@ struct dect_cnn {
     float *out, *wpart, *cpart, *hpart;
     size_t wpart_elems;
     int steps;  // Adam step count
+    int conv_path;  // DECT_CNN_CONV_TCGEN05 or DECT_CNN_CONV_MMA_SYNC
+    int conv_blocks_per_sm;  // k_conv_tc: 1 or 2 resident blocks per SM
+    unsigned *err;  // device word: bit 0 = a bounded wait of k_conv_tc ran out
 };
 
 namespace {
 
 bool alloc(void **p, size_t bytes) { return cudaMalloc(p, bytes) == cudaSuccess; }
 
+// cuTensorMapEncodeTiled, fetched from the driver once (no link to libcuda)
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder()
+{
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    });
+    return fn;
+}
+
+// Launch plan of k_conv_tc for one layer: output channels per block (the
+// whole layer up to 128; 96 for 192), weights resident when they fit in
+// kTcWeightMax, else streamed with the pixels; the deepest ring that fits,
+// with two blocks per SM when asked for and each keeps two stages or more.
+struct TcPlan {
+    int bn = 0, nstage = 0, per_sm = 1, smem = 0;
+    bool stream = false, dxn = false;
+};
+
+TcPlan tc_plan(int Cin, int Cout, int blocks_per_sm)
+{
+    TcPlan p;
+    if (Cin % kTcBK || Cout % 32) return p;
+    const int bn = Cout <= 128 ? Cout : (Cout % 128 == 0 ? 128 : 96);
+    if (Cout % bn) return p;
+    // up to 64 output channels the three taps of a row go into N (3 BN)
+    p.dxn = bn <= 64;
+    p.stream = tc_weight_bytes(Cin, bn) > kTcWeightMax;
+    const int stage = tc_stage_bytes(bn, p.stream, p.dxn), fixed = tc_fixed_bytes(Cin, bn, p.stream);
+    p.nstage = std::min(kTcMaxStages, (kTcSmemMax - fixed) / stage);
+    // a block holding all 512 tensor-memory columns must have its SM alone
+    if (blocks_per_sm == 2 && tc_tmem_cols(bn, p.dxn) <= 256) {
+        const int half = (228 * 1024) / 2 - 1024;  // per-block reservation of 1 KB
+        const int st2 = std::min(kTcMaxStages, (half - fixed) / stage);
+        if (st2 >= 2) {
+            p.nstage = st2;
+            p.per_sm = 2;
+        }
+    }
+    if (p.nstage < 2) return TcPlan();
+    p.bn = bn;
+    p.smem = fixed + p.nstage * stage;
+    // one block per SM: more than half of the SM's shared memory
+    if (p.per_sm == 1) p.smem = std::max(p.smem, 116 * 1024);
+    return p;
+}
+
+template <int BN, bool STREAM, bool DXN>
+dect_status launch_conv_tc(const dect_cnn *n, const ConvArgs &a, const TcPlan &plan, cudaStream_t s)
+{
+    PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+    if (!enc) {
+        set_error_text("k_conv_tc: cuTensorMapEncodeTiled is not available from the driver");
+        return DECT_ERR_CUDA;
+    }
+    // X: NHWC view, 4-D {channel, x, y, image}; the box is one shifted halo copy
+    CUtensorMap tx, tw;
+    const cuuint64_t xdim[4] = {(cuuint64_t)a.Cin, (cuuint64_t)a.W, (cuuint64_t)a.H, (cuuint64_t)a.B};
+    const cuuint64_t xstr[3] = {(cuuint64_t)a.ldx * 2, (cuuint64_t)a.W * a.ldx * 2, (cuuint64_t)a.H * a.W * a.ldx * 2};
+    const cuuint32_t xbox[4] = {(cuuint32_t)kTcBK, (cuuint32_t)kTcTW, (cuuint32_t)(kTcTH + 2), 1u};
+    const cuuint32_t ones[4] = {1u, 1u, 1u, 1u};
+    CUresult r = enc(&tx, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<bf16 *>(a.X), xdim, xstr, xbox, ones,
+                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    // Wt [Cout][9][Cin].  Streamed: one 3-D box {32 channels, BN rows, 9 taps}
+    // per chunk (the tap stride Cin is smaller than the row stride 9 Cin), or,
+    // if the driver does not take that map, boxes of BN rows x 32 channels of
+    // one tap in a 2-D view [Cout][9 Cin] (the resident weights use those).
+    int w3d = 0;
+    if (r == CUDA_SUCCESS && STREAM) {
+        const cuuint64_t wdim3[3] = {(cuuint64_t)a.Cin, (cuuint64_t)a.Cout, 9};
+        const cuuint64_t wstr3[2] = {(cuuint64_t)9 * a.Cin * 2, (cuuint64_t)a.Cin * 2};
+        const cuuint32_t wbox3[3] = {(cuuint32_t)kTcBK, (cuuint32_t)BN, 9u};
+        w3d = enc(&tw, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<bf16 *>(a.Wt), wdim3, wstr3, wbox3, ones,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+    }
+    const cuuint64_t wdim[2] = {(cuuint64_t)9 * a.Cin, (cuuint64_t)a.Cout};
+    const cuuint64_t wstr[1] = {(cuuint64_t)9 * a.Cin * 2};
+    const cuuint32_t wbox[2] = {(cuuint32_t)kTcBK, (cuuint32_t)BN};
+    if (r == CUDA_SUCCESS && !w3d)
+        r = enc(&tw, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<bf16 *>(a.Wt), wdim, wstr, wbox, ones,
+                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) {
+        set_error_text("k_conv_tc: cuTensorMapEncodeTiled failed with CUresult " + std::to_string((int)r));
+        return DECT_ERR_CUDA;
+    }
+    // Every block takes more than a third of the SM's shared memory, so at
+    // most two share an SM and their tensor memory (at most 256 columns
+    // each) always fits in its 512.
+    DECT_CUDA(
+        cudaFuncSetAttribute(k_conv_tc<BN, STREAM, DXN>, cudaFuncAttributeMaxDynamicSharedMemorySize, plan.smem));
+    constexpr int OW = DXN ? kTcTW - 2 : kTcTW;  // output columns per tile
+    const int tiles_x = (a.W + OW - 1) / OW, tiles_y = (a.H + kTcTH - 1) / kTcTH;
+    const int ntiles = a.B * tiles_x * tiles_y, ny = a.Cout / BN;
+    const int gx = std::max(1, std::min(ntiles, (kSMs * plan.per_sm + ny - 1) / ny));
+    k_conv_tc<BN, STREAM, DXN><<<dim3(gx, ny), kTcThreads, plan.smem, s>>>(tx, tw, a, tiles_x, tiles_y, plan.nstage,
+                                                                            w3d, n->err);
+    return DECT_OK;
+}
+
 dect_status conv(const dect_cnn *n, const bf16 *X, int ldx, int Cin, const bf16 *Wt, const float *bias, bf16 *Y,
                  int ldy, int Cout, const bf16 *mask, int ldm, bool relu, int B, int H, int W, cudaStream_t s)
 {
     ConvArgs a{X, ldx, Cin, Wt, bias, Y, ldy, Cout, mask, ldm, relu ? 1 : 0, B, H, W};
     const int P = B * H * W;
-    if (Cout % 64 == 0) {
+    if (n->conv_path == DECT_CNN_CONV_TCGEN05) {
+        dect_status st = DECT_ERR_INVALID_ARG;
+        const TcPlan pl = tc_plan(Cin, Cout, n->conv_blocks_per_sm);
+        switch (pl.bn * 2 + (pl.stream ? 1 : 0)) {
+        case 256: st = launch_conv_tc<128, false, false>(n, a, pl, s); break;
+        case 257: st = launch_conv_tc<128, true, false>(n, a, pl, s); break;
+        case 192: st = launch_conv_tc<96, false, false>(n, a, pl, s); break;
+        case 193: st = launch_conv_tc<96, true, false>(n, a, pl, s); break;
+        case 128: st = launch_conv_tc<64, false, true>(n, a, pl, s); break;
+        case 129: st = launch_conv_tc<64, true, true>(n, a, pl, s); break;
+        case 64: st = launch_conv_tc<32, false, true>(n, a, pl, s); break;
+        case 65: st = launch_conv_tc<32, true, true>(n, a, pl, s); break;
+        default: set_error_text("k_conv_tc: no launch plan fits this layer");
+        }
+        if (st != DECT_OK) return st;
+    } else if (Cout % 64 == 0) {
         dim3 g((P + 63) / 64, Cout / 64);
         k_conv<64><<<g, 128, 0, s>>>(a);
     } else {
@@ -690,6 +1221,7 @@ extern "C" dect_status dect_cnn_create(int device, int max_pixels, dect_cnn **ou
     std::memset(n, 0, sizeof(*n));
     n->device = device;
     n->max_p = max_pixels;
+    n->conv_blocks_per_sm = 2;
     n->np = num_params();
     int64_t o = 0;
     for (int l = 0; l < kLayers; ++l) {
@@ -716,8 +1248,9 @@ extern "C" dect_status dect_cnn_create(int device, int max_pixels, dect_cnn **ou
     n->wpart_elems = (size_t)64 << 20;  // 256 MB of FP32 split-K partials at most
     if (ok) ok = alloc((void **)&n->out, 4 * P) && alloc((void **)&n->wpart, 4 * n->wpart_elems) &&
                  alloc((void **)&n->cpart, 4 * ((P / 4096 + 2) * 192)) && alloc((void **)&n->hpart, 4 * 4096 * 33);
+    if (ok) ok = alloc((void **)&n->err, sizeof(unsigned));
     if (ok) ok = cudaMemset(n->m, 0, 4 * n->np) == cudaSuccess && cudaMemset(n->v, 0, 4 * n->np) == cudaSuccess &&
-                 cudaMemset(n->prm, 0, 4 * n->np) == cudaSuccess;
+                 cudaMemset(n->prm, 0, 4 * n->np) == cudaSuccess && cudaMemset(n->err, 0, sizeof(unsigned)) == cudaSuccess;
     if (!ok) {
         dect_cnn_destroy(n);
         return DECT_ERR_OOM;
@@ -733,7 +1266,7 @@ extern "C" dect_status dect_cnn_destroy(dect_cnn *n)
     cudaDeviceSynchronize();
     void *ptrs[] = {n->prm, n->grad, n->m, n->v, n->xin, n->a1, n->e1, n->c1, n->a9, n->d1, n->p1, n->a3,
                     n->c2, n->a7, n->d2, n->p2, n->a5, n->bt, n->g_full_a, n->g_full_b, n->g_c1, n->g_half_a,
-                    n->g_half_b, n->g_c2, n->g_q_a, n->g_q_b, n->out, n->wpart, n->cpart, n->hpart};
+                    n->g_half_b, n->g_c2, n->g_q_a, n->g_q_b, n->out, n->wpart, n->cpart, n->hpart, n->err};
     for (void *p : ptrs) cudaFree(p);
     for (int l = 0; l < kLayers; ++l) {
         cudaFree(n->wf[l]);
@@ -827,6 +1360,7 @@ extern "C" dect_status dect_cnn_loss_grad(dect_cnn *n, const float *x, const flo
     count_launches(3);
     DECT_LAUNCH_CHECK();
     DECT_CUDA(cudaStreamSynchronize(s));
+    if ((st = dect_cnn_check(n)) != DECT_OK) return st;
     if (loss) *loss = lsum / (float)P;
     if (grad_host) DECT_CUDA(cudaMemcpy(grad_host, n->grad, 4 * n->np, cudaMemcpyDeviceToHost));
     return DECT_OK;
@@ -844,5 +1378,36 @@ extern "C" dect_status dect_cnn_adam_step(dect_cnn *n, float lr, float beta1, fl
                                                              eps, c1, c2);
     count_launches(1);
     DECT_LAUNCH_CHECK();
+    return DECT_OK;
+}
+
+extern "C" dect_status dect_cnn_set_conv_path(dect_cnn *n, int path)
+{
+    if (!n || (path != DECT_CNN_CONV_TCGEN05 && path != DECT_CNN_CONV_MMA_SYNC)) return DECT_ERR_INVALID_ARG;
+    n->conv_path = path;
+    return DECT_OK;
+}
+
+extern "C" int dect_cnn_get_conv_path(const dect_cnn *n) { return n ? n->conv_path : -1; }
+
+extern "C" dect_status dect_cnn_set_conv_tuning(dect_cnn *n, int blocks_per_sm)
+{
+    if (!n || (blocks_per_sm != 1 && blocks_per_sm != 2)) return DECT_ERR_INVALID_ARG;
+    n->conv_blocks_per_sm = blocks_per_sm;
+    return DECT_OK;
+}
+
+extern "C" dect_status dect_cnn_check(dect_cnn *n)
+{
+    if (!n) return DECT_ERR_INVALID_ARG;
+    DECT_CUDA(cudaSetDevice(n->device));
+    DECT_CUDA(cudaDeviceSynchronize());
+    unsigned h = 0;
+    DECT_CUDA(cudaMemcpy(&h, n->err, sizeof(h), cudaMemcpyDeviceToHost));
+    if (h) {
+        DECT_CUDA(cudaMemset(n->err, 0, sizeof(unsigned)));
+        set_error_text("k_conv_tc: a bounded wait ran out (the convolution's output is not valid)");
+        return DECT_ERR_TIMEOUT;
+    }
     return DECT_OK;
 }

@@ -75,6 +75,9 @@ def test_host_side_argument_checks(lib):
     assert L.dect_plan_create(C.byref(bad), 0, None, C.byref(out)) == 1
     assert L.dect_plan_destroy(None) == 0
     assert L.dect_plan_get_tuning(None, 2, None, None) == 1
+    assert L.dect_cnn_set_conv_path(None, 0) == 1
+    assert L.dect_cnn_get_conv_path(None) == -1
+    assert L.dect_cnn_check(None) == 1
 
 
 def test_struct_layouts_match_the_header(tmp_path):
