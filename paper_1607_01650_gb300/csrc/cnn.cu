@@ -12,11 +12,13 @@
 //
 // Activations are NHWC BF16 (channel counts padded to multiples of 32; the
 // input has 32 channels of which only the first is non-zero); the 3x3
-// convolutions are implicit GEMMs on the tensor cores (mma.sync m16n8k16,
-// BF16 inputs, FP32 accumulation).  Input gradients use the same kernel with
-// the weights flipped and transposed; weight gradients are a split-K
-// implicit GEMM reduced in a fixed order.  Master weights, gradients and the
-// Adam state are FP32.  Parameter vector layout (shared with the host):
+// convolutions are implicit GEMMs on the 5th-generation tensor cores
+// (tcgen05.mma, BF16 inputs, FP32 accumulation in tensor memory, operands
+// staged by TMA): k_conv_tc for the forward pass and the input gradients
+// (the same kernel with the weights flipped and transposed), k_wgrad_tc for
+// the weight gradients, whose per-block partials are added in a fixed order.
+// The warp-level mma.sync kernels (k_conv, k_wgrad) remain as a second,
+// selectable path.  Master weights, gradients and the Adam state are FP32.  Parameter vector layout (shared with the host):
 // per layer W[Cout][Cin][3][3] then b[Cout]; then the head Wh[32], bh.
 #include <cuda.h>  // CUtensorMap and its enums (the encoder is fetched from the driver at run time)
 #include <cuda_bf16.h>
@@ -421,7 +423,7 @@ __host__ __device__ constexpr uint32_t tc_idesc(int m, int n)
 template <int BN, bool STREAM, bool DXN>
 __global__ void __launch_bounds__(kTcThreads, 1)
     k_conv_tc(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmW, ConvArgs a,
-              int tiles_x, int tiles_y, int nstage, int w3d, unsigned *err)
+              int tiles_x, int tiles_y, int nstage, int cps, int w3d, unsigned *err)
 {
     static_assert(BN % 32 == 0 && BN >= 32 && BN <= 128, "output channels per block: 32 .. 128, a multiple of 32");
     static_assert(!DXN || BN <= 64, "with the taps folded into N, N = 3 BN <= 192");
@@ -432,7 +434,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     extern __shared__ unsigned char smraw[];
     unsigned char *sm =
         reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smraw) + 1023) & ~(uintptr_t)1023);
-    constexpr int STAGE = tc_stage_bytes(BN, STREAM, DXN);
+    constexpr int CHUNK = tc_stage_bytes(BN, STREAM, DXN);  // one chunk of 32 input channels
+    const int STAGE = cps * CHUNK;                          // a stage: cps chunks of the same tile
     constexpr int ACOPY = DXN ? kTcCopy : kTcAStage;  // the pixel part of a stage
     const int nck = a.Cin / kTcBK;
     const int wbytes = STREAM ? 0 : tc_weight_bytes(a.Cin, BN);
@@ -483,13 +486,14 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             for (int t = blockIdx.x; t < ntiles && !s_fail; t += gridDim.x) {
                 const int b = t / per_img, r = t % per_img;
                 const int y0 = (r / tiles_x) * kTcTH, x0 = (r % tiles_x) * OW - (DXN ? 1 : 0);
-                for (int c = 0; c < nck; ++c, ++n, s = (s + 1 == nstage) ? 0 : s + 1, u += (s == 0)) {
+                for (int c0 = 0; c0 < nck; c0 += cps, ++n, s = (s + 1 == nstage) ? 0 : s + 1, u += (s == 0)) {
                     if (u > 0 && !tc_wait(a_empty + s, (u - 1) & 1, &s_fail)) {
                         s_fail = 1;
                         break;
                     }
                     mbar_arrive_expect_tx(a_full + s, (unsigned)STAGE);
-                    unsigned char *dst = sA + s * STAGE;
+                    for (int c = c0; c < c0 + cps; ++c) {
+                    unsigned char *dst = sA + s * STAGE + (c - c0) * CHUNK;
                     if (DXN) {
                         tma_load_4d(dst, &tmX, c * kTcBK, x0, y0 - 1, b, a_full + s);
                     } else {
@@ -506,6 +510,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                                 tma_load_2d(dst + ACOPY + tap * BN * kTcBK * 2, &tmW, tap * a.Cin + c * kTcBK, n0,
                                             a_full + s);
                         }
+                    }
                     }
                     issued = n + 1;
                 }
@@ -526,14 +531,15 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                 }
                 tc_fence_after();
                 const uint32_t d = tmem + (uint32_t)(acc * AW);
-                for (int c = 0; c < nck; ++c, ++n, s = (s + 1 == nstage) ? 0 : s + 1, u += (s == 0)) {
+                for (int c0 = 0; c0 < nck; c0 += cps, ++n, s = (s + 1 == nstage) ? 0 : s + 1, u += (s == 0)) {
                     if (!tc_wait(a_full + s, u & 1, &s_fail)) {
                         ok = false;
                         break;
                     }
                     tc_fence_after();
+                    for (int c = c0; c < c0 + cps; ++c) {
                     // (start address >> 4) sits in the low bits and never carries
-                    const uint64_t ad0 = a_desc0 + (uint64_t)((s * STAGE) >> 4);
+                    const uint64_t ad0 = a_desc0 + (uint64_t)((s * STAGE + (c - c0) * CHUNK) >> 4);
                     const uint64_t bd0 = STREAM ? ad0 + (uint64_t)(ACOPY >> 4)
                                                 : w_desc0 + (uint64_t)((c * tc_wslice_bytes(BN)) >> 4);
                     if (DXN) {
@@ -555,6 +561,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                             tc_mma(d, ad, bd, idesc, (c | tap) ? 1u : 0u);
                             tc_mma(d, ad + 2, bd + 2, idesc, 1u);
                         }
+                    }
                     }
                     tc_commit(a_empty + s);
                     s_consumed = n + 1;
@@ -588,40 +595,42 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             const bool in = y < a.H && x < a.W && (!DXN || (xm >= 1 && xm <= kTcTW - 2));
             const int64_t p = ((int64_t)b * a.H + y) * a.W + x;
             const uint32_t trow = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * AW);
-#pragma unroll 1
-            for (int c0 = cbeg; c0 < cbeg + HALF; c0 += 16) {
+            // all of the warp's columns are loaded before one wait: NP pieces
+            // of 16 columns (three blocks of them with folded taps)
+            constexpr int NP = HALF / 16, NB3 = DXN ? 3 : 1;
+            uint32_t rv[NB3][NP][16];
+#pragma unroll
+            for (int k = 0; k < NB3; ++k)
+#pragma unroll
+                for (int j = 0; j < NP; ++j) tc_ld16_nowait(trow + (uint32_t)(k * BN + cbeg + 16 * j), rv[k][j]);
+            tc_wait_ld();
+#pragma unroll
+            for (int j = 0; j < NP; ++j) {
                 float v[16];
                 if (DXN) {
                     // Y[x] = D[x - 1][tap dx = -1] + D[x][dx = 0] + D[x + 1][dx = +1]:
                     // the neighbours are lanes m -+ 1 of the same 16-pixel row
-                    uint32_t l[16], c[16], rr[16];
-                    tc_ld16_nowait(trow + (uint32_t)c0, l);
-                    tc_ld16_nowait(trow + (uint32_t)(BN + c0), c);
-                    tc_ld16_nowait(trow + (uint32_t)(2 * BN + c0), rr);
-                    tc_wait_ld();
 #pragma unroll
                     for (int i = 0; i < 16; ++i)
-                        v[i] = __shfl_up_sync(0xffffffffu, __uint_as_float(l[i]), 1) + __uint_as_float(c[i]) +
-                               __shfl_down_sync(0xffffffffu, __uint_as_float(rr[i]), 1);
+                        v[i] = __shfl_up_sync(0xffffffffu, __uint_as_float(rv[0][j][i]), 1) +
+                               __uint_as_float(rv[DXN ? 1 : 0][j][i]) +
+                               __shfl_down_sync(0xffffffffu, __uint_as_float(rv[DXN ? 2 : 0][j][i]), 1);
                 } else {
-                    uint32_t c[16];
-                    tc_ld16_nowait(trow + (uint32_t)c0, c);
-                    tc_wait_ld();
 #pragma unroll
-                    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(c[i]);
+                    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(rv[0][j][i]);
                 }
                 if (!in) continue;
-                const int co = n0 + c0;
+                const int c0 = cbeg + 16 * j, co = n0 + c0;
 #pragma unroll
                 for (int g = 0; g < 2; ++g) {
                     B8 mk, o;
                     if (a.mask) mk = ld8(a.mask + p * a.ldm + co + 8 * g);
 #pragma unroll
                     for (int i = 0; i < 8; ++i) {
-                        float rv = v[8 * g + i] + s_bias[c0 + 8 * g + i];
-                        if (a.relu) rv = fmaxf(rv, 0.f);
-                        if (a.mask && !(mk.v[i] > 0.f)) rv = 0.f;
-                        o.v[i] = rv;
+                        float rvl = v[8 * g + i] + s_bias[c0 + 8 * g + i];
+                        if (a.relu) rvl = fmaxf(rvl, 0.f);
+                        if (a.mask && !(mk.v[i] > 0.f)) rvl = 0.f;
+                        o.v[i] = rvl;
                     }
                     st8(a.Y + p * a.ldy + co + 8 * g, o);
                 }
@@ -748,16 +757,234 @@ __global__ void __launch_bounds__(128) k_wgrad(WgradArgs a)
         }
 }
 
-// dW (flat layout [Cout][Cin_real][3][3]) = sum over splits, in order.
-__global__ void k_wgrad_reduce(const float *part, int splits, int Cout, int Cin_pad, int Cin_real, float *dW)
+// dW (flat layout [Cout][Cin_real][3][3]) = sum over the splits of
+// part[split][co][tap][ci], in a fixed order: a block takes 32 consecutive
+// elements e = (co * 9 + tap) * Cin_pad + ci (coalesced reads) and 8 slices
+// of the splits (slice j sums splits j, j + 8, ...); the slices are then
+// added in slice order.
+__global__ void __launch_bounds__(256) k_wgrad_reduce(const float *part, int splits, int Cout, int Cin_pad,
+                                                      int Cin_real, float *dW)
 {
-    const int64_t n = (int64_t)Cout * Cin_real * 9;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        const int co = (int)(i / (Cin_real * 9)), r = (int)(i % (Cin_real * 9));
-        const int ci = r / 9, tap = r % 9;
-        double s = 0.0;
-        for (int k = 0; k < splits; ++k) s += part[(((int64_t)k * Cout + co) * 9 + tap) * Cin_pad + ci];
-        dW[i] = (float)s;
+    __shared__ double red[8][32];
+    const int64_t n = (int64_t)Cout * 9 * Cin_pad;
+    const int64_t e = (int64_t)blockIdx.x * 32 + (threadIdx.x & 31);
+    const int j = threadIdx.x >> 5;
+    double acc = 0.0;
+    if (e < n)
+        for (int k = j; k < splits; k += 8) acc += part[(int64_t)k * n + e];
+    red[j][threadIdx.x & 31] = acc;
+    __syncthreads();
+    if (threadIdx.x < 32 && e < n) {
+        double t = 0.0;
+        for (int jj = 0; jj < 8; ++jj) t += red[jj][threadIdx.x];
+        const int ci = (int)(e % Cin_pad);
+        const int64_t r = e / Cin_pad;
+        const int tap = (int)(r % 9), co = (int)(r / 9);
+        if (ci < Cin_real) dW[((int64_t)co * Cin_real + ci) * 9 + tap] = (float)t;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Weight gradient on the tensor cores (tcgen05):
+//   dW[co][tap][ci] = sum over pixels p of X[p + off(tap)][ci] * dY[p][co]
+// as D[m][n] = sum over k of A[m][k] B[n][k] with k = pixel, n = co and m a
+// row of a "slot" (tap, 32 input channels): an MMA of M = 128 covers a
+// group of four slots.  Both operands are read in their NHWC layout, i.e.
+// MN-major (the 32 channels of a pixel contiguous): TMA copies, per tile of
+// 8 x 16 pixels, one box {32 channels, 16, 8} of X shifted by each slot's
+// tap (zero outside the image) and the Cout / 32 boxes of dY; in the 64-byte
+// swizzle an atom is 32 channels x 8 pixels, atoms along M (or N) are one
+// box apart (LBO) and groups of 8 pixels 512 bytes apart (SBO); a K = 16
+// step is one image row of the tile (+1 KB).  A persistent block keeps its
+// groups' accumulators (FP32, G x Cout columns) in tensor memory over all
+// its tiles and writes them once as a partial; the partials are then added
+// in block order (k_wgrad_tc_reduce).  Roles and bounded waits as in
+// k_conv_tc: warp 0 TMA, warp 1 MMA, warps 2-5 read the accumulators.
+// ---------------------------------------------------------------------------
+constexpr int kWgR = 8;                               // image rows per tile (K = 128 pixels)
+constexpr int kWgBox = kWgR * kTcTW * kTcBK * 2;      // one box {32 channels, 16, 8}: 8 KB
+constexpr int kWgMaxStages = 4;
+constexpr int kWgThreads = 192;
+
+struct WgTcArgs {
+    int Cin, Cout, B, H, W;
+    int ncb;      // Cin / 32: slots per tap
+    int ngroups;  // ceil(9 ncb / 4)
+};
+
+__host__ __device__ constexpr int wg_stage_bytes(int G, int N) { return (4 * G + N / 32) * kWgBox; }
+
+// MN-major operand in the 64-byte swizzle: atoms of 32 elements x 8 rows,
+// `lbo` bytes between atoms along M (or N), 512 bytes between 8-row groups
+__device__ __forceinline__ uint64_t sw64_mn_desc(const void *tile, uint32_t lbo)
+{
+    const uint32_t a = smem_u32(tile);
+    return (uint64_t)((a >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+           ((uint64_t)(512 >> 4) << 32) | ((uint64_t)1 << 46) | ((uint64_t)4 << 61);
+}
+
+// kind::f16 instruction descriptor with both operands MN-major (bits 15, 16)
+__host__ __device__ constexpr uint32_t tc_idesc_mn(int m, int n) { return tc_idesc(m, n) | (1u << 15) | (1u << 16); }
+
+template <int N>
+__global__ void __launch_bounds__(kWgThreads, 1)
+    k_wgrad_tc(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmD, WgTcArgs a,
+               int G, int nstage, float *part, unsigned *err)
+{
+    static_assert(N == 32 || N == 64 || N == 128, "Cout of a forward layer");
+    constexpr uint32_t idesc = tc_idesc_mn(128, N);
+    extern __shared__ unsigned char smraw[];
+    unsigned char *sm =
+        reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smraw) + 1023) & ~(uintptr_t)1023);
+    const int STAGE = wg_stage_bytes(G, N);
+    uint64_t *bars = reinterpret_cast<uint64_t *>(sm + nstage * STAGE);
+    uint64_t *full = bars, *empty = bars + kWgMaxStages, *done = bars + 2 * kWgMaxStages;
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(done + 1);
+    __shared__ volatile int s_fail;
+    __shared__ int s_consumed;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int tiles_x = (a.W + kTcTW - 1) / kTcTW, tiles_y = (a.H + kWgR - 1) / kWgR;
+    const int per_img = tiles_x * tiles_y, ntiles = a.B * per_img;
+    // blockIdx.x: the group set (the blocks sharing a tile are launched side
+    // by side, so that they read its pixels from L2 at about the same time);
+    // blockIdx.y: the block's share of the tiles
+    const int g0 = blockIdx.x * G, gn = min(G, a.ngroups - g0);
+    const int nslot = 9 * a.ncb;
+    uint32_t tm_cols = 32;
+    while (tm_cols < (uint32_t)(G * N)) tm_cols *= 2;
+
+    if (threadIdx.x == 0) {
+        for (int q = 0; q < nstage; ++q) {
+            mbar_init(full + q, 1);
+            mbar_init(empty + q, 1);
+        }
+        mbar_init(done, 1);
+        s_fail = 0;
+        s_consumed = 0;
+    }
+    if (warp == 0) tc_alloc(tmem_slot, tm_cols);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+
+    int issued = 0;
+    if (warp == 0) {
+        if (lane == 0) {
+            // boxes per tile: the valid slots of the block's groups, then dY
+            int nvalid = 0;
+            for (int k = 0; k < 4 * gn; ++k) nvalid += (g0 * 4 + k) < nslot;
+            const unsigned bytes = (unsigned)((nvalid + N / 32) * kWgBox);
+            int n = 0, st = 0, u = 0;
+            for (int t = blockIdx.y; t < ntiles && !s_fail; t += gridDim.y, ++n) {
+                if (u > 0 && !tc_wait(empty + st, (u - 1) & 1, &s_fail)) {
+                    s_fail = 1;
+                    break;
+                }
+                const int b = t / per_img, r = t % per_img;
+                const int y0 = (r / tiles_x) * kWgR, x0 = (r % tiles_x) * kTcTW;
+                unsigned char *dst = sm + st * STAGE;
+                mbar_arrive_expect_tx(full + st, bytes);
+                for (int k = 0; k < 4 * gn; ++k) {
+                    const int sidx = g0 * 4 + k;
+                    if (sidx >= nslot) break;
+                    const int tap = sidx / a.ncb, cb = sidx % a.ncb;
+                    tma_load_4d(dst + k * kWgBox, &tmX, cb * kTcBK, x0 + tap % 3 - 1, y0 + tap / 3 - 1, b, full + st);
+                }
+#pragma unroll
+                for (int j = 0; j < N / 32; ++j)
+                    tma_load_4d(dst + (4 * G + j) * kWgBox, &tmD, j * kTcBK, x0, y0, b, full + st);
+                issued = n + 1;
+                if (++st == nstage) {
+                    st = 0;
+                    ++u;
+                }
+            }
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            int n = 0, st = 0, u = 0;
+            bool ok = true;
+            for (int t = blockIdx.y; t < ntiles; t += gridDim.y, ++n) {
+                if (!tc_wait(full + st, u & 1, &s_fail)) {
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
+                const unsigned char *base = sm + st * STAGE;
+                const uint64_t bd0 = sw64_mn_desc(base + 4 * G * kWgBox, kWgBox);
+                for (int gi = 0; gi < gn; ++gi) {
+                    const uint64_t ad0 = sw64_mn_desc(base + gi * 4 * kWgBox, kWgBox);
+#pragma unroll
+                    for (int i = 0; i < kWgR; ++i)  // one image row (16 pixels) per K step: +1 KB
+                        tc_mma(tmem + (uint32_t)(gi * N), ad0 + (uint64_t)(i * 64), bd0 + (uint64_t)(i * 64), idesc,
+                               (n | i) ? 1u : 0u);
+                }
+                tc_commit(empty + st);
+                s_consumed = n + 1;
+                if (++st == nstage) {
+                    st = 0;
+                    ++u;
+                }
+            }
+            if (!ok) s_fail = 1;
+            tc_commit(done);
+        }
+    } else {
+        // accumulators -> partial: part[block y][group][row][co], row = slot-in-group * 32 + channel
+        const int q = warp & 3;
+        const bool ok = tc_wait(done, 0, &s_fail);
+        if (__all_sync(0xffffffffu, ok)) {
+            tc_fence_after();
+            for (int gi = 0; gi < gn; ++gi) {
+                float *dst = part + (((int64_t)blockIdx.y * a.ngroups + g0 + gi) * 128 + q * 32 + lane) * N;
+#pragma unroll 1
+                for (int c0 = 0; c0 < N; c0 += 16) {
+                    uint32_t v[16];
+                    tc_ld16_nowait(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(gi * N + c0), v);
+                    tc_wait_ld();
+#pragma unroll
+                    for (int i = 0; i < 16; i += 4)
+                        *reinterpret_cast<float4 *>(dst + c0 + i) =
+                            make_float4(__uint_as_float(v[i]), __uint_as_float(v[i + 1]), __uint_as_float(v[i + 2]),
+                                        __uint_as_float(v[i + 3]));
+                }
+            }
+        } else {
+            s_fail = 1;
+        }
+    }
+    __syncwarp();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const bool mma_ok = mbar_wait_bounded(done, 0, kTcPolls);
+        if (s_fail || !mma_ok) {
+            atomicOr(err, 1u);
+            for (int n = s_consumed; n < issued; ++n)
+                mbar_wait_bounded(full + n % nstage, (n / nstage) & 1, kTcPolls);
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == 0) tc_dealloc(tmem, tm_cols);
+}
+
+// dW (flat [Cout][Cin_real][3][3]) = sum over blocks k of part[k][g][row][co]
+// (fixed order), row = (slot % 4) * 32 + channel, slot = tap * ncb + ci / 32.
+__global__ void k_wgrad_tc_reduce(const float *part, int nparts, int ngroups, int N, int ncb, int Cin_real,
+                                  float *dW)
+{
+    const int64_t n = (int64_t)ngroups * 128 * N;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+        const int co = (int)(e % N);
+        const int64_t rr = e / N;
+        const int row = (int)(rr % 128), g = (int)(rr / 128);
+        const int sidx = g * 4 + row / 32, ci = (sidx % ncb) * 32 + row % 32, tap = sidx / ncb;
+        if (sidx >= 9 * ncb || ci >= Cin_real) continue;
+        double acc = 0.0;
+        for (int k = 0; k < nparts; ++k) acc += part[(int64_t)k * n + e];
+        dW[((int64_t)co * Cin_real + ci) * 9 + tap] = (float)acc;
     }
 }
 
@@ -789,13 +1016,21 @@ __global__ void k_chansum(const bf16 *Y, int ld, int C, int P, int pps, float *p
     }
 }
 
-__global__ void k_chansum_reduce(const float *part, int splits, int C, float *out)
+// out[c] = sum over k of part[k][c] (k < nblk), fixed order: one block per
+// column; thread t sums k = t, t + 256, ...; then a fixed tree.
+__global__ void __launch_bounds__(256) k_sum_cols(const float *part, int nblk, int width, float *out)
 {
-    const int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= C) return;
-    double s = 0.0;
-    for (int k = 0; k < splits; ++k) s += part[(int64_t)k * C + c];
-    out[c] = (float)s;
+    __shared__ double red[256];
+    const int c = blockIdx.x;
+    double acc = 0.0;
+    for (int k = threadIdx.x; k < nblk; k += 256) acc += part[(int64_t)k * width + c];
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    for (int h = 128; h > 0; h >>= 1) {
+        if (threadIdx.x < h) red[threadIdx.x] += red[threadIdx.x + h];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) out[c] = (float)red[0];
 }
 
 // ---------------------------------------------------------------------------
@@ -885,7 +1120,11 @@ __global__ void k_head(const bf16 *d1, const float *Wh, const float *bh, const f
         float h = *bh;
         const bf16 *row = d1 + (int64_t)p * 32;
 #pragma unroll
-        for (int c = 0; c < 32; ++c) h = fmaf(Wh[c], __bfloat162float(row[c]), h);
+        for (int g = 0; g < 4; ++g) {
+            const B8 v = ld8(row + 8 * g);
+#pragma unroll
+            for (int c = 0; c < 8; ++c) h = fmaf(Wh[8 * g + c], v.v[c], h);
+        }
         const float o = x[p] + s * h;
         if (out) out[p] = o;
         if (t) {
@@ -916,10 +1155,15 @@ __global__ void k_head_back(const bf16 *d1, const float *Wh, const float *out, c
         const float dh = s * 2.f * (out[p] - t[p]) / (float)P;
         const bf16 *row = d1 + (int64_t)p * 32;
 #pragma unroll
-        for (int c = 0; c < 32; ++c) {
-            const float v = __bfloat162float(row[c]);
-            acc[c] = fmaf(dh, v, acc[c]);
-            dd1[(int64_t)p * 32 + c] = __float2bfloat16(v > 0.f ? dh * Wh[c] : 0.f);
+        for (int g = 0; g < 4; ++g) {
+            const B8 v = ld8(row + 8 * g);
+            B8 o;
+#pragma unroll
+            for (int c = 0; c < 8; ++c) {
+                acc[8 * g + c] = fmaf(dh, v.v[c], acc[8 * g + c]);
+                o.v[c] = v.v[c] > 0.f ? dh * Wh[8 * g + c] : 0.f;
+            }
+            st8(dd1 + (int64_t)p * 32 + 8 * g, o);
         }
         acc[32] += dh;
     }
@@ -933,14 +1177,6 @@ __global__ void k_head_back(const bf16 *d1, const float *Wh, const float *out, c
     }
 }
 
-__global__ void k_sum_parts(const float *part, int nblk, int width, float *out)
-{
-    const int c = threadIdx.x;
-    if (c >= width) return;
-    double s = 0.0;
-    for (int k = 0; k < nblk; ++k) s += part[k * width + c];
-    out[c] = (float)s;
-}
 
 // FP32 flat layer weights -> BF16 [Cout][9][Cin_pad] (forward) and
 // [Cin][9][Cout] flipped (input gradient).
@@ -1024,7 +1260,7 @@ PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder()
 // kTcWeightMax, else streamed with the pixels; the deepest ring that fits,
 // with two blocks per SM when asked for and each keeps two stages or more.
 struct TcPlan {
-    int bn = 0, nstage = 0, per_sm = 1, smem = 0;
+    int bn = 0, nstage = 0, per_sm = 1, smem = 0, cps = 1;
     bool stream = false, dxn = false;
 };
 
@@ -1037,17 +1273,30 @@ TcPlan tc_plan(int Cin, int Cout, int blocks_per_sm)
     // up to 64 output channels the three taps of a row go into N (3 BN)
     p.dxn = bn <= 64;
     p.stream = tc_weight_bytes(Cin, bn) > kTcWeightMax;
-    const int stage = tc_stage_bytes(bn, p.stream, p.dxn), fixed = tc_fixed_bytes(Cin, bn, p.stream);
-    p.nstage = std::min(kTcMaxStages, (kTcSmemMax - fixed) / stage);
-    // a block holding all 512 tensor-memory columns must have its SM alone
-    if (blocks_per_sm == 2 && tc_tmem_cols(bn, p.dxn) <= 256) {
-        const int half = (228 * 1024) / 2 - 1024;  // per-block reservation of 1 KB
-        const int st2 = std::min(kTcMaxStages, (half - fixed) / stage);
-        if (st2 >= 2) {
-            p.nstage = st2;
-            p.per_sm = 2;
-        }
-    }
+    const int chunk = tc_stage_bytes(bn, p.stream, p.dxn), fixed = tc_fixed_bytes(Cin, bn, p.stream);
+    const int nck = Cin / kTcBK;
+    // Chunks per stage: the most of a tile's chunks (a divisor of Cin / 32)
+    // that leave the ring `min_st` stages in `budget` bytes.
+    auto pick = [&](int budget, int min_st, int &cps, int &nst) {
+        for (int c = nck; c >= 1; --c)
+            if (nck % c == 0 && (budget - fixed) / (c * chunk) >= min_st) {
+                cps = c;
+                nst = std::min(kTcMaxStages, (budget - fixed) / (c * chunk));
+                return true;
+            }
+        return false;
+    };
+    // two blocks per SM (each in half the SM's shared memory, at least two
+    // stages) when asked for; otherwise, or when that does not fit, one block
+    // with at least three stages (two if nothing more fits).  A block holding
+    // all 512 tensor-memory columns must have its SM alone.
+    const bool two = blocks_per_sm == 2 && tc_tmem_cols(bn, p.dxn) <= 256 &&
+                     pick((228 * 1024) / 2 - 1024, 2, p.cps, p.nstage);
+    if (two)
+        p.per_sm = 2;
+    else if (!pick(kTcSmemMax, 3, p.cps, p.nstage))
+        pick(kTcSmemMax, 2, p.cps, p.nstage);
+    const int stage = p.cps * chunk;
     if (p.nstage < 2) return TcPlan();
     p.bn = bn;
     p.smem = fixed + p.nstage * stage;
@@ -1107,7 +1356,7 @@ dect_status launch_conv_tc(const dect_cnn *n, const ConvArgs &a, const TcPlan &p
     const int ntiles = a.B * tiles_x * tiles_y, ny = a.Cout / BN;
     const int gx = std::max(1, std::min(ntiles, (kSMs * plan.per_sm + ny - 1) / ny));
     k_conv_tc<BN, STREAM, DXN><<<dim3(gx, ny), kTcThreads, plan.smem, s>>>(tx, tw, a, tiles_x, tiles_y, plan.nstage,
-                                                                            w3d, n->err);
+                                                                            plan.cps, w3d, n->err);
     return DECT_OK;
 }
 
@@ -1144,10 +1393,85 @@ dect_status conv(const dect_cnn *n, const bf16 *X, int ldx, int Cin, const bf16 
     return DECT_OK;
 }
 
+// NHWC BF16 view {C channels, W, H, B} (row stride ld) with boxes of
+// 32 channels x 16 x `rows` pixels in the 64-byte swizzle
+CUresult encode_nhwc(PFN_cuTensorMapEncodeTiled_v12000 enc, CUtensorMap *m, const bf16 *p, int C, int ld, int B,
+                     int H, int W, int rows)
+{
+    const cuuint64_t dim[4] = {(cuuint64_t)C, (cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)B};
+    const cuuint64_t str[3] = {(cuuint64_t)ld * 2, (cuuint64_t)W * ld * 2, (cuuint64_t)H * W * ld * 2};
+    const cuuint32_t box[4] = {(cuuint32_t)kTcBK, (cuuint32_t)kTcTW, (cuuint32_t)rows, 1u};
+    const cuuint32_t ones[4] = {1u, 1u, 1u, 1u};
+    return enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<bf16 *>(p), dim, str, box, ones,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+}
+
+// Weight gradient of layer l on the tensor cores (k_wgrad_tc + its reduce).
+template <int N>
+dect_status wgrad_tc(dect_cnn *n, int l, const bf16 *dY, int ldd, const bf16 *X, int ldx, int B, int H, int W,
+                     cudaStream_t s)
+{
+    PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+    if (!enc) {
+        set_error_text("k_wgrad_tc: cuTensorMapEncodeTiled is not available from the driver");
+        return DECT_ERR_CUDA;
+    }
+    const int Cinp = cin_pad(l);
+    WgTcArgs a{Cinp, N, B, H, W, Cinp / kTcBK, (9 * (Cinp / kTcBK) + 3) / 4};
+    // groups of four slots per block: as many as two stages of the ring allow
+    const int G = std::min(N == 32 ? 3 : 2, a.ngroups);
+    const int stage = wg_stage_bytes(G, N);
+    const int nstage = std::min(kWgMaxStages, (kTcSmemMax - 1024 - 256 - kWgBox) / stage);
+    if (nstage < 2) {
+        set_error_text("k_wgrad_tc: no ring of two stages fits");
+        return DECT_ERR_INVALID_ARG;
+    }
+    // (plus one box of slack after the barriers: no operand address, under
+    // either stride of its descriptor, can leave the block's shared memory)
+    const int smem = 1024 + nstage * stage + 256 + kWgBox;
+    CUtensorMap tx, td;
+    CUresult r = encode_nhwc(enc, &tx, X, Cinp, ldx, B, H, W, kWgR);
+    if (r == CUDA_SUCCESS) r = encode_nhwc(enc, &td, dY, N, ldd, B, H, W, kWgR);
+    if (r != CUDA_SUCCESS) {
+        set_error_text("k_wgrad_tc: cuTensorMapEncodeTiled failed with CUresult " + std::to_string((int)r));
+        return DECT_ERR_CUDA;
+    }
+    const int gy = (a.ngroups + G - 1) / G;
+    const int ntiles = B * ((W + kTcTW - 1) / kTcTW) * ((H + kWgR - 1) / kWgR);
+    const int gx = std::max(1, std::min(ntiles, kSMs / gy));
+    if ((int64_t)gx * a.ngroups * 128 * N > (int64_t)n->wpart_elems) {
+        set_error_text("k_wgrad_tc: partials exceed the scratch buffer");
+        return DECT_ERR_INVALID_ARG;
+    }
+    DECT_CUDA(cudaFuncSetAttribute(k_wgrad_tc<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    k_wgrad_tc<N><<<dim3(gy, gx), kWgThreads, smem, s>>>(tx, td, a, G, nstage, n->wpart, n->err);
+    k_wgrad_tc_reduce<<<grid_for((int64_t)a.ngroups * 128 * N), 256, 0, s>>>(n->wpart, gx, a.ngroups, N, a.ncb,
+                                                                            kCin[l], n->grad + n->off_w[l]);
+    count_launches(2);
+    return DECT_OK;
+}
+
 dect_status wgrad(dect_cnn *n, int l, const bf16 *dY, int ldd, const bf16 *X, int ldx, int B, int H, int W,
                   cudaStream_t s)
 {
     const int Cout = kCout[l], Cinp = cin_pad(l), P = B * H * W;
+    if (n->conv_path == DECT_CNN_CONV_TCGEN05) {
+        dect_status st = DECT_ERR_INVALID_ARG;
+        switch (Cout) {
+        case 32: st = wgrad_tc<32>(n, l, dY, ldd, X, ldx, B, H, W, s); break;
+        case 64: st = wgrad_tc<64>(n, l, dY, ldd, X, ldx, B, H, W, s); break;
+        case 128: st = wgrad_tc<128>(n, l, dY, ldd, X, ldx, B, H, W, s); break;
+        default: set_error_text("k_wgrad_tc: unsupported output channel count");
+        }
+        if (st != DECT_OK) return st;
+        const int cpps = 4096, csplits = (P + cpps - 1) / cpps;
+        k_chansum<<<csplits, 256, 0, s>>>(dY, ldd, Cout, P, cpps, n->cpart);
+        k_sum_cols<<<Cout, 256, 0, s>>>(n->cpart, csplits, Cout, n->grad + n->off_b[l]);
+        count_launches(2);
+        DECT_CUDA(cudaGetLastError());
+        return DECT_OK;
+    }
     const int tiles = 9 * (Cinp / 32) * (Cout / 32);
     int pps = 2048;
     while ((int64_t)((P + pps - 1) / pps) * Cout * 9 * Cinp > (int64_t)n->wpart_elems) pps *= 2;
@@ -1156,11 +1480,11 @@ dect_status wgrad(dect_cnn *n, int l, const bf16 *dY, int ldd, const bf16 *X, in
     dim3 g(splits, 9 * (Cinp / 32), Cout / 32);
     (void)tiles;
     k_wgrad<<<g, 128, 0, s>>>(a);
-    k_wgrad_reduce<<<grid_for((int64_t)Cout * kCin[l] * 9), 256, 0, s>>>(n->wpart, splits, Cout, Cinp, kCin[l],
+    k_wgrad_reduce<<<(unsigned)(((int64_t)Cout * 9 * Cinp + 31) / 32), 256, 0, s>>>(n->wpart, splits, Cout, Cinp, kCin[l],
                                                                         n->grad + n->off_w[l]);
     const int cpps = 4096, csplits = (P + cpps - 1) / cpps;
     k_chansum<<<csplits, 256, 0, s>>>(dY, ldd, Cout, P, cpps, n->cpart);
-    k_chansum_reduce<<<1, 128, 0, s>>>(n->cpart, csplits, Cout, n->grad + n->off_b[l]);
+    k_sum_cols<<<Cout, 256, 0, s>>>(n->cpart, csplits, Cout, n->grad + n->off_b[l]);
     count_launches(4);
     DECT_CUDA(cudaGetLastError());
     return DECT_OK;
@@ -1324,12 +1648,12 @@ extern "C" dect_status dect_cnn_loss_grad(dect_cnn *n, const float *x, const flo
     const int hb = (int)std::min<int64_t>((P + 255) / 256, 4096);
     k_head<<<hb, 256, 0, s>>>(n->d1, n->prm + n->off_h, n->prm + n->off_h + 32, x, scale, P, n->out, target,
                               n->hpart);
-    k_sum_parts<<<1, 64, 0, s>>>(n->hpart, hb, 1, n->cpart);  // loss * P in cpart[0]
+    k_sum_cols<<<1, 256, 0, s>>>(n->hpart, hb, 1, n->cpart);  // loss * P in cpart[0]
     float lsum = 0.f;
     DECT_CUDA(cudaMemcpyAsync(&lsum, n->cpart, 4, cudaMemcpyDeviceToHost, s));
     // head backward
     k_head_back<<<hb, 256, 0, s>>>(n->d1, n->prm + n->off_h, n->out, target, scale, P, n->g_full_a, n->hpart);
-    k_sum_parts<<<1, 64, 0, s>>>(n->hpart, hb, 33, n->grad + n->off_h);
+    k_sum_cols<<<33, 256, 0, s>>>(n->hpart, hb, 33, n->grad + n->off_h);
     count_launches(4);
     // conv10: input a9, output grad g_full_a (dd1, masked)
     if ((st = wgrad(n, 9, n->g_full_a, 32, n->a9, 32, B, H, W, s)) != DECT_OK) return st;
