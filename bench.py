@@ -64,6 +64,8 @@ def parse():
                     help="fix the A^T variant (0-7, see dect_plan_get_tuning) instead of autotuning")
     ap.add_argument("--fwd-variant", type=int, default=-1,
                     help="fix the A variant (0-3, see dect_plan_get_fwd_tuning) instead of autotuning")
+    ap.add_argument("--tv-variant", type=int, default=-1,
+                    help="fix the TV-step variant (0-1, see dect_plan_get_tv_tuning) instead of autotuning")
     ap.add_argument("--batched-otf", action="store_true",
                     help="batched workload through dect_adm_tv_batch (one launch per ADM phase over all slices, "
                          "on-the-fly projector) instead of dect_adm_tv_groups")
@@ -706,6 +708,8 @@ def main():
         plan.set_tuning(min(64, 1 << (2 * S - 1).bit_length()), args.bwd_variant)
     if args.fwd_variant >= 0:
         plan.set_fwd_tuning(min(64, 1 << (2 * S - 1).bit_length()), args.fwd_variant)
+    if args.tv_variant >= 0:
+        plan.set_tv_tuning(min(64, 1 << (2 * S - 1).bit_length()), args.tv_variant)
     m_host = torch.from_numpy(make_inputs(geom, seeds_for(rank, S), STRESS_I0 if stress else I0)).pin_memory()
     m_dev = m_host.to("cuda")
     x_dev = torch.zeros((S, 2, geom.n, geom.n), device="cuda")
@@ -871,6 +875,7 @@ def main():
                    "plan_seconds": round(plan_s, 3), "nnz": plan.nnz,
                    "bwd_autotune": dict(zip(("choice", "us"), plan.tuning(width))),
                    "fwd_autotune": dict(zip(("choice", "us"), plan.fwd_tuning(width))),
+                   "tv_autotune": dict(zip(("choice", "us"), plan.tv_tuning(width))),
                    "l2": "inputs larger than L2 (tables %.0f MB)" % (plan.table_bytes / 1e6),
                    "parallelism": "replicas" if world > 1 else "1 GPU"},
         "roofline": roofline, "roofline_l1": roofline_l1, "operators": ops, "cpu_baseline": cpu, "e2e": e2e,

@@ -251,7 +251,10 @@ typedef struct {
  * reports: HOST array [n_slices * 2] (may be NULL).  Synchronises `stream`.
  * Device scratch is taken from the stream-ordered allocator and returned
  * before the call ends.
- * Errors: DECT_ERR_INVALID_ARG, DECT_ERR_OOM, DECT_ERR_CUDA.
+ * Errors: DECT_ERR_INVALID_ARG, DECT_ERR_OOM, DECT_ERR_CUDA;
+ * DECT_ERR_NONFINITE when an objective was not finite; DECT_ERR_TIMEOUT when
+ * a bounded wait inside the TV step (variant 1, dect_plan_get_tv_tuning) ran
+ * out (the images are then not valid).
  */
 dect_status dect_adm_tv(const dect_plan *plan, const float *m, float *x, int n_slices,
                         const dect_adm_params *params, dect_adm_report *reports,
@@ -489,6 +492,33 @@ dect_status dect_plan_get_fwd_tuning(const dect_plan *plan, int images, int *cho
 /* Fix the A variant for batch width `images`, or -1 to time the candidates
  * again on the next ADM call with that width. */
 dect_status dect_plan_set_fwd_tuning(dect_plan *plan, int images, int choice);
+
+/*
+ * Autotuner record of the TV step inside dect_adm_tv (the f and r step, the
+ * multiplier step of Eq. (7), the z-shrink of Eq. (8) and p, with the TV
+ * norm and |r|^2), as dect_plan_get_tuning gives it for A^T: the variant
+ * chosen for batch width `images` and the measured median time of each
+ * (microseconds; -1 = not timed).
+ *   0 blocks claim tiles of 16 rows from a counter and walk down their
+ *     columns; the updated row is exchanged through shared memory, one
+ *     block barrier per row,
+ *   1 each block takes an equal range of (strip, row) pairs; one warp
+ *     streams the rows (f, G, the multiplier) into a ring of four
+ *     shared-memory stages with 1-D bulk copies (TMA) completing on
+ *     mbarriers, the other warps compute from shared memory, no block
+ *     barrier per row; 4 or more channels only (otherwise 0 is used).
+ * Both give the same images (the same per-pixel arithmetic); the FP32
+ * partial sums of the two norms are taken in a different order.  Timed
+ * before the first iteration of the first ADM call with that width, where
+ * the step changes nothing.  Host memory: us has DECT_TV_VARIANTS elements.
+ */
+#define DECT_TV_VARIANTS 2
+dect_status dect_plan_get_tv_tuning(const dect_plan *plan, int images, int *choice,
+                                    float us[DECT_TV_VARIANTS]);
+
+/* Fix the TV-step variant for batch width `images`, or -1 to time the
+ * candidates again on the next ADM call with that width. */
+dect_status dect_plan_set_tv_tuning(dect_plan *plan, int images, int choice);
 
 /* Number of kernels libdect has launched in this process so far (kernel
  * launches plus the kernel nodes of every graph launch). */

@@ -126,6 +126,8 @@ _SIGS = {
     "dect_plan_set_tuning": (C.c_int, [_P, C.c_int, C.c_int]),
     "dect_plan_get_fwd_tuning": (C.c_int, [_P, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_float)]),
     "dect_plan_set_fwd_tuning": (C.c_int, [_P, C.c_int, C.c_int]),
+    "dect_plan_get_tv_tuning": (C.c_int, [_P, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_float)]),
+    "dect_plan_set_tv_tuning": (C.c_int, [_P, C.c_int, C.c_int]),
     "dect_status_string": (C.c_char_p, [C.c_int]),
     "dect_last_error": (C.c_char_p, []),
     "dect_version": (C.c_int, []),
@@ -264,6 +266,17 @@ class Plan:
     def set_fwd_tuning(self, images: int, choice: int):
         """Force the A variant for a batch width (-1: re-time on the next ADM call)."""
         _check(load().dect_plan_set_fwd_tuning(self._h, images, choice), "dect_plan_set_fwd_tuning")
+
+    def tv_tuning(self, images: int):
+        """(chosen TV-step variant, [median us of each variant]) for a batch width; see dect.h."""
+        ch = C.c_int(-1)
+        us = (C.c_float * TV_VARIANTS)()
+        _check(load().dect_plan_get_tv_tuning(self._h, images, C.byref(ch), us), "dect_plan_get_tv_tuning")
+        return ch.value, list(us)
+
+    def set_tv_tuning(self, images: int, choice: int):
+        """Force the TV-step variant for a batch width (-1: re-time on the next ADM call)."""
+        _check(load().dect_plan_set_tv_tuning(self._h, images, choice), "dect_plan_set_tv_tuning")
 
     def table(self):
         """(rowptr int64 [M+1], pix int32 [nnz], len float32 [nnz]) as numpy arrays."""
@@ -421,6 +434,7 @@ def fbp(plan: Plan, m, x=None, stream=None):
 BB1, CAUCHY = 0, 1
 BWD_VARIANTS = 8                        # DECT_BWD_VARIANTS in include/dect.h
 FWD_VARIANTS = 3                        # DECT_FWD_VARIANTS in include/dect.h
+TV_VARIANTS = 2                         # DECT_TV_VARIANTS in include/dect.h
 
 
 @dataclasses.dataclass

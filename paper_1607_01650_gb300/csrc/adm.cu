@@ -172,6 +172,102 @@ struct TvShape {
     static constexpr size_t SMEM = XS_BYTES > RED_BYTES ? XS_BYTES : RED_BYTES;
 };
 
+// Per-pixel work of the TV step at pixel (i, j), offset o of the thread's
+// vector: fc, gc are the stepped f and the G of the pixel, fu, gu those of
+// the pixel above and fl, gl those of the pixel to the left (the pixel's own
+// on the first row / column); l0, l1 the multiplier rows read for the pixel
+// (p^{k-1} with xi = rho, else lambda^{k-1}).  Adds |grad f| (Eq. (2)) to
+// acc and, unless final_pass, applies the multiplier step (Eq. (7)), the
+// z-shrink (Eq. (8)) and writes p (and, without the xi = rho shortcut,
+// lambda and z).  Both TV kernels call it, so they compute the same values.
+template <int NB, bool JOINT>
+__device__ __forceinline__ void tv_pixel(const Vec<Batch<NB>::VW> &fc, const Vec<Batch<NB>::VW> &gc,
+                                         const Vec<Batch<NB>::VW> &fu, const Vec<Batch<NB>::VW> &gu_,
+                                         const Vec<Batch<NB>::VW> &fl, const Vec<Batch<NB>::VW> &gl_,
+                                         Vec<Batch<NB>::VW> l0, Vec<Batch<NB>::VW> l1, int i, int j, int64_t o,
+                                         int64_t sN, const Vec<Batch<NB>::VW> &a, int k, float inv_rho,
+                                         const AdmConst &C, int final_pass, float *__restrict__ lam,
+                                         float *__restrict__ z, float *__restrict__ p, Vec<Batch<NB>::VW> &acc)
+{
+    constexpr int VW = Batch<NB>::VW;
+    // With xi = rho the multiplier step of Eq. (7) and
+    // p^{k-1} = rho(grad f^{k-1} - z^k) - lambda^{k-1} give
+    // lambda^k = xi alpha^{k-1} grad G^{k-1} - p^{k-1}: neither lambda nor z
+    // has to be stored (l0, l1 carry p^{k-1} then; otherwise lambda^{k-1}).
+    Vec<VW> z0, z1;
+    if (!final_pass && !C.xi_is_rho && k > 0) {
+        z0 = ld_v<VW>(z + o);
+        z1 = ld_v<VW>(z + sN + o);
+    }
+    Vec<VW> p0, p1, d0, d1;
+#pragma unroll
+    for (int c = 0; c < VW; ++c) {
+        d0.v[c] = fc.v[c] - fu.v[c];   // Eq. (2), 0 on the first row
+        d1.v[c] = fc.v[c] - fl.v[c];   // Eq. (2), 0 on the first column
+    }
+    if (JOINT) {  // one norm per slice over both channels (c, c + 1)
+#pragma unroll
+        for (int c = 0; c < VW; c += 2)
+            acc.v[c] += sqrtf(d0.v[c] * d0.v[c] + d1.v[c] * d1.v[c] + d0.v[c + 1] * d0.v[c + 1] +
+                              d1.v[c + 1] * d1.v[c + 1]);
+    } else {
+#pragma unroll
+        for (int c = 0; c < VW; ++c) acc.v[c] += sqrtf(d0.v[c] * d0.v[c] + d1.v[c] * d1.v[c]);
+    }
+    if (!final_pass) {
+#pragma unroll
+        for (int c = 0; c < VW; ++c) {
+            const float g0 = d0.v[c], g1 = d1.v[c];
+            float a0, a1;
+            if (C.xi_is_rho) {
+                a0 = 0.f;
+                a1 = 0.f;
+                if (k > 0) {
+                    const float dg0 = i > 0 ? gc.v[c] - gu_.v[c] : 0.f;
+                    const float dg1 = j > 0 ? gc.v[c] - gl_.v[c] : 0.f;
+                    a0 = C.xi * a.v[c] * dg0 - l0.v[c];
+                    a1 = C.xi * a.v[c] * dg1 - l1.v[c];
+                }
+            } else {
+                a0 = l0.v[c];
+                a1 = l1.v[c];
+                if (k > 0) {  // lambda^k = lambda^{k-1} - xi (grad f^k - z^k), Eq. (7)
+                    a0 -= C.xi * (g0 - z0.v[c]);
+                    a1 -= C.xi * (g1 - z1.v[c]);
+                }
+            }
+            l0.v[c] = a0;  // lambda^k
+            l1.v[c] = a1;
+            if (!JOINT) {
+                float s0, s1;
+                shrink2(g0 - a0 * inv_rho, g1 - a1 * inv_rho, inv_rho, s0, s1);
+                z0.v[c] = s0;
+                z1.v[c] = s1;
+            }
+        }
+        if (JOINT) {
+#pragma unroll
+            for (int c = 0; c < VW; c += 2)
+                shrink4(d0.v[c] - l0.v[c] * inv_rho, d1.v[c] - l1.v[c] * inv_rho,
+                        d0.v[c + 1] - l0.v[c + 1] * inv_rho, d1.v[c + 1] - l1.v[c + 1] * inv_rho,
+                        inv_rho, z0.v[c], z1.v[c], z0.v[c + 1], z1.v[c + 1]);
+        }
+#pragma unroll
+        for (int c = 0; c < VW; ++c) {
+            p0.v[c] = C.rho * (d0.v[c] - z0.v[c]) - l0.v[c];
+            p1.v[c] = C.rho * (d1.v[c] - z1.v[c]) - l1.v[c];
+        }
+        if (!C.xi_is_rho) {
+            st_v<VW>(lam + o, l0);
+            st_v<VW>(lam + sN + o, l1);
+            st_v<VW>(z + o, z0);
+            st_v<VW>(z + sN + o, z1);
+        }
+        st_v<VW>(p + o, p0);
+        st_v<VW>(p + sN + o, p1);
+    }
+}
+
 template <int NB, bool JOINT>
 __global__ void __launch_bounds__(TvShape<NB>::BLK) k_tv(const float *__restrict__ f_in, float *__restrict__ f_out,
                                                        const float *__restrict__ G, float *__restrict__ lam,
@@ -263,83 +359,8 @@ __global__ void __launch_bounds__(TvShape<NB>::BLK) k_tv(const float *__restrict
                     fl = fc;
                     gl_ = gc;
                 }
-                // With xi = rho the multiplier step of Eq. (7) and
-                // p^{k-1} = rho(grad f^{k-1} - z^k) - lambda^{k-1} give
-                // lambda^k = xi alpha^{k-1} grad G^{k-1} - p^{k-1}: neither
-                // lambda nor z has to be stored (l0, l1 carry p^{k-1} then;
-                // otherwise lambda^{k-1}).
-                Vec<VW> l0 = lc0, l1 = lc1, z0, z1;
-                if (!final_pass && !C.xi_is_rho && k > 0) {
-                    z0 = ld_v<VW>(z + o);
-                    z1 = ld_v<VW>(z + sN + o);
-                }
-                Vec<VW> p0, p1, d0, d1;
-#pragma unroll
-                for (int c = 0; c < VW; ++c) {
-                    d0.v[c] = fc.v[c] - fu.v[c];   // Eq. (2), 0 on the first row
-                    d1.v[c] = fc.v[c] - fl.v[c];   // Eq. (2), 0 on the first column
-                }
-                if (JOINT) {  // one norm per slice over both channels (c, c + 1)
-#pragma unroll
-                    for (int c = 0; c < VW; c += 2)
-                        acc[0].v[c] += sqrtf(d0.v[c] * d0.v[c] + d1.v[c] * d1.v[c] + d0.v[c + 1] * d0.v[c + 1] +
-                                             d1.v[c + 1] * d1.v[c + 1]);
-                } else {
-#pragma unroll
-                    for (int c = 0; c < VW; ++c) acc[0].v[c] += sqrtf(d0.v[c] * d0.v[c] + d1.v[c] * d1.v[c]);
-                }
-                if (!final_pass) {
-#pragma unroll
-                    for (int c = 0; c < VW; ++c) {
-                        const float g0 = d0.v[c], g1 = d1.v[c];
-                        float a0, a1;
-                        if (C.xi_is_rho) {
-                            a0 = 0.f;
-                            a1 = 0.f;
-                            if (k > 0) {
-                                const float dg0 = i > 0 ? gc.v[c] - gu_.v[c] : 0.f;
-                                const float dg1 = j > 0 ? gc.v[c] - gl_.v[c] : 0.f;
-                                a0 = C.xi * a.v[c] * dg0 - l0.v[c];
-                                a1 = C.xi * a.v[c] * dg1 - l1.v[c];
-                            }
-                        } else {
-                            a0 = l0.v[c];
-                            a1 = l1.v[c];
-                            if (k > 0) {  // lambda^k = lambda^{k-1} - xi (grad f^k - z^k), Eq. (7)
-                                a0 -= C.xi * (g0 - z0.v[c]);
-                                a1 -= C.xi * (g1 - z1.v[c]);
-                            }
-                        }
-                        l0.v[c] = a0;  // lambda^k
-                        l1.v[c] = a1;
-                        if (!JOINT) {
-                            float s0, s1;
-                            shrink2(g0 - a0 * inv_rho, g1 - a1 * inv_rho, inv_rho, s0, s1);
-                            z0.v[c] = s0;
-                            z1.v[c] = s1;
-                        }
-                    }
-                    if (JOINT) {
-#pragma unroll
-                        for (int c = 0; c < VW; c += 2)
-                            shrink4(d0.v[c] - l0.v[c] * inv_rho, d1.v[c] - l1.v[c] * inv_rho,
-                                    d0.v[c + 1] - l0.v[c + 1] * inv_rho, d1.v[c + 1] - l1.v[c + 1] * inv_rho,
-                                    inv_rho, z0.v[c], z1.v[c], z0.v[c + 1], z1.v[c + 1]);
-                    }
-#pragma unroll
-                    for (int c = 0; c < VW; ++c) {
-                        p0.v[c] = C.rho * (d0.v[c] - z0.v[c]) - l0.v[c];
-                        p1.v[c] = C.rho * (d1.v[c] - z1.v[c]) - l1.v[c];
-                    }
-                    if (!C.xi_is_rho) {
-                        st_v<VW>(lam + o, l0);
-                        st_v<VW>(lam + sN + o, l1);
-                        st_v<VW>(z + o, z0);
-                        st_v<VW>(z + sN + o, z1);
-                    }
-                    st_v<VW>(p + o, p0);
-                    st_v<VW>(p + sN + o, p1);
-                }
+                tv_pixel<NB, JOINT>(fc, gc, fu, gu_, fl, gl_, lc0, lc1, i, j, o, sN, a, k, inv_rho, C, final_pass,
+                                    lam, z, p, acc[0]);
             }
             fup = fc;
             gup = gc;
@@ -362,6 +383,201 @@ __global__ void __launch_bounds__(TvShape<NB>::BLK) k_tv(const float *__restrict
                                      reinterpret_cast<double *>(sbuf)) &&
         threadIdx.x == 0)
         D.ctr[C_COUNT] = 0u;  // every block has left the tile loop: reset the tile counter
+}
+
+// ---------------------------------------------------------------------------
+// The same TV step with its rows staged by the TMA (TV variant 1).  The
+// image is cut into `strips` strips of Wd <= SLOTS - 1 columns; a strip row
+// is held together with the column to its left (computed, never written) in
+// SLOTS slots of NB floats.  The (strip, row) pairs, strip by strip, are
+// split into equal contiguous ranges, one per block, so there is no tile
+// counter and no tail of unequal tiles.  The last warp of the block is the
+// producer: its lane 0 streams the rows of the block's range -- f, G and the
+// two multiplier rows, each one contiguous run of at most SLOTS x NB floats
+// -- into a ring of STAGES shared-memory stages with 1-D bulk copies that
+// complete on the stage's `full` mbarrier; for the row above the range only
+// f and G are copied.  The consumer threads take the rows in order: the
+// pixel and its left neighbour from the stage, the pixel above from their
+// own registers (the previous row); each consumer warp then releases the
+// stage by one arrival on its `empty` mbarrier.  No block-wide barrier per
+// row, STAGES rows in flight.  Per pixel the arithmetic is k_tv's (tv_pixel,
+// the same f step), so both variants give the same images; only the order
+// of the FP32 partial sums of the two norms differs.  Every wait is bounded:
+// one that runs out sets bit 1 of *D.bad (DECT_ERR_TIMEOUT), ends the loops
+// of the whole block and the producer then waits (bounded) for its copies
+// in flight.  Needs 16-byte pixels (NB >= 4) for the copies' alignment.
+// ---------------------------------------------------------------------------
+template <int NB>
+struct TvTmaShape {
+    static constexpr int VW = Batch<NB>::VW, CPB = Batch<NB>::CPB;
+    static constexpr int BLK = NB > 32 ? 512 : 256;  // consumer threads
+    static constexpr int THREADS = BLK + 32;          // + the producer warp
+    static constexpr int SLOTS = BLK / CPB;           // a strip's columns + the column to their left
+    static constexpr int STAGES = 4;
+    static constexpr int RF = SLOTS * NB;             // floats of one array row of a stage
+    static constexpr size_t SMEM = sizeof(float) * STAGES * 4 * RF;
+    static_assert(NB >= 4, "the bulk copies need 16-byte pixels");
+};
+
+constexpr unsigned kTvPolls = 1u << 22;
+
+// wait for phase `parity` of `bar`; false once *fail is set or after
+// kTvPolls polls (then *fail is set and the timeout recorded in bit 1 of *bad)
+__device__ __forceinline__ bool tv_wait(uint64_t *bar, unsigned parity, volatile int *fail, int *bad)
+{
+    for (unsigned i = 0; i < kTvPolls; ++i) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if ((i & 255u) == 255u && *fail) return false;
+    }
+    *fail = 1;
+    atomicOr(bad, 2);
+    return false;
+}
+
+// strip layout of an n x n image for SLOTS slots per strip row
+__host__ __device__ inline int tv_strips(int n, int slots) { return (n + slots - 2) / (slots - 1); }
+
+template <int NB, bool JOINT>
+__global__ void __launch_bounds__(TvTmaShape<NB>::THREADS) k_tv_tma(
+    const float *__restrict__ f_in, float *__restrict__ f_out, const float *__restrict__ G, float *__restrict__ lam,
+    float *__restrict__ z, float *__restrict__ p, float *__restrict__ r, const float *__restrict__ q, AdmConst C,
+    AdmDev D, int final_pass)
+{
+    using S = TvTmaShape<NB>;
+    constexpr int VW = S::VW, CPB = S::CPB, SLOTS = S::SLOTS, NST = S::STAGES, RF = S::RF;
+    extern __shared__ __align__(128) float ring[];  // [stage][f | G | l0 | l1][slot][NB]
+    __shared__ __align__(8) uint64_t full[NST], empty[NST];
+    __shared__ int fail;
+    __shared__ double rsm[reduce_smem_doubles<NB, S::BLK>(2)];
+    const int k = *D.k;
+    const float inv_rho = 1.0f / C.rho;
+    const bool clamp = C.nonneg && k > 0;
+    const int vl = threadIdx.x % CPB;
+    Vec<VW> a;
+#pragma unroll
+    for (int c = 0; c < VW; ++c) a.v[c] = (float)D.alpha[vl * VW + c];
+    Vec<VW> acc[2];
+    acc[0].zero();
+    acc[1].zero();
+    const int64_t sN = C.N * NB;  // component stride of lam, z, p
+    const float *lsrc = C.xi_is_rho ? p : lam;
+    const bool need_l = !final_pass;
+    const int strips = tv_strips(C.n, SLOTS), Wd = (C.n + strips - 1) / strips;
+    const int64_t T = (int64_t)strips * C.n;  // (strip, row) pairs
+    const int64_t t0 = T * blockIdx.x / gridDim.x, t1 = T * (blockIdx.x + 1) / gridDim.x;
+    const int halo0 = (t1 > t0 && t0 % C.n > 0) ? 1 : 0;  // the row above the range
+    const int L = (int)(t1 - t0) + halo0;                  // rows this block streams
+    // row `it` of the block: strip s, image row i; `halo`: the row above the range
+    auto row_of = [&](int it, int &s, int &i, bool &halo) {
+        halo = it < halo0;
+        const int64_t t = halo ? t0 : t0 + it - halo0;
+        s = (int)(t / C.n);
+        i = (int)(t % C.n) - (halo ? 1 : 0);
+    };
+    if (threadIdx.x == 0) {
+        for (int st = 0; st < NST; ++st) {
+            mbar_init(&full[st], 1);
+            mbar_init(&empty[st], S::BLK / 32);
+        }
+        fail = 0;
+    }
+    __syncthreads();
+    if (threadIdx.x >= S::BLK) {
+        if (threadIdx.x == S::BLK) {  // producer
+            int issued = 0;
+            for (int it = 0; it < L; ++it) {
+                const int st = it % NST;
+                if (it >= NST && !tv_wait(&empty[st], ((it / NST) - 1) & 1, &fail, D.bad)) break;
+                int s, i;
+                bool halo;
+                row_of(it, s, i, halo);
+                const int jl = s * Wd - 1;  // column of slot 0
+                const int c0 = max(jl, 0), c1 = min(s * Wd + Wd - 1, C.n - 1);
+                const unsigned bytes = (unsigned)((c1 - c0 + 1) * NB * sizeof(float));
+                const bool wl = need_l && !halo;
+                mbar_arrive_expect_tx(&full[st], wl ? 4 * bytes : 2 * bytes);
+                float *dst = ring + (size_t)st * 4 * RF + (size_t)(c0 - jl) * NB;
+                const int64_t go = ((int64_t)i * C.n + c0) * NB;
+                bulk_g2s(dst, f_in + go, bytes, &full[st]);
+                bulk_g2s(dst + RF, G + go, bytes, &full[st]);
+                if (wl) {
+                    bulk_g2s(dst + 2 * RF, lsrc + go, bytes, &full[st]);
+                    bulk_g2s(dst + 3 * RF, lsrc + sN + go, bytes, &full[st]);
+                }
+                issued = it + 1;
+            }
+            // the copies of the last rows must have landed before the block
+            // leaves (they have, unless a consumer gave up waiting)
+            for (int it = max(issued - NST, 0); it < issued; ++it)
+                mbar_wait_bounded(&full[it % NST], (it / NST) & 1, kTvPolls);
+        }
+    } else {
+        const int slot = threadIdx.x / CPB;
+        Vec<VW> fup, gup;
+        fup.zero();
+        gup.zero();
+        for (int it = 0; it < L; ++it) {
+            const int st = it % NST;
+            if (!tv_wait(&full[st], (it / NST) & 1, &fail, D.bad)) break;
+            int s, i;
+            bool halo;
+            row_of(it, s, i, halo);
+            const int j = s * Wd - 1 + slot;
+            const bool colok = slot <= Wd && j >= 0 && j < C.n;
+            const float *sf = ring + (size_t)st * 4 * RF + slot * NB + vl * VW;
+            Vec<VW> fc, gc;
+            fc.zero();
+            gc.zero();
+            if (colok) {
+                fc = ld_v<VW>(sf);
+                gc = ld_v<VW>(sf + RF);
+#pragma unroll
+                for (int c = 0; c < VW; ++c) fc.v[c] = nonneg_step(fc.v[c], a.v[c], gc.v[c], clamp);
+            }
+            if (colok && slot > 0 && !halo) {
+                const int64_t o = ((int64_t)i * C.n + j) * NB + vl * VW;
+                st_v<VW>(f_out + o, fc);
+                Vec<VW> fu = fc, gu_ = gc, fl = fc, gl_ = gc, l0, l1;
+                if (i > 0) {
+                    fu = fup;
+                    gu_ = gup;
+                }
+                if (j > 0) {
+                    fl = ld_v<VW>(sf - NB);
+                    gl_ = ld_v<VW>(sf - NB + RF);
+#pragma unroll
+                    for (int c = 0; c < VW; ++c) fl.v[c] = nonneg_step(fl.v[c], a.v[c], gl_.v[c], clamp);
+                }
+                l0.zero();
+                l1.zero();
+                if (need_l) {
+                    l0 = ld_v<VW>(sf + 2 * RF);
+                    l1 = ld_v<VW>(sf + 3 * RF);
+                }
+                tv_pixel<NB, JOINT>(fc, gc, fu, gu_, fl, gl_, l0, l1, i, j, o, sN, a, k, inv_rho, C, final_pass,
+                                    lam, z, p, acc[0]);
+            }
+            fup = fc;
+            gup = gc;
+            __syncwarp();
+            if ((threadIdx.x & 31) == 0) mbar_arrive(&empty[st]);
+        }
+    }
+    // r pass on the consumer threads only: the reduction below sums the
+    // partials of the first BLK threads
+    const int64_t rn = C.nonneg || threadIdx.x >= S::BLK ? 0 : C.M * CPB;  // with the projection k_fwd rebuilds r
+    const int64_t stride = (int64_t)gridDim.x * S::BLK;
+    for (int64_t t = (int64_t)blockIdx.x * S::BLK + threadIdx.x; t < rn; t += stride) {
+        float *rp = r + t * VW;
+        Vec<VW> rv = ld_v<VW>(rp), qv = ld_v<VW>(q + t * VW);
+#pragma unroll
+        for (int c = 0; c < VW; ++c) {
+            rv.v[c] = fmaf(-a.v[c], qv.v[c], rv.v[c]);
+            acc[1].v[c] = fmaf(rv.v[c], rv.v[c], acc[1].v[c]);
+        }
+        st_v<VW>(rp, rv);
+    }
+    reduce_images<NB, 2, S::BLK>(acc, part_of<NB>(D, C_TV), D.red + R_TV * NB, D.ctr + C_TV, rsm);
 }
 
 // G = mu A^T r + grad^T p over the pixel-major table.  A block of BLK
@@ -861,6 +1077,8 @@ struct Work {
     size_t win_smem;  // its dynamic shared memory
     int bwd;          // A^T variant in use
     int fwd;          // A variant in use
+    int tv;           // TV-step variant in use (0 k_tv, 1 k_tv_tma)
+    int tv_grid;      // blocks of k_tv_tma
 };
 
 constexpr size_t kWinSmemMax = 210 * 1024;
@@ -1047,9 +1265,105 @@ cudaError_t tune_fwd(const dect_plan *P, Work &W, const AdmConst &C, cudaStream_
     return cudaSuccess;
 }
 
+// TV-step variants (autotuner candidates): 0 k_tv (tiles claimed from a
+// counter, rows exchanged through shared memory, one barrier per row); 1
+// k_tv_tma (rows streamed by bulk copies into a ring of stages, NB >= 4).
+// Both give the same images.
+constexpr int kTvVariants = DECT_TV_VARIANTS;
+
+// Prepare k_tv_tma for this width: its shared memory, and the grid (blocks
+// that fit on an SM x SMs, at most kGrid, whose partials the reduction holds).
+template <int NB>
+cudaError_t setup_tv_tma(Work &W)
+{
+    W.tv_grid = 0;
+    if constexpr (NB >= 4) {
+        using T = TvTmaShape<NB>;
+        cudaError_t e = cudaFuncSetAttribute(k_tv_tma<NB, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)T::SMEM);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(k_tv_tma<NB, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)T::SMEM);
+        int per_sm = 0;
+        if (e == cudaSuccess)
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tv_tma<NB, false>, T::THREADS, T::SMEM);
+        if (e != cudaSuccess) return e;
+        W.tv_grid = std::min(std::max(per_sm, 0) * kSMs, kGrid);
+    }
+    return cudaSuccess;
+}
+
+template <int NB>
+void launch_tv(const Work &W, const AdmConst &C, int par, int final_pass, cudaStream_t s);
+
+// Time the TV-step variants (CUDA events, median of three launches after
+// one warm-up) and keep the faster in the plan.  Called before the first
+// iteration (k = 0, alpha = 0), where the step is idempotent: f[1] = f[0],
+// r is unchanged and p (lambda, z) and the two norms are those the first
+// iteration computes again, so timing changes no result.
+template <int NB>
+cudaError_t tune_tv(const dect_plan *P, Work &W, const AdmConst &C, cudaStream_t s)
+{
+    cudaError_t e = setup_tv_tma<NB>(W);
+    if (e != cudaSuccess) return e;
+    const int idx = nb_index<NB>();
+    const bool tma_ok = NB >= 4 && W.tv_grid > 0;
+    if (P->tv_choice[idx] >= 0) {
+        W.tv = (P->tv_choice[idx] == 1 && tma_ok) ? 1 : 0;
+        return cudaSuccess;
+    }
+    cudaEvent_t a = nullptr, b = nullptr;
+    e = cudaEventCreate(&a);
+    if (e == cudaSuccess) e = cudaEventCreate(&b);
+    int best = 0;
+    float best_us = 1e30f;
+    for (int v = 0; v < kTvVariants && e == cudaSuccess; ++v) {
+        P->tv_us[idx][v] = -1.f;
+        if (v == 1 && !tma_ok) continue;
+        W.tv = v;
+        launch_tv<NB>(W, C, 0, 0, s);
+        count_launches(1);
+        float t[3];
+        for (int k = 0; k < 3 && e == cudaSuccess; ++k) {
+            e = cudaEventRecord(a, s);
+            launch_tv<NB>(W, C, 0, 0, s);
+            count_launches(1);
+            if (e == cudaSuccess) e = cudaEventRecord(b, s);
+            if (e == cudaSuccess) e = cudaEventSynchronize(b);
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&t[k], a, b);
+        }
+        if (e != cudaSuccess) break;
+        std::sort(t, t + 3);
+        const float us = t[1] * 1e3f;
+        P->tv_us[idx][v] = us;
+        if (us < best_us) {
+            best_us = us;
+            best = v;
+        }
+    }
+    if (a) cudaEventDestroy(a);
+    if (b) cudaEventDestroy(b);
+    if (e == cudaSuccess) e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    P->tv_choice[idx] = best;
+    W.tv = best;
+    return cudaSuccess;
+}
+
 template <int NB>
 void launch_tv(const Work &W, const AdmConst &C, int par, int final_pass, cudaStream_t s)
 {
+    if constexpr (NB >= 4) {
+        if (W.tv == 1) {
+            using T = TvTmaShape<NB>;
+            if (C.joint)
+                k_tv_tma<NB, true><<<W.tv_grid, T::THREADS, T::SMEM, s>>>(W.f[par], W.f[1 - par], W.G, W.lam, W.z,
+                                                                          W.p, W.r, W.q, C, W.D, final_pass);
+            else
+                k_tv_tma<NB, false><<<W.tv_grid, T::THREADS, T::SMEM, s>>>(W.f[par], W.f[1 - par], W.G, W.lam, W.z,
+                                                                           W.p, W.r, W.q, C, W.D, final_pass);
+            return;
+        }
+    }
     using S = TvShape<NB>;
     const int ntiles = ((C.n + S::W - 1) / S::W) * ((C.n + S::H - 1) / S::H);
     const int grid = std::max(1, std::min(ntiles, kGrid));  // the partials hold kGrid blocks
@@ -1283,8 +1597,10 @@ dect_status iterate(const dect_plan *P, const AdmConst &C, Work W, char *base, f
                         W2.bwd = 1;
                         W2.fwd = 0;
                         // time the A and A^T variants on the empty workspace, before the state arrives
+                        W2.tv = 0;
                         err = tune_bwd<NB2>(P, W2, C, cs);
                         if (err == cudaSuccess) err = tune_fwd<NB2>(P, W2, C, cs);
+                        if (err == cudaSuccess) err = tune_tv<NB2>(P, W2, C, cs);
                     }
                     if (err == cudaSuccess)
                         err = cudaMemcpyAsync(W2.map, map.data(), sizeof(int) * NB2, cudaMemcpyHostToDevice, cs);
@@ -1402,6 +1718,10 @@ dect_status iterate(const dect_plan *P, const AdmConst &C, Work W, char *base, f
     if (rep)
         for (int j = 0; j < NB; ++j)
             if (hslot[j] >= 0) fill_report(rep[hslot[j]], NB, j, C, prm->mu, K, hred, hrel, hit, hconv);
+    if (hbad & 2) {
+        set_error_text("dect_adm_tv: a bounded wait of the TV step ran out");
+        return DECT_ERR_TIMEOUT;
+    }
     return (hbad & 1) ? DECT_ERR_NONFINITE : DECT_OK;
 }
 
@@ -1466,6 +1786,8 @@ dect_status run_chunk(const dect_plan *P, const float *m, float *x, int nimg,
     if ((e = cudaGetLastError()) != cudaSuccess) return fail(e);
     W.bwd = 1;
     if ((e = tune_bwd<NB>(P, W, C, s)) != cudaSuccess) return fail(e);
+    W.tv = 0;
+    if ((e = tune_tv<NB>(P, W, C, s)) != cudaSuccess) return fail(e);
     // (hbeta, hact and hslot are pageable: their copies have read them by now)
     return iterate<NB>(P, C, W, base, x, prm, rep, prof, s, 0);
 }

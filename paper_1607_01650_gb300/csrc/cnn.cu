@@ -310,11 +310,6 @@ __host__ __device__ constexpr int tc_fixed_bytes(int Cin, int BN, bool stream)
            BN * 4 /* bias */;
 }
 
-__device__ __forceinline__ void mbar_arrive(uint64_t *bar)
-{
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(smem_u32(bar)) : "memory");
-}
-
 // wait for phase `parity`, giving up after kTcPolls polls or once *fail is set
 __device__ __forceinline__ bool tc_wait(uint64_t *bar, unsigned parity, volatile int *fail)
 {

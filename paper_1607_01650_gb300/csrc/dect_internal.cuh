@@ -125,6 +125,9 @@ struct dect_plan {
     // The same for the A variant (k_fwd).
     mutable int fwd_choice[6];
     mutable float fwd_us[6][DECT_FWD_VARIANTS];
+    // The same for the TV step (k_tv or k_tv_tma).
+    mutable int tv_choice[6];
+    mutable float tv_us[6][DECT_TV_VARIANTS];
     // On-the-fly projector geometry (built on first use, see batch.cu): per
     // ray the point closest to the rotation axis and the unit direction
     // (otf_ray), the reciprocals of the direction (otf_inv); per view the

@@ -553,7 +553,7 @@ extern "C" dect_status dect_plan_create(const dect_geometry *geom, int device, d
     p->nb = geom->n_bins;
     p->N = (int64_t)p->n * p->n;
     p->M = (int64_t)p->nv * p->nb;
-    for (int k = 0; k < 6; ++k) p->bwd_choice[k] = p->fwd_choice[k] = -1;
+    for (int k = 0; k < 6; ++k) p->bwd_choice[k] = p->fwd_choice[k] = p->tv_choice[k] = -1;
 
     // ray end points on the host, FP64 (see file header)
     std::vector<RayPts> h(p->M);
@@ -768,7 +768,7 @@ extern "C" dect_status dect_plan_create_cone(const dect_cone_geometry *geom, int
     p->nb = geom->n_cols;
     p->N = (int64_t)geom->n * geom->n * geom->nz;
     p->M = (int64_t)geom->n_views * geom->n_rows * geom->n_cols;
-    for (int k = 0; k < 6; ++k) p->bwd_choice[k] = p->fwd_choice[k] = -1;
+    for (int k = 0; k < 6; ++k) p->bwd_choice[k] = p->fwd_choice[k] = p->tv_choice[k] = -1;
 
     // ray end points on the host, FP64 (ray (v, r, c) -> (v nr + r) nc + c)
     std::vector<RayPts3> h(p->M);
@@ -1006,5 +1006,26 @@ extern "C" dect_status dect_plan_set_fwd_tuning(dect_plan *p, int images, int ch
     if (idx < 0) return DECT_ERR_INVALID_ARG;
     p->fwd_choice[idx] = choice;
     for (int v = 0; v < DECT_FWD_VARIANTS; ++v) p->fwd_us[idx][v] = -1.f;
+    return DECT_OK;
+}
+
+extern "C" dect_status dect_plan_get_tv_tuning(const dect_plan *p, int images, int *choice,
+                                               float us[DECT_TV_VARIANTS])
+{
+    if (!p || !choice || !us) return DECT_ERR_INVALID_ARG;
+    const int idx = width_index(images);
+    if (idx < 0) return DECT_ERR_INVALID_ARG;
+    *choice = p->tv_choice[idx];
+    for (int v = 0; v < DECT_TV_VARIANTS; ++v) us[v] = p->tv_choice[idx] >= 0 ? p->tv_us[idx][v] : -1.f;
+    return DECT_OK;
+}
+
+extern "C" dect_status dect_plan_set_tv_tuning(dect_plan *p, int images, int choice)
+{
+    if (!p || choice < -1 || choice >= DECT_TV_VARIANTS) return DECT_ERR_INVALID_ARG;
+    const int idx = width_index(images);
+    if (idx < 0) return DECT_ERR_INVALID_ARG;
+    p->tv_choice[idx] = choice;
+    for (int v = 0; v < DECT_TV_VARIANTS; ++v) p->tv_us[idx][v] = -1.f;
     return DECT_OK;
 }

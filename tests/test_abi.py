@@ -75,6 +75,8 @@ def test_host_side_argument_checks(lib):
     assert L.dect_plan_create(C.byref(bad), 0, None, C.byref(out)) == 1
     assert L.dect_plan_destroy(None) == 0
     assert L.dect_plan_get_tuning(None, 2, None, None) == 1
+    assert L.dect_plan_get_tv_tuning(None, 2, None, None) == 1
+    assert L.dect_plan_set_tv_tuning(None, 2, 0) == 1
     assert L.dect_cnn_set_conv_path(None, 0) == 1
     assert L.dect_cnn_get_conv_path(None) == -1
     assert L.dect_cnn_check(None) == 1
@@ -115,6 +117,8 @@ def test_variant_count_matches_the_header():
     assert m and int(m.group(1)) == dect.BWD_VARIANTS
     m = re.search(r"#define\s+DECT_FWD_VARIANTS\s+(\d+)", open(HEADER).read())
     assert m and int(m.group(1)) == dect.FWD_VARIANTS
+    m = re.search(r"#define\s+DECT_TV_VARIANTS\s+(\d+)", open(HEADER).read())
+    assert m and int(m.group(1)) == dect.TV_VARIANTS
 
 
 def test_checked_library_exports_and_host_checks(lib):

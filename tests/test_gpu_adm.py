@@ -215,17 +215,20 @@ def test_paper_size_first_iterations():
             assert rel_l2(x[i, e], outs[i][0][e]) <= 1e-4
 
 
-@pytest.mark.parametrize("ns,joint", [(8, False), (6, True)])
-def test_narrowing_batch_matches_oracle(ns, joint):
+@pytest.mark.parametrize("ns,joint,tv", [(8, False, None), (6, True, None), (8, False, 1), (6, True, 1)])
+def test_narrowing_batch_matches_oracle(ns, joint, tv):
     """Channels whose relative-objective stop comes at different iterations
     (slices of very different dose): once half of a batch has stopped, the
     running channels continue in a batch half as wide.  Every channel ends as
     the oracle does at the channel's own iteration count, with the report of
-    that result."""
+    that result.  tv = 1: the TMA-staged TV step at every width that has it."""
     g = synth.tiny_geometry(n=48, nv=24, nb=72, px=1.0, sod=120.0, sdd=240.0)
     doses = [3e2, 1e6, 1e3, 3e5, 1e4, 3e3, 1e5, 5e2][:ns]
     slices = [synth.make_slice(g, seed=500 + i, i0=doses[i]) for i in range(ns)]
     plan = dect.Plan(g)
+    if tv is not None:
+        for w in (4, 8, 16, 32, 64):
+            plan.set_tv_tuning(w, tv)
     t = oracle.table(g)
     m = np.stack([s.m for s in slices]).astype(np.float32)
     prm = dect.AdmParams(mu=MU, rho=RHO, max_iter=3000, rel_obj_tol=1e-4, check_every=10, joint=joint)
@@ -316,6 +319,48 @@ def test_every_backprojector_variant(ns):
     dect.adm_tv(plan, torch.tensor(m, dtype=torch.float32, device="cuda"), prm)
     choice, us = plan.tuning(width)
     assert 0 <= choice < dect.BWD_VARIANTS and us[choice] > 0
+
+
+@pytest.mark.parametrize("ns", [1, 3, 32])
+@pytest.mark.parametrize("opts", [{}, {"joint": True}, {"nonneg": True}, {"xi": 128.0}, {"rule": dect.BB1}])
+def test_every_tv_variant(ns, opts):
+    """Each TV-step variant the autotuner can pick gives the oracle's result,
+    and both give the same images (the same per-pixel arithmetic; only the
+    FP32 partial sums of the norms, hence the reported objective, differ in
+    their order).  52 x 52 pixels: two strips of 26 columns at 64 channels,
+    more blocks than (strip, row) pairs, so some blocks get no rows."""
+    g = synth.tiny_geometry(n=52, nv=24, nb=80, px=1.0, sod=130.0, sdd=260.0)
+    slices = [synth.make_slice(g, seed=700 + i, i0=1e5) for i in range(ns)]
+    plan = dect.Plan(g)
+    t = oracle.table(g)
+    m = np.stack([s.m for s in slices])
+    width = min(64, 1 << (2 * ns - 1).bit_length())
+    K = 12
+    rule = opts.get("rule", dect.CAUCHY)
+    xi = opts.get("xi", 0.0)
+    joint, nonneg = opts.get("joint", False), opts.get("nonneg", False)
+    prm = dect.AdmParams(mu=MU, rho=RHO, xi=xi, step_rule=rule, max_iter=K, joint=joint, nonneg=nonneg)
+    xs, objs = [], []
+    for v in range(dect.TV_VARIANTS):
+        plan.set_tv_tuning(width, v)
+        x, reps = dect.adm_tv(plan, torch.tensor(m, dtype=torch.float32, device="cuda"), prm)
+        xs.append(x.cpu().numpy())
+        objs.append([r.objective for r in reps])
+        assert all(r.iters == K for r in reps)
+    assert np.array_equal(xs[0], xs[1])
+    np.testing.assert_allclose(objs[0], objs[1], rtol=1e-6)
+    for i in range(ns):
+        op = oracle.AdmParams(mu=MU, rho=RHO, xi=(xi if xi > 0 else None), step_rule=rule, max_iter=K,
+                              joint=joint, nonneg=nonneg)
+        xo, _ = oracle.adm_dual(t, m[i].astype(np.float32).astype(np.float64), op)
+        for e in range(2):
+            assert rel_l2(xs[1][i, e], xo[e]) <= 1e-4, (i, e)
+    plan.set_tv_tuning(width, -1)
+    dect.adm_tv(plan, torch.tensor(m, dtype=torch.float32, device="cuda"), prm)
+    choice, us = plan.tv_tuning(width)
+    assert 0 <= choice < dect.TV_VARIANTS and us[choice] > 0
+    if width >= 4:
+        assert all(u > 0 for u in us)
 
 
 def test_uneven_geometry_groups():
