@@ -172,6 +172,39 @@ struct TvShape {
     static constexpr size_t SMEM = XS_BYTES > RED_BYTES ? XS_BYTES : RED_BYTES;
 };
 
+// r <- r - alpha q over the rays' vectors first, first + stride, ... < rn
+// (VW channels each, those of the thread's alpha), adding |r|^2 to acc.
+// U vectors' loads are issued together, so the pass is not one load latency
+// per vector; the sum runs in the same order as a plain loop.
+template <int VW, int U = 4>
+__device__ __forceinline__ void r_step(float *__restrict__ r, const float *__restrict__ q, int64_t rn, int64_t first,
+                                       int64_t stride, const Vec<VW> &a, Vec<VW> &acc)
+{
+    for (int64_t t0 = first; t0 < rn; t0 += U * stride) {
+        Vec<VW> rv[U], qv[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int64_t t = t0 + u * stride;
+            if (t < rn) {
+                rv[u] = ld_v<VW>(r + t * VW);
+                qv[u] = ld_v<VW>(q + t * VW);
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int64_t t = t0 + u * stride;
+            if (t < rn) {
+#pragma unroll
+                for (int c = 0; c < VW; ++c) {
+                    rv[u].v[c] = fmaf(-a.v[c], qv[u].v[c], rv[u].v[c]);
+                    acc.v[c] = fmaf(rv[u].v[c], rv[u].v[c], acc.v[c]);
+                }
+                st_v<VW>(r + t * VW, rv[u]);
+            }
+        }
+    }
+}
+
 // Per-pixel work of the TV step at pixel (i, j), offset o of the thread's
 // vector: fc, gc are the stepped f and the G of the pixel, fu, gu those of
 // the pixel above and fl, gl those of the pixel to the left (the pixel's own
@@ -368,17 +401,7 @@ __global__ void __launch_bounds__(TvShape<NB>::BLK) k_tv(const float *__restrict
         __syncthreads();  // the next tile's first row reuses the exchange buffer (and s_tile)
     }
     const int64_t rn = C.nonneg ? 0 : C.M * CPB;  // with the projection r is rebuilt by k_fwd
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < rn; t += stride) {
-        float *rp = r + t * VW;
-        Vec<VW> rv = ld_v<VW>(rp), qv = ld_v<VW>(q + t * VW);
-#pragma unroll
-        for (int c = 0; c < VW; ++c) {
-            rv.v[c] = fmaf(-a.v[c], qv.v[c], rv.v[c]);
-            acc[1].v[c] = fmaf(rv.v[c], rv.v[c], acc[1].v[c]);
-        }
-        st_v<VW>(rp, rv);
-    }
+    r_step<VW>(r, q, rn, (int64_t)blockIdx.x * blockDim.x + threadIdx.x, (int64_t)gridDim.x * blockDim.x, a, acc[1]);
     if (reduce_images<NB, 2, S::BLK>(acc, part_of<NB>(D, C_TV), D.red + R_TV * NB, D.ctr + C_TV,
                                      reinterpret_cast<double *>(sbuf)) &&
         threadIdx.x == 0)
@@ -566,17 +589,7 @@ __global__ void __launch_bounds__(TvTmaShape<NB>::THREADS) k_tv_tma(
     // r pass on the consumer threads only: the reduction below sums the
     // partials of the first BLK threads
     const int64_t rn = C.nonneg || threadIdx.x >= S::BLK ? 0 : C.M * CPB;  // with the projection k_fwd rebuilds r
-    const int64_t stride = (int64_t)gridDim.x * S::BLK;
-    for (int64_t t = (int64_t)blockIdx.x * S::BLK + threadIdx.x; t < rn; t += stride) {
-        float *rp = r + t * VW;
-        Vec<VW> rv = ld_v<VW>(rp), qv = ld_v<VW>(q + t * VW);
-#pragma unroll
-        for (int c = 0; c < VW; ++c) {
-            rv.v[c] = fmaf(-a.v[c], qv.v[c], rv.v[c]);
-            acc[1].v[c] = fmaf(rv.v[c], rv.v[c], acc[1].v[c]);
-        }
-        st_v<VW>(rp, rv);
-    }
+    r_step<VW>(r, q, rn, (int64_t)blockIdx.x * S::BLK + threadIdx.x, (int64_t)gridDim.x * S::BLK, a, acc[1]);
     reduce_images<NB, 2, S::BLK>(acc, part_of<NB>(D, C_TV), D.red + R_TV * NB, D.ctr + C_TV, rsm);
 }
 
@@ -632,7 +645,7 @@ __global__ void __launch_bounds__(BLK) k_bwd(const int64_t *__restrict__ colptr,
                     out.v[c] = fmaf(C.mu, acc.v[c], gt);
                     nrm[0].v[c] = fmaf(out.v[c], out.v[c], nrm[0].v[c]);
                 }
-                st_v<VW>(G + o, out);
+                st_keep<VW>(G + o, out, pol);
             }
         }
     }
@@ -794,7 +807,7 @@ __global__ void __launch_bounds__(kWinBlock, 1) k_bwd_win(WinArgs A, const float
                 out.v[c] = fmaf(C.mu, acc.v[c], gt);
                 nrm[0].v[c] = fmaf(out.v[c], out.v[c], nrm[0].v[c]);
             }
-            st_v<VW>(G + o, out);
+            st_keep<VW>(G + o, out, l2_evict_last_policy());
         }
         __syncthreads();  // every read of this stage precedes its next copies
     }
@@ -884,25 +897,38 @@ __global__ void __launch_bounds__(BLK) k_fwd(const int64_t *__restrict__ rowptr,
     Vec<VW> nrm[2];
     nrm[0].zero();
     nrm[1].zero();
+    const unsigned long long pol = l2_evict_last_policy();
     if (MODE == 1) {
-        const int64_t row = (int64_t)C.n * NB;
-        for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < C.N * CPB;
-             t += (int64_t)gridDim.x * blockDim.x) {
-            const int64_t pix = t / CPB;
-            const int i = (int)(pix / C.n), j = (int)(pix % C.n);
-            const int64_t o = pix * NB + (t % CPB) * VW;
-            Vec<VW> gc = ld_v<VW>(src + o), gu, gl;
-            if (i > 0) gu = ld_v<VW>(src + o - row); else gu = gc;
-            if (j > 0) gl = ld_v<VW>(src + o - NB); else gl = gc;
+        // |grad G|^2, U pixels' loads issued together (the sum in plain loop order)
+        constexpr int U = 2;
+        const int64_t row = (int64_t)C.n * NB, tot = C.N * CPB, gs = (int64_t)gridDim.x * blockDim.x;
+        for (int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t0 < tot; t0 += U * gs) {
+            Vec<VW> gc[U], gu[U], gl[U];
 #pragma unroll
-            for (int c = 0; c < VW; ++c) {
-                float d0 = gc.v[c] - gu.v[c], d1 = gc.v[c] - gl.v[c];
-                nrm[0].v[c] += d0 * d0 + d1 * d1;
+            for (int u = 0; u < U; ++u) {
+                const int64_t t = t0 + u * gs;
+                if (t < tot) {
+                    const int64_t pix = t / CPB;
+                    const int i = (int)(pix / C.n), j = (int)(pix % C.n);
+                    const int64_t o = pix * NB + (t % CPB) * VW;
+                    gc[u] = ld_gather<VW>(src + o, pol);
+                    gu[u] = i > 0 ? ld_gather<VW>(src + o - row, pol) : gc[u];
+                    gl[u] = j > 0 ? ld_gather<VW>(src + o - NB, pol) : gc[u];
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                if (t0 + u * gs < tot) {
+#pragma unroll
+                    for (int c = 0; c < VW; ++c) {
+                        float d0 = gc[u].v[c] - gu[u].v[c], d1 = gc[u].v[c] - gl[u].v[c];
+                        nrm[0].v[c] += d0 * d0 + d1 * d1;
+                    }
+                }
             }
         }
     }
     const int64_t rstep = (int64_t)gridDim.x * rpb;
-    const unsigned long long pol = l2_evict_last_policy();
     for (int64_t row0 = (int64_t)blockIdx.x * rpb; row0 < C.M; row0 += rstep) {
         const int64_t ray = row0 + threadIdx.x / G_;
         int64_t b = 0, e = 0;

@@ -104,6 +104,24 @@ __device__ __forceinline__ void st_v(float *p, const Vec<VW> &a)
     }
 }
 
+// Store of data that the next kernels read again (G: gathered by A G, read
+// by the TV step): written to L2 with evict-last priority, so that it stays
+// there while the table streams (evict-first) pass through.
+template <int VW>
+__device__ __forceinline__ void st_keep(float *p, const Vec<VW> &a, unsigned long long pol)
+{
+    if constexpr (VW == 4) {
+        asm volatile("st.global.L2::cache_hint.v4.f32 [%0], {%1,%2,%3,%4}, %5;" ::"l"(p), "f"(a.v[0]), "f"(a.v[1]),
+                     "f"(a.v[2]), "f"(a.v[3]), "l"(pol)
+                     : "memory");
+    } else if constexpr (VW == 2) {
+        asm volatile("st.global.L2::cache_hint.v2.f32 [%0], {%1,%2}, %3;" ::"l"(p), "f"(a.v[0]), "f"(a.v[1]), "l"(pol)
+                     : "memory");
+    } else {
+        asm volatile("st.global.L2::cache_hint.f32 [%0], %1, %2;" ::"l"(p), "f"(a.v[0]), "l"(pol) : "memory");
+    }
+}
+
 __device__ __forceinline__ Entry ld_entry(const Entry *p)
 {
     // table entries are read once per pass: stream them past L1
