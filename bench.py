@@ -69,6 +69,9 @@ def parse():
     ap.add_argument("--batched-otf", action="store_true",
                     help="batched workload through dect_adm_tv_batch (one launch per ADM phase over all slices, "
                          "on-the-fly projector) instead of dect_adm_tv_groups")
+    ap.add_argument("--batched-table", action="store_true",
+                    help="batched workload through dect_adm_tv_batch_ex with the stored tables (one launch per "
+                         "ADM phase over all slices) instead of dect_adm_tv_groups")
     ap.add_argument("--train-slices", type=int, default=2048,
                     help="learned workload: training slices (x 2 energies = training pairs)")
     ap.add_argument("--epochs", type=int, default=8, help="learned workload: training epochs")
@@ -593,7 +596,8 @@ def run_batched(args, rank, world, local):
     bins 368 + round((n - 256) / 256 * 368) x 0.6 mm; one dect_adm_tv_groups
     call per step (one stored-table ADM per geometry on its own stream;
     --batched-otf: dect_adm_tv_batch, every slice advanced by the same
-    launches with the on-the-fly projector), then PLS per geometry."""
+    launches with the on-the-fly projector; --batched-table: the same
+    launches over the stored tables), then PLS per geometry."""
     import torch
     import paper_1607_01650_gb300 as dect
     torch.cuda.set_device(local)
@@ -625,7 +629,12 @@ def run_batched(args, rank, world, local):
     def step():
         a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a0.record()
-        res = (dect.adm_tv_batch(groups, prm) if args.batched_otf else dect.adm_tv_groups(groups, prm))
+        if args.batched_table:
+            res = dect.adm_tv_batch(groups, prm, projector="table")
+        elif args.batched_otf:
+            res = dect.adm_tv_batch(groups, prm)
+        else:
+            res = dect.adm_tv_groups(groups, prm)
         a1.record()
         iters[:] = [r.iters for _, reps in res for r in reps]
         for (x, _), u in zip(res, us):
@@ -659,8 +668,10 @@ def run_batched(args, rank, world, local):
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
                 "data": "synthetic",
                 "config": {"workload": "uneven batch: 64 slices, n in {256..512} at 0.5 mm, 30-180 views",
-                           "path": "dect_adm_tv_batch (one launch per ADM phase over all slices, on-the-fly projector)"
-                           if args.batched_otf else "dect_adm_tv_groups (stored tables, a stream per geometry)",
+                           "path": ("dect_adm_tv_batch_ex (one launch per ADM phase over all slices, stored tables)"
+                                    if args.batched_table else
+                                    "dect_adm_tv_batch (one launch per ADM phase over all slices, on-the-fly projector)"
+                                    if args.batched_otf else "dect_adm_tv_groups (stored tables, a stream per geometry)"),
                            "geometries": len(groups), "mean_adm_iterations": float(np.mean(iters)),
                            "adm_ms_per_step": float(np.mean(adm_ms[-args.steps:])),
                            "operator_intersections_per_s": float(np.mean(isect[-args.steps:]) /

@@ -306,6 +306,24 @@ dect_status dect_adm_tv_groups(const dect_adm_group *groups, int n_groups,
 dect_status dect_adm_tv_batch(const dect_adm_group *groups, int n_groups, const dect_adm_params *params,
                               dect_stream stream);
 
+/* Projector forms of dect_adm_tv_batch_ex. */
+#define DECT_PROJ_TABLE 0 /* the plans' stored Siddon tables (Eq. (1), ref. [42]) */
+#define DECT_PROJ_OTF 1   /* computed on the fly, as dect_adm_tv_batch          */
+
+/*
+ * dect_adm_tv_batch with a choice of projector.  DECT_PROJ_TABLE streams
+ * each slice's stored tables, the ones dect_adm_tv uses (A x: a warp per ray
+ * of the ray-major table; A^T y: a warp per pixel of the pixel-major table,
+ * deterministic, no atomics), so every slice runs the iteration of
+ * dect_adm_tv on its plan, with the same launches per ADM phase over all
+ * slices as dect_adm_tv_batch; plans with rays along grid lines are
+ * accepted.  DECT_PROJ_OTF is dect_adm_tv_batch.  Arguments, layouts,
+ * reports and errors as dect_adm_tv_batch; DECT_ERR_INVALID_ARG for another
+ * `projector`.
+ */
+dect_status dect_adm_tv_batch_ex(const dect_adm_group *groups, int n_groups, const dect_adm_params *params,
+                                 int projector, dect_stream stream);
+
 /*
  * A x and A^T y as dect_project / dect_backproject, with the on-the-fly
  * projector of dect_adm_tv_batch (no table is read; the plan's ray and view

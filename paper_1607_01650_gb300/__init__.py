@@ -102,6 +102,7 @@ _SIGS = {
     "dect_pls_decompose_noalloc": (C.c_int, [_P, C.c_int, C.c_int, C.POINTER(_PlsParams), _P, _P, _P]),
     "dect_pls_edge_mask": (C.c_int, [_P, C.c_int, C.c_int, C.c_double, _P, _P]),
     "dect_adm_tv_batch": (C.c_int, [C.POINTER(_AdmGroup), C.c_int, C.POINTER(_AdmParams), _P]),
+    "dect_adm_tv_batch_ex": (C.c_int, [C.POINTER(_AdmGroup), C.c_int, C.POINTER(_AdmParams), C.c_int, _P]),
     "dect_project_otf": (C.c_int, [_P, _P, _P, C.c_int, _P]),
     "dect_backproject_otf": (C.c_int, [_P, _P, _P, C.c_int, _P]),
     "dect_kernel_launches": (C.c_int64, []),
@@ -541,11 +542,18 @@ def adm_tv_groups(groups, params: AdmParams, workers: int = 0, stream=None):
     return [(x, [_report(r) for r in rep[:2 * S]]) for x, rep, S in out]
 
 
-def adm_tv_batch(groups, params: AdmParams, stream=None):
+PROJ_TABLE, PROJ_OTF = 0, 1              # DECT_PROJ_* in include/dect.h
+
+
+def adm_tv_batch(groups, params: AdmParams, stream=None, projector: str = "otf"):
     """ADM-TV (Eq. (3)-(10)) of slices of uneven geometry, all advanced together
-    with one launch per ADM phase and the on-the-fly projector
-    (dect_adm_tv_batch).  groups: list of (plan, m [S, 2, nv, nb], x [S, 2, n, n]
-    or None); plans may repeat.  Returns [(x, reports)] in the order given."""
+    with one launch per ADM phase (dect_adm_tv_batch_ex), the projector
+    computed on the fly ("otf") or streamed from the plans' stored tables
+    ("table").  groups: list of (plan, m [S, 2, nv, nb], x [S, 2, n, n] or
+    None); plans may repeat.  Returns [(x, reports)] in the order given."""
+    proj = {"table": PROJ_TABLE, "otf": PROJ_OTF}.get(projector)
+    if proj is None:
+        raise DectError("projector must be 'table' or 'otf'")
     import torch
     cg = (_AdmGroup * max(len(groups), 1))()
     keep, out = [], []
@@ -563,7 +571,8 @@ def adm_tv_batch(groups, params: AdmParams, stream=None):
         cg[i] = _AdmGroup(plan.handle.value, _ptr(m, torch.float32, plan.device).value,
                           _ptr(x, torch.float32, plan.device).value, S, C.cast(rep, C.c_void_p).value)
         out.append((x, rep, S))
-    _check(load().dect_adm_tv_batch(cg, len(groups), C.byref(params._c()), _stream(stream)), "dect_adm_tv_batch")
+    _check(load().dect_adm_tv_batch_ex(cg, len(groups), C.byref(params._c()), proj, _stream(stream)),
+           "dect_adm_tv_batch_ex")
     return [(x, [_report(r) for r in rep[:2 * S]]) for x, rep, S in out]
 
 

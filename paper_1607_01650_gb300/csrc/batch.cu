@@ -21,6 +21,11 @@
 // point nearest the axis, so |t| <= half the image diagonal); the ray and
 // view parameters are computed in FP64 and stored in FP32.
 //
+// The multi-slice ADM also runs on the plans' stored tables instead
+// (dect_adm_tv_batch_ex with DECT_PROJ_TABLE): a warp per ray of the
+// ray-major table for A, a warp per pixel of the pixel-major table for A^T
+// (the row kernels of the single-plan ADM at two channels).
+//
 // Multi-slice ADM.  Each slice (both energies interleaved, [pixel][2])
 // keeps its own state and scalars; one launch per ADM phase covers every
 // running slice: a block map assigns blocks to (slice, part), and each
@@ -280,6 +285,10 @@ cudaError_t otf_operator(const dect_plan *P, const float *src, float *dst, int b
 // Multi-slice ADM
 // ---------------------------------------------------------------------------
 enum { PH_TV = 0, PH_BWD = 1, PH_FWD = 2, PH_COUNT = 3 };
+// stored-table projector: a warp per ray of the ray-major table (A) and per
+// pixel of the pixel-major table (A^T, the warps of a block taking turns
+// over the block's 16 x 16 tile, whose pixels share sinogram lines in L1)
+constexpr int kTabRaysPerBlock = kOtfBlock / 32;
 enum { Q_TV = 0, Q_RR = 1, Q_DD = 2, Q_QQ = 3, Q_GG = 4, Q_COUNT = 5 };
 
 struct SliceDesc {
@@ -290,6 +299,9 @@ struct SliceDesc {
     float *x;                                  // [2][N] images (caller's)
     float beta[2];
     int blk0[PH_COUNT], nblk[PH_COUNT];        // this slice's blocks in each phase's launch
+    // stored-table projector: the plan's ray-major and pixel-major tables
+    const int64_t *rowptr, *colptr;
+    const Entry *ent, *tent;
 };
 
 struct BatchDev {
@@ -489,7 +501,28 @@ __global__ void __launch_bounds__(kOtfBlock) k_tv_m(const SliceDesc *__restrict_
     }
 }
 
-// G = mu A^T r + grad^T p per pixel (adjoint on the fly); |G|^2 per channel.
+// G = mu A^T r + grad^T p of pixel (i, j), given a = (A^T r)(i, j); adds |G|^2.
+__device__ __forceinline__ void bwd_finish(const SliceDesc &d, const BatchConst &C, int i, int j, float2 a,
+                                           float (&acc)[1][2])
+{
+    const int n = d.G.g.n;
+    const int64_t q = (int64_t)i * n + j, N = d.N;
+    const float2 p0 = d.p[q], p1 = d.p[N + q];
+    const float2 pd = i + 1 < n ? d.p[q + n] : make_float2(0.f, 0.f);
+    const float2 pr = j + 1 < n ? d.p[N + q + 1] : make_float2(0.f, 0.f);
+    float2 g;
+    g.x = fmaf(C.mu, a.x, (i > 0 ? p0.x : 0.f) - pd.x + (j > 0 ? p1.x : 0.f) - pr.x);
+    g.y = fmaf(C.mu, a.y, (i > 0 ? p0.y : 0.f) - pd.y + (j > 0 ? p1.y : 0.f) - pr.y);
+    d.Gr[q] = g;
+    acc[0][0] += g.x * g.x;
+    acc[0][1] += g.y * g.y;
+}
+
+// G = mu A^T r + grad^T p per pixel of the block's 16 x 16 tile; |G|^2 per
+// channel.  TABLE: A^T r from the pixel-major table (a warp per pixel, the
+// block's warps taking the tile's pixels in turn); otherwise on the fly (a
+// thread per pixel).
+template <bool TABLE>
 __global__ void __launch_bounds__(kOtfBlock) k_bwd_m(const SliceDesc *__restrict__ SD, const int *__restrict__ bmap,
                                                     BatchDev B, BatchConst C)
 {
@@ -497,19 +530,25 @@ __global__ void __launch_bounds__(kOtfBlock) k_bwd_m(const SliceDesc *__restrict
     const SliceDesc &d = SD[s];
     const int n = d.G.g.n, lb = blockIdx.x - d.blk0[PH_BWD];
     float acc[1][2] = {{0.f, 0.f}};
-    int i, j;
-    if (tile_pixel(n, lb, i, j)) {
-        const int64_t q = (int64_t)i * n + j, N = d.N;
-        const float2 a = pixel_sum(d.G, i, j, d.r);
-        const float2 p0 = d.p[q], p1 = d.p[N + q];
-        const float2 pd = i + 1 < n ? d.p[q + n] : make_float2(0.f, 0.f);
-        const float2 pr = j + 1 < n ? d.p[N + q + 1] : make_float2(0.f, 0.f);
-        float2 g;
-        g.x = fmaf(C.mu, a.x, (i > 0 ? p0.x : 0.f) - pd.x + (j > 0 ? p1.x : 0.f) - pr.x);
-        g.y = fmaf(C.mu, a.y, (i > 0 ? p0.y : 0.f) - pd.y + (j > 0 ? p1.y : 0.f) - pr.y);
-        d.Gr[q] = g;
-        acc[0][0] = g.x * g.x;
-        acc[0][1] = g.y * g.y;
+    if constexpr (TABLE) {
+        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+        const int tx = (n + kOtfTile - 1) / kOtfTile;
+        const int i0 = (lb / tx) * kOtfTile, j0 = (lb % tx) * kOtfTile;
+        for (int k = warp; k < kOtfTile * kOtfTile; k += kOtfBlock / 32) {
+            const int i = i0 + k / kOtfTile, j = j0 + k % kOtfTile;
+            const bool ok = i < n && j < n;
+            int64_t b = 0, e = 0;
+            if (ok) {
+                b = d.colptr[(int64_t)i * n + j];
+                e = d.colptr[(int64_t)i * n + j + 1];
+            }
+            const Vec<2> a = row_dot<2, 32, true>(d.tent, b, e, reinterpret_cast<const float *>(d.r), d.M, lane,
+                                                 CHK_GATHER_AT);
+            if (ok && lane == 0) bwd_finish(d, C, i, j, make_float2(a.v[0], a.v[1]), acc);
+        }
+    } else {
+        int i, j;
+        if (tile_pixel(n, lb, i, j)) bwd_finish(d, C, i, j, pixel_sum(d.G, i, j, d.r), acc);
     }
     double out[2];
     if (slice_reduce<1>(acc, B.part, d.blk0[PH_BWD], d.nblk[PH_BWD], B.ctr + s * (PH_COUNT + 1) + PH_BWD, out) &&
@@ -573,7 +612,9 @@ __device__ void slice_finish(int s, const BatchConst &C, const BatchDev &B)
 // slice's step.  MODE 0: r = A f - beta m.  MODE 2: the same and |r|^2
 // (projected f-step).  MODE 3: |A f - beta m|^2 and |r - (A f - beta m)|^2
 // (check of the carried residual, into QQ and GG).
-template <int MODE>
+// TABLE: q (or A f) from the ray-major table, a warp per ray; otherwise on
+// the fly, a thread per ray.
+template <int MODE, bool TABLE>
 __global__ void __launch_bounds__(kOtfBlock) k_fwd_m(const SliceDesc *__restrict__ SD, const int *__restrict__ bmap,
                                                     BatchDev B, BatchConst C, int fsel)
 {
@@ -590,10 +631,27 @@ __global__ void __launch_bounds__(kOtfBlock) k_fwd_m(const SliceDesc *__restrict
             acc[0][1] += h0 * h0 + h1 * h1;
         }
     }
-    const int64_t ray = (int64_t)lb * kOtfBlock + threadIdx.x;
-    if (ray < d.M) {
-        const float2 *src = MODE == 1 ? d.Gr : d.f[fsel];
-        float2 v = ray_sum(d.G.g, __ldg(d.G.ray + ray), __ldg(d.G.inv + ray), src);
+    const float2 *src = MODE == 1 ? d.Gr : d.f[fsel];
+    int64_t ray;
+    float2 v = make_float2(0.f, 0.f);
+    bool mine;  // this thread holds the ray's sum
+    if constexpr (TABLE) {
+        ray = (int64_t)lb * kTabRaysPerBlock + (threadIdx.x >> 5);
+        int64_t b = 0, e = 0;
+        if (ray < d.M) {
+            b = d.rowptr[ray];
+            e = d.rowptr[ray + 1];
+        }
+        const Vec<2> a = row_dot<2, 32, true>(d.ent, b, e, reinterpret_cast<const float *>(src), d.N,
+                                             threadIdx.x & 31, CHK_GATHER_A);
+        v = make_float2(a.v[0], a.v[1]);
+        mine = ray < d.M && (threadIdx.x & 31) == 0;
+    } else {
+        ray = (int64_t)lb * kOtfBlock + threadIdx.x;
+        mine = ray < d.M;
+        if (mine) v = ray_sum(d.G.g, __ldg(d.G.ray + ray), __ldg(d.G.inv + ray), src);
+    }
+    if (mine) {
         if (MODE == 1) {
             d.q[ray] = v;
             acc[1][0] = v.x * v.x;
@@ -720,19 +778,42 @@ struct SliceIn {
 int tiles_of(int n) { return ((n + kOtfTile - 1) / kOtfTile) * ((n + kOtfTile - 1) / kOtfTile); }
 
 // Block maps of the three phases for the slices with `on[s]`; writes each
-// slice's first block and block count into its descriptor.
-void build_maps(std::vector<SliceDesc> &desc, const std::vector<char> &on, std::vector<int> (&map)[PH_COUNT])
+// slice's first block and block count into its descriptor.  table: the
+// forward phase takes a warp per ray.
+void build_maps(std::vector<SliceDesc> &desc, const std::vector<char> &on, std::vector<int> (&map)[PH_COUNT],
+                bool table)
 {
+    const int rays_per_block = table ? kTabRaysPerBlock : kOtfBlock;
     for (int ph = 0; ph < PH_COUNT; ++ph) map[ph].clear();
     for (size_t s = 0; s < desc.size(); ++s) {
         SliceDesc &d = desc[s];
-        const int nb[PH_COUNT] = {tiles_of(d.G.g.n), tiles_of(d.G.g.n), (int)((d.M + kOtfBlock - 1) / kOtfBlock)};
+        const int nb[PH_COUNT] = {tiles_of(d.G.g.n), tiles_of(d.G.g.n),
+                                  (int)((d.M + rays_per_block - 1) / rays_per_block)};
         for (int ph = 0; ph < PH_COUNT; ++ph) {
             d.blk0[ph] = (int)map[ph].size();
             d.nblk[ph] = nb[ph];
             if (on[s]) map[ph].insert(map[ph].end(), nb[ph], (int)s);
         }
     }
+}
+
+template <int MODE>
+void launch_fwd_m(bool table, int nblk, cudaStream_t st, const SliceDesc *dd, const int *map, const BatchDev &B,
+                  const BatchConst &C, int fsel)
+{
+    if (table)
+        k_fwd_m<MODE, true><<<nblk, kOtfBlock, 0, st>>>(dd, map, B, C, fsel);
+    else
+        k_fwd_m<MODE, false><<<nblk, kOtfBlock, 0, st>>>(dd, map, B, C, fsel);
+}
+
+void launch_bwd_m(bool table, int nblk, cudaStream_t st, const SliceDesc *dd, const int *map, const BatchDev &B,
+                  const BatchConst &C)
+{
+    if (table)
+        k_bwd_m<true><<<nblk, kOtfBlock, 0, st>>>(dd, map, B, C);
+    else
+        k_bwd_m<false><<<nblk, kOtfBlock, 0, st>>>(dd, map, B, C);
 }
 
 }  // namespace
@@ -761,10 +842,12 @@ extern "C" dect_status dect_backproject_otf(const dect_plan *plan, const float *
     return DECT_OK;
 }
 
-extern "C" dect_status dect_adm_tv_batch(const dect_adm_group *groups, int n_groups, const dect_adm_params *prm,
-                                         dect_stream stream)
+extern "C" dect_status dect_adm_tv_batch_ex(const dect_adm_group *groups, int n_groups, const dect_adm_params *prm,
+                                            int projector, dect_stream stream)
 {
     if (!groups || n_groups < 0 || !prm) return DECT_ERR_INVALID_ARG;
+    if (projector != DECT_PROJ_TABLE && projector != DECT_PROJ_OTF) return DECT_ERR_INVALID_ARG;
+    const bool table = projector == DECT_PROJ_TABLE;
     if (!(prm->mu > 0) || !(prm->rho > 0) || !(prm->beta[0] > 0) || !(prm->beta[1] > 0) || prm->max_iter < 0 ||
         (prm->step_rule != DECT_STEP_BB1 && prm->step_rule != DECT_STEP_CAUCHY) || !std::isfinite(prm->mu) ||
         !std::isfinite(prm->rho) || !std::isfinite(prm->xi) || !std::isfinite(prm->beta[0]) ||
@@ -779,7 +862,7 @@ extern "C" dect_status dect_adm_tv_batch(const dect_adm_group *groups, int n_gro
         if (G.n_slices > 0 && (!G.m || !G.x)) return DECT_ERR_INVALID_ARG;
         if (device >= 0 && G.plan->device != device) return DECT_ERR_INVALID_ARG;
         device = G.plan->device;
-        if (G.plan->n_grid_aligned > 0) {
+        if (!table && G.plan->n_grid_aligned > 0) {
             set_error_text("dect_adm_tv_batch: a plan has rays along grid lines, where the on-the-fly projector "
                            "and the stored table take different pixels; use dect_adm_tv for that geometry");
             return DECT_ERR_INVALID_ARG;
@@ -792,7 +875,8 @@ extern "C" dect_status dect_adm_tv_batch(const dect_adm_group *groups, int n_gro
     if (S == 0) return DECT_OK;
     DECT_CUDA(cudaSetDevice(device));
     cudaStream_t s = (cudaStream_t)stream;
-    for (const SliceIn &q : in) DECT_CUDA(otf_setup(q.plan, s));
+    if (!table)
+        for (const SliceIn &q : in) DECT_CUDA(otf_setup(q.plan, s));
 
     BatchConst C;
     const double xi = prm->xi > 0 ? prm->xi : prm->rho;
@@ -828,8 +912,12 @@ extern "C" dect_status dect_adm_tv_batch(const dect_adm_group *groups, int n_gro
         d.x = in[i].x;
         d.beta[0] = (float)prm->beta[0];
         d.beta[1] = (float)prm->beta[1];
+        d.rowptr = in[i].plan->rowptr;
+        d.colptr = in[i].plan->colptr;
+        d.ent = in[i].plan->ent;
+        d.tent = in[i].plan->tent;
     }
-    build_maps(desc, on, map);
+    build_maps(desc, on, map, table);
     const size_t max_blocks = std::max({map[0].size(), map[1].size(), map[2].size()});
     const size_t o_dbl = bytes;
     bytes += sizeof(double) * ((size_t)S * 2 * 4 + (size_t)S * Q_COUNT * 2 + max_blocks * 2 * 2);
@@ -919,7 +1007,7 @@ extern "C" dect_status dect_adm_tv_batch(const dect_adm_group *groups, int n_gro
         e = cudaGetLastError();
     }
     if (e == cudaSuccess) {  // r^0 = A f^0 - beta m
-        k_fwd_m<0><<<nblocks[PH_FWD], kOtfBlock, 0, s>>>(ddesc, dmap[PH_FWD], B, C, 0);
+        launch_fwd_m<0>(table, nblocks[PH_FWD], s, ddesc, dmap[PH_FWD], B, C, 0);
         count_launches(1);
         e = cudaGetLastError();
     }
@@ -930,9 +1018,9 @@ extern "C" dect_status dect_adm_tv_batch(const dect_adm_group *groups, int n_gro
     const int per_iter = C.nonneg ? 4 : 3;
     auto enqueue_iter = [&](int par, cudaStream_t st) {
         k_tv_m<<<nblocks[PH_TV], kOtfBlock, 0, st>>>(ddesc, dmap[PH_TV], B, C, par, 0);
-        if (C.nonneg) k_fwd_m<2><<<nblocks[PH_FWD], kOtfBlock, 0, st>>>(ddesc, dmap[PH_FWD], B, C, 1 - par);
-        k_bwd_m<<<nblocks[PH_BWD], kOtfBlock, 0, st>>>(ddesc, dmap[PH_BWD], B, C);
-        k_fwd_m<1><<<nblocks[PH_FWD], kOtfBlock, 0, st>>>(ddesc, dmap[PH_FWD], B, C, 0);
+        if (C.nonneg) launch_fwd_m<2>(table, nblocks[PH_FWD], st, ddesc, dmap[PH_FWD], B, C, 1 - par);
+        launch_bwd_m(table, nblocks[PH_BWD], st, ddesc, dmap[PH_BWD], B, C);
+        launch_fwd_m<1>(table, nblocks[PH_FWD], st, ddesc, dmap[PH_FWD], B, C, 0);
     };
     cudaStream_t cs = nullptr;
     cudaEvent_t ev = nullptr;
@@ -984,7 +1072,7 @@ extern "C" dect_status dect_adm_tv_batch(const dect_adm_group *groups, int n_gro
         }
         if (dropped && done + block <= K) {
             // stopped slices leave the launches (their state stays as it is)
-            build_maps(desc, on, map);
+            build_maps(desc, on, map, table);
             e = cudaStreamSynchronize(cs);
             if (e == cudaSuccess) e = cudaEventRecord(ev, cs);
             if (e == cudaSuccess) e = cudaStreamWaitEvent(s, ev, 0);
@@ -1006,14 +1094,14 @@ extern "C" dect_status dect_adm_tv_batch(const dect_adm_group *groups, int n_gro
     if (e == cudaSuccess) e = cudaStreamWaitEvent(s, ev, 0);
     if (e == cudaSuccess) {
         std::fill(on.begin(), on.end(), 1);
-        build_maps(desc, on, map);
+        build_maps(desc, on, map, table);
         e = upload_maps();
     }
     const int par = done & 1;
     if (e == cudaSuccess) {
         k_tv_m<<<nblocks[PH_TV], kOtfBlock, 0, s>>>(ddesc, dmap[PH_TV], B, C, par, 1);
-        if (C.nonneg) k_fwd_m<2><<<nblocks[PH_FWD], kOtfBlock, 0, s>>>(ddesc, dmap[PH_FWD], B, C, 1 - par);
-        k_fwd_m<3><<<nblocks[PH_FWD], kOtfBlock, 0, s>>>(ddesc, dmap[PH_FWD], B, C, 1 - par);
+        if (C.nonneg) launch_fwd_m<2>(table, nblocks[PH_FWD], s, ddesc, dmap[PH_FWD], B, C, 1 - par);
+        launch_fwd_m<3>(table, nblocks[PH_FWD], s, ddesc, dmap[PH_FWD], B, C, 1 - par);
         k_pack_m<<<nblocks[PH_TV], kOtfBlock, 0, s>>>(ddesc, dmap[PH_TV], 0, 1 - par);
         count_launches(C.nonneg ? 4 : 3);
         e = cudaGetLastError();
@@ -1050,4 +1138,10 @@ extern "C" dect_status dect_adm_tv_batch(const dect_adm_group *groups, int n_gro
         }
     }
     return (hbad & 1) ? DECT_ERR_NONFINITE : DECT_OK;
+}
+
+extern "C" dect_status dect_adm_tv_batch(const dect_adm_group *groups, int n_groups, const dect_adm_params *prm,
+                                         dect_stream stream)
+{
+    return dect_adm_tv_batch_ex(groups, n_groups, prm, DECT_PROJ_OTF, stream);
 }

@@ -105,13 +105,15 @@ def uneven_groups(seed0=600, i0=1e5):
     return groups, refs
 
 
+@pytest.mark.parametrize("proj", ["otf", "table"])
 @pytest.mark.parametrize("opts", [{}, {"joint": True}, {"nonneg": True}, {"xi": 100.0, "step_rule": dect.BB1}])
-def test_batch_matches_oracle_fixed_iterations(opts):
-    """Eight geometries (28^2 - 64^2, 30 - 180 views), 13 slices in one call."""
+def test_batch_matches_oracle_fixed_iterations(opts, proj):
+    """Eight geometries (28^2 - 64^2, 30 - 180 views), 13 slices in one call,
+    the projector on the fly or from the stored tables."""
     groups, refs = uneven_groups()
     K = 15
     prm = dect.AdmParams(mu=MU, rho=RHO, max_iter=K, **opts)
-    res = dect.adm_tv_batch(groups, prm)
+    res = dect.adm_tv_batch(groups, prm, projector=proj)
     for (x, reps), (g, m) in zip(res, refs):
         t = oracle.table(g)
         x = x.cpu().numpy()
@@ -127,14 +129,15 @@ def test_batch_matches_oracle_fixed_iterations(opts):
                 assert x.min() >= 0.0
 
 
-def test_batch_stop_and_reports_match_oracle():
+@pytest.mark.parametrize("proj", ["otf", "table"])
+def test_batch_stop_and_reports_match_oracle(proj):
     """Run to the 1e-4 relative-objective stop: slices leave the launches as
     they stop; each channel's stop iteration within 2 of the oracle's, its
     image at that count and its reported objective as the oracle's, and the
     carried residual on A f - g."""
     groups, refs = uneven_groups(seed0=700, i0=3e3)
     prm = dect.AdmParams(mu=MU, rho=RHO, max_iter=3000, rel_obj_tol=1e-4, check_every=10)
-    res = dect.adm_tv_batch(groups, prm)
+    res = dect.adm_tv_batch(groups, prm, projector=proj)
     stops = []
     b = (1.0, 0.6)
     for (x, reps), (g, m) in zip(res, refs):
@@ -157,24 +160,47 @@ def test_batch_stop_and_reports_match_oracle():
     assert max(stops) - min(stops) >= 20  # slices left the launches at different checks
 
 
-def test_batch_equals_single_plan_path():
-    """One geometry through dect_adm_tv_batch and through dect_adm_tv (stored
-    table): the same iterates to FP32 rounding."""
+@pytest.mark.parametrize("proj", ["otf", "table"])
+def test_batch_equals_single_plan_path(proj):
+    """One geometry through dect_adm_tv_batch_ex and through dect_adm_tv
+    (stored table): the same iterates to FP32 rounding."""
     g = synth.tiny_geometry(n=48, nv=24, nb=72, px=1.0, sod=120.0, sdd=240.0)
     plan = dect.Plan(g)
     m = torch.tensor(np.stack([synth.make_slice(g, seed=90 + i).m for i in range(3)]), dtype=torch.float32,
                      device="cuda")
     prm = dect.AdmParams(mu=MU, rho=RHO, max_iter=40)
     xa, _ = dect.adm_tv(plan, m, prm)
-    [(xb, _)] = dect.adm_tv_batch([(plan, m, None)], prm)
+    [(xb, _)] = dect.adm_tv_batch([(plan, m, None)], prm, projector=proj)
     assert float((xa - xb).norm() / xa.norm()) <= 1e-5
 
 
-def test_batch_deterministic_and_empty():
+def test_batch_table_accepts_grid_aligned_rays():
+    """Rays along grid lines (the even detector of a centred geometry) are
+    refused by the on-the-fly form but run from the stored table, as the
+    oracle's Siddon table assigns them."""
+    g = synth.tiny_geometry(n=24, nv=12, nb=41, px=1.0, sod=60.0, sdd=120.0)  # odd nb: a ray through the axis
+    plan = dect.Plan(g)
+    assert plan.n_grid_aligned > 0
+    m = np.stack([synth.make_slice(g, seed=40 + i).m for i in range(2)]).astype(np.float32)
+    prm = dect.AdmParams(mu=MU, rho=RHO, max_iter=10)
+    with pytest.raises(dect.DectError):
+        dect.adm_tv_batch([(plan, torch.tensor(m, device="cuda"), None)], prm, projector="otf")
+    [(x, _)] = dect.adm_tv_batch([(plan, torch.tensor(m, device="cuda"), None)], prm, projector="table")
+    t = oracle.table(g)
+    x = x.cpu().numpy()
+    for i in range(2):
+        xo, _ = oracle.adm_dual(t, m[i].astype(np.float64),
+                                oracle.AdmParams(mu=MU, rho=RHO, max_iter=10, step_rule=oracle.CAUCHY))
+        for e in range(2):
+            assert rel_l2(x[i, e], xo[e]) <= 1e-4
+
+
+@pytest.mark.parametrize("proj", ["otf", "table"])
+def test_batch_deterministic_and_empty(proj):
     groups, _ = uneven_groups()
     prm = dect.AdmParams(mu=MU, rho=RHO, max_iter=12)
-    a = dect.adm_tv_batch(groups, prm)
-    b = dect.adm_tv_batch(groups, prm)
+    a = dect.adm_tv_batch(groups, prm, projector=proj)
+    b = dect.adm_tv_batch(groups, prm, projector=proj)
     for (xa, _), (xb, _) in zip(a, b):
         assert torch.equal(xa, xb)
     assert dect.adm_tv_batch([], prm) == []
