@@ -878,6 +878,11 @@ def main():
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": wdesc,
+                   "adm": {"mu": MU, "rho": RHO, "xi": RHO, "beta": list(BETA),
+                           "step_rule": "exact (Cauchy) step |G|^2 / (mu |AG|^2 + rho |grad G|^2) of the current "
+                                        "gradient; the paper's lagged BB-like step (step_rule BB1) is built and "
+                                        "tested, but often never meets the 1e-4 stop",
+                           "nonneg": bool(args.nonneg), "joint_tv": bool(args.joint)},
                    "slices_per_step_per_gpu": S, "mean_adm_iterations": mean_it,
                    "max_adm_iterations": int(max(state["iters"])),
                    "adm_iteration_quantiles": [int(v) for v in np.percentile(state["iters"], [0, 25, 50, 75, 100])],
