@@ -75,6 +75,8 @@ def parse():
     ap.add_argument("--train-slices", type=int, default=2048,
                     help="learned workload: training slices (x 2 energies = training pairs)")
     ap.add_argument("--epochs", type=int, default=8, help="learned workload: training epochs")
+    ap.add_argument("--conv-path", default="tcgen05", choices=["tcgen05", "mma"],
+                    help="learned workload: convolution kernels (tensor-memory tcgen05, or warp-level mma.sync)")
     ap.add_argument("--workload", default="paper", choices=["paper", "batched", "learned", "stress", "fbp", "cone"],
                     help="paper: 32 slices of 512^2/60 views per step (the headline); batched: "
                          "64 slices of uneven size (256^2-512^2) and view count (30-180) per step; "
@@ -424,8 +426,9 @@ def run_learned(args, rank, world, local):
     t_pairs = time.perf_counter() - t0
     net = dect.Cnn(device=local, max_pixels=64 * 512 * 512)  # 32 slices x 2 energies
     net.set_params(synth.cnn_init(0).astype(np.float32))
+    net.conv_path = dect.Cnn.CONV_TCGEN05 if args.conv_path == "tcgen05" else dect.Cnn.CONV_MMA_SYNC
     t0 = time.perf_counter()
-    losses = ws.train(net, pairs, epochs=args.epochs, batch=16, lr=1e-3)
+    losses = ws.train(net, pairs, epochs=args.epochs, batch=16)
     torch.cuda.synchronize()
     t_train = time.perf_counter() - t0
     ge = synth.paper_geometry()
@@ -472,6 +475,7 @@ def run_learned(args, rank, world, local):
             "config": {"workload": "learned warm start: train 256^2/60 views/368 bins, evaluate 512^2/60 views/736 bins",
                        "train_slices": args.train_slices, "train_images": 2 * args.train_slices,
                        "epochs": args.epochs, "final_train_mse": losses[-1], "first_epoch_mse": losses[0],
+                       "epoch_mse": [float("%.5g" % v) for v in losses], "conv_path": args.conv_path,
                        "pairs_seconds": round(t_pairs, 2), "train_seconds": round(t_train, 2),
                        "cold": res["cold"], "warm": res["warm"],
                        "speedup_vs_cold": res["warm"]["slices_per_s"] / res["cold"]["slices_per_s"]}}

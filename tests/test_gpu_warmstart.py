@@ -32,7 +32,7 @@ def test_trained_network_reduces_adm_iterations():
     pairs = ws.make_pairs(plan, _sinos(g, range(20000, 20256)), prm)
     net = dect.Cnn(max_pixels=64 * 128 * 128)
     net.set_params(synth.cnn_init(1).astype(np.float32))
-    losses = ws.train(net, pairs, epochs=6, batch=16, lr=1e-3)
+    losses = ws.train(net, pairs, epochs=6, batch=16)
     assert losses[-1] < losses[0]
     # held-out slices
     m = _sinos(g, range(30000, 30016))
@@ -66,7 +66,7 @@ def test_warm_start_is_faster_at_paper_size():
     pairs = ws.make_pairs(plan_t, _sinos(gt, range(10000, 11024)), prm)
     net = dect.Cnn(max_pixels=32 * 512 * 512)
     net.set_params(synth.cnn_init(0).astype(np.float32))
-    ws.train(net, pairs, epochs=6, batch=16, lr=1e-3)
+    ws.train(net, pairs, epochs=6, batch=16)
     g = synth.paper_geometry()
     plan = dect.Plan(g)
     m = _sinos(g, range(90000, 90016))
