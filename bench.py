@@ -69,6 +69,8 @@ def parse():
     ap.add_argument("--batched-otf", action="store_true",
                     help="batched workload through dect_adm_tv_batch (one launch per ADM phase over all slices, "
                          "on-the-fly projector) instead of dect_adm_tv_groups")
+    ap.add_argument("--workers", type=int, default=0,
+                    help="batched workload: host threads (geometries in flight) of dect_adm_tv_groups (0: min(groups, 8))")
     ap.add_argument("--batched-table", action="store_true",
                     help="batched workload through dect_adm_tv_batch_ex with the stored tables (one launch per "
                          "ADM phase over all slices) instead of dect_adm_tv_groups")
@@ -638,7 +640,7 @@ def run_batched(args, rank, world, local):
         elif args.batched_otf:
             res = dect.adm_tv_batch(groups, prm)
         else:
-            res = dect.adm_tv_groups(groups, prm)
+            res = dect.adm_tv_groups(groups, prm, workers=args.workers)
         a1.record()
         iters[:] = [r.iters for _, reps in res for r in reps]
         for (x, _), u in zip(res, us):
