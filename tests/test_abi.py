@@ -77,6 +77,11 @@ def test_host_side_argument_checks(lib):
     assert L.dect_plan_get_tuning(None, 2, None, None) == 1
     assert L.dect_plan_get_tv_tuning(None, 2, None, None) == 1
     assert L.dect_plan_set_tv_tuning(None, 2, 0) == 1
+    prm = dect.AdmParams()._c()
+    grp = (dect._AdmGroup * 1)()
+    assert L.dect_adm_tv_batch_ex(None, 1, C.byref(prm), dect.PROJ_TABLE, None) == 1  # no groups
+    assert L.dect_adm_tv_batch_ex(grp, 0, C.byref(prm), 2, None) == 1                 # unknown projector
+    assert L.dect_adm_tv_batch_ex(grp, 0, C.byref(prm), dect.PROJ_TABLE, None) == 0   # nothing to do
     assert L.dect_cnn_set_conv_path(None, 0) == 1
     assert L.dect_cnn_get_conv_path(None) == -1
     assert L.dect_cnn_check(None) == 1
