@@ -442,7 +442,10 @@ dect_status dect_pls_decompose_noalloc(const float *x, int n, int batch, const d
                                        float *u, dect_pls_report *reports, dect_stream stream);
 
 /* Kernel timing of one dect_adm_tv_ex call, from CUDA events recorded
- * around the launches of the two table kernels inside the iteration graph. */
+ * around the launches of the two table kernels of one iteration in each
+ * launched iteration graph (the middle one of each block of check_every
+ * iterations, and each single iteration): launch counts and totals cover
+ * those sampled launches. */
 typedef struct {
     double fwd_ms_total;   /* q = A G launches (ray-major table)      */
     double bwd_ms_total;   /* G = mu A^T r + ... (pixel-major table)  */
@@ -456,8 +459,10 @@ typedef struct {
 /*
  * dect_adm_tv with optional kernel timing (prof may be NULL, which makes it
  * identical to dect_adm_tv).  With prof != NULL, events are recorded around
- * every A G and A^T r launch and read back after each block of check_every
- * iterations; the totals cover all chunks of the call.
+ * the A G and A^T r launches of the middle iteration of each block of
+ * check_every iterations (an event pair per launch would add a few
+ * microseconds to every iteration) and read back after each block; the
+ * totals cover all chunks of the call.
  */
 dect_status dect_adm_tv_ex(const dect_plan *plan, const float *m, float *x, int n_slices,
                            const dect_adm_params *params, dect_adm_report *reports,
