@@ -247,7 +247,11 @@ typedef struct {
  * Up to 64 channels (32 slices) share one pass over the system matrix.  With
  * rel_obj_tol > 0, once no more than half of such a batch is still running,
  * the running channels continue in a batch half as wide (the same iterates;
- * only the order of the FP64 cross-block sums changes).
+ * only the order of the FP64 cross-block sums changes).  Calls of more than
+ * 32 slices run their chunks of 32 two at a time, from two host threads on
+ * streams of their own ordered after `stream`, after autotuning every batch
+ * width on the calling thread; each chunk's result is that of the chunk
+ * alone.
  * reports: HOST array [n_slices * 2] (may be NULL).  Synchronises `stream`.
  * Device scratch is taken from the stream-ordered allocator and returned
  * before the call ends.

@@ -42,6 +42,7 @@
 #include <algorithm>
 #include <atomic>
 #include <cmath>
+#include <string>
 #include <thread>
 #include <vector>
 
@@ -1755,15 +1756,11 @@ dect_status iterate(const dect_plan *P, const AdmConst &C, Work W, char *base, f
     return (hbad & 1) ? DECT_ERR_NONFINITE : DECT_OK;
 }
 
-template <int NB>
-dect_status run_chunk(const dect_plan *P, const float *m, float *x, int nimg,
-                      const dect_adm_params *prm, const float *beta_host, dect_adm_report *rep,
-                      dect_adm_profile *prof, cudaStream_t s)
+AdmConst adm_const(const dect_plan *P, const dect_adm_params *prm)
 {
-    const int64_t N = P->N;
     AdmConst C;
     C.n = P->n;
-    C.N = N;
+    C.N = P->N;
     C.M = P->M;
     C.mu = (float)prm->mu;
     C.rho = (float)prm->rho;
@@ -1776,6 +1773,45 @@ dect_status run_chunk(const dect_plan *P, const float *m, float *x, int nimg,
     C.rho_d = prm->rho;
     C.tol = prm->rel_obj_tol;
     C.rule = prm->step_rule;
+    return C;
+}
+
+// Autotune the A, A^T and TV-step variants of width NB and of every width a
+// batch of NB can narrow to, each on an empty workspace (as a narrowing does
+// before the state arrives), so that chunks run side by side later find
+// their choices made and no timing sees another chunk's kernels.  m: a
+// sinogram of the plan (read by the set-up projection only).
+template <int NB>
+cudaError_t pretune(const dect_plan *P, const float *m, const AdmConst &C, cudaStream_t s)
+{
+    const int idx = nb_index<NB>();
+    cudaError_t e = cudaSuccess;
+    if (P->bwd_choice[idx] < 0 || P->fwd_choice[idx] < 0 || P->tv_choice[idx] < 0) {
+        Work W;
+        char *base = nullptr;
+        e = alloc_work<NB>(P, W, &base, m, s);
+        W.bwd = 1;
+        W.fwd = 0;
+        W.tv = 0;
+        if (e == cudaSuccess) e = tune_bwd<NB>(P, W, C, s);
+        if (e == cudaSuccess) e = tune_fwd<NB>(P, W, C, s);
+        if (e == cudaSuccess) e = tune_tv<NB>(P, W, C, s);
+        if (base) cudaFreeAsync(base, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    }
+    if constexpr (NB > 2) {
+        if (e == cudaSuccess) e = pretune<NB / 2>(P, m, C, s);
+    }
+    return e;
+}
+
+template <int NB>
+dect_status run_chunk(const dect_plan *P, const float *m, float *x, int nimg,
+                      const dect_adm_params *prm, const float *beta_host, dect_adm_report *rep,
+                      dect_adm_profile *prof, cudaStream_t s)
+{
+    const int64_t N = P->N;
+    const AdmConst C = adm_const(P, prm);
 
     Work W;
     char *base = nullptr;
@@ -1848,30 +1884,98 @@ extern "C" dect_status dect_adm_tv_ex(const dect_plan *plan, const float *m, flo
         prof->fwd_launches = prof->bwd_launches = 0;
     }
     const int total = 2 * n_slices;
-    dect_status worst = DECT_OK;
-    for (int c0 = 0; c0 < total; c0 += kMaxBatchImages) {
+    const int nchunks = (total + kMaxBatchImages - 1) / kMaxBatchImages;
+    // one chunk of up to kMaxBatchImages channels (32 slices) on stream st
+    auto run_one = [&](int ci, cudaStream_t st, dect_adm_profile *pf) -> dect_status {
+        const int c0 = ci * kMaxBatchImages;
         const int nimg = std::min(kMaxBatchImages, total - c0);
         std::vector<float> beta(nimg);
         for (int b = 0; b < nimg; ++b) beta[b] = (float)prm->beta[(c0 + b) % 2];
         const float *mc = m + (int64_t)c0 * plan->M;
         float *xc = x + (int64_t)c0 * plan->N;
         dect_adm_report *rc = reports ? reports + c0 : nullptr;
-        dect_status st;
-        if (nimg <= 2)
-            st = run_chunk<2>(plan, mc, xc, nimg, prm, beta.data(), rc, prof, s);
-        else if (nimg <= 4)
-            st = run_chunk<4>(plan, mc, xc, nimg, prm, beta.data(), rc, prof, s);
-        else if (nimg <= 8)
-            st = run_chunk<8>(plan, mc, xc, nimg, prm, beta.data(), rc, prof, s);
-        else if (nimg <= 16)
-            st = run_chunk<16>(plan, mc, xc, nimg, prm, beta.data(), rc, prof, s);
-        else if (nimg <= 32)
-            st = run_chunk<32>(plan, mc, xc, nimg, prm, beta.data(), rc, prof, s);
-        else
-            st = run_chunk<64>(plan, mc, xc, nimg, prm, beta.data(), rc, prof, s);
-        if (st == DECT_ERR_NONFINITE) worst = st;
-        else if (st != DECT_OK) return st;
+        if (nimg <= 2) return run_chunk<2>(plan, mc, xc, nimg, prm, beta.data(), rc, pf, st);
+        if (nimg <= 4) return run_chunk<4>(plan, mc, xc, nimg, prm, beta.data(), rc, pf, st);
+        if (nimg <= 8) return run_chunk<8>(plan, mc, xc, nimg, prm, beta.data(), rc, pf, st);
+        if (nimg <= 16) return run_chunk<16>(plan, mc, xc, nimg, prm, beta.data(), rc, pf, st);
+        if (nimg <= 32) return run_chunk<32>(plan, mc, xc, nimg, prm, beta.data(), rc, pf, st);
+        return run_chunk<64>(plan, mc, xc, nimg, prm, beta.data(), rc, pf, st);
+    };
+    if (nchunks == 1) return run_one(0, s, prof);
+
+    // Several chunks: two at a time, each from its own host thread on its
+    // own stream, so that one chunk's kernels fill the SMs another leaves
+    // idle (the tail of each launch, the narrowed end of each chunk).  Every
+    // width is autotuned first; chunks share no data, so each gives the
+    // result it gives alone.
+    {
+        cudaError_t e = pretune<kMaxBatchImages>(plan, m, adm_const(plan, prm), s);
+        if (e != cudaSuccess) {
+            set_error("dect_adm_tv", e);
+            return e == cudaErrorMemoryAllocation ? DECT_ERR_OOM : DECT_ERR_CUDA;
+        }
     }
+    cudaEvent_t start = nullptr;
+    DECT_CUDA(cudaEventCreateWithFlags(&start, cudaEventDisableTiming));
+    DECT_CUDA(cudaEventRecord(start, s));
+    std::vector<dect_status> status(nchunks, DECT_OK);
+    std::vector<dect_adm_profile> profs(nchunks, dect_adm_profile{});
+    std::vector<std::string> errs(nchunks);
+    std::vector<cudaEvent_t> done(nchunks, nullptr);
+    std::atomic<int> next{0};
+    auto work = [&]() {
+        cudaSetDevice(plan->device);
+        cudaStream_t ws = nullptr;
+        if (cudaStreamCreateWithFlags(&ws, cudaStreamNonBlocking) != cudaSuccess) {
+            for (int c; (c = next.fetch_add(1)) < nchunks;) status[c] = DECT_ERR_CUDA;
+            return;
+        }
+        for (int c; (c = next.fetch_add(1)) < nchunks;) {
+            if (cudaStreamWaitEvent(ws, start, 0) != cudaSuccess) {
+                status[c] = DECT_ERR_CUDA;
+                continue;
+            }
+            status[c] = run_one(c, ws, prof ? &profs[c] : nullptr);
+            if (status[c] != DECT_OK) errs[c] = dect_last_error();
+            cudaEvent_t ev = nullptr;
+            if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) == cudaSuccess &&
+                cudaEventRecord(ev, ws) == cudaSuccess)
+                done[c] = ev;
+        }
+        cudaStreamSynchronize(ws);
+        cudaStreamDestroy(ws);
+    };
+    std::thread second(work);
+    work();
+    second.join();
+    dect_status worst = DECT_OK;
+    for (int c = 0; c < nchunks; ++c) {
+        if (done[c]) {
+            cudaStreamWaitEvent(s, done[c], 0);
+            cudaEventDestroy(done[c]);
+        }
+        if (status[c] == DECT_ERR_NONFINITE) {
+            if (worst == DECT_OK) worst = status[c];
+        } else if (status[c] != DECT_OK && (worst == DECT_OK || worst == DECT_ERR_NONFINITE)) {
+            worst = status[c];
+            set_error_text(errs[c]);
+        }
+        if (prof) {
+            const dect_adm_profile &q = profs[c];
+            const int64_t n0 = prof->fwd_launches, n1 = n0 + q.fwd_launches;
+            if (n1 > 0) {
+                prof->table_bytes_fwd = (int64_t)(((double)prof->table_bytes_fwd * n0 +
+                                                   (double)q.table_bytes_fwd * q.fwd_launches) / n1);
+                prof->table_bytes_bwd = (int64_t)(((double)prof->table_bytes_bwd * n0 +
+                                                   (double)q.table_bytes_bwd * q.fwd_launches) / n1);
+            }
+            prof->fwd_ms_total += q.fwd_ms_total;
+            prof->bwd_ms_total += q.bwd_ms_total;
+            prof->fwd_launches = n1;
+            prof->bwd_launches += q.bwd_launches;
+        }
+    }
+    cudaEventDestroy(start);
     return worst;
 }
 

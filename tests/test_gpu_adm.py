@@ -66,6 +66,28 @@ def test_batched_slices(ns):
             assert rel_l2(x[i, e], outs[i][0][e]) <= 1e-4
 
 
+def test_chunks_in_flight_equal_chunks_alone():
+    """A call of more than 32 slices runs its chunks of 32 two at a time on
+    their own streams; each chunk must give, bit for bit, what it gives as a
+    call of its own (the same plan, so the same autotuned variants), with the
+    relative-objective stop and the narrowing in play."""
+    g = synth.tiny_geometry(n=40, nv=20, nb=64, px=1.0, sod=120.0, sdd=240.0)
+    doses = [3e2, 1e6, 1e3, 3e5, 1e4]
+    ns = 70  # three chunks: 32, 32, 6 slices
+    m = np.stack([synth.make_slice(g, seed=900 + i, i0=doses[i % 5]).m for i in range(ns)]).astype(np.float32)
+    plan = dect.Plan(g)
+    prm = dect.AdmParams(mu=MU, rho=RHO, max_iter=2000, rel_obj_tol=1e-4, check_every=10)
+    md = torch.tensor(m, device="cuda")
+    x_all, rep_all = dect.adm_tv(plan, md, prm)
+    for c0 in range(0, ns, 32):
+        xc, rc = dect.adm_tv(plan, md[c0:c0 + 32].contiguous(), prm)
+        assert torch.equal(xc, x_all[c0:c0 + 32])
+        for a, b in zip(rc, rep_all[2 * c0: 2 * c0 + 2 * xc.shape[0]]):
+            assert (a.iters, a.converged, a.objective, a.rel_change) == (b.iters, b.converged, b.objective,
+                                                                         b.rel_change)
+    assert len({r.iters for r in rep_all}) > 1  # the stops (and narrowings) differ between channels
+
+
 def test_bb1_rule_and_xi():
     g = synth.tiny_geometry(n=40, nv=20, nb=64, px=1.0, sod=120.0, sdd=240.0)
     slices = [synth.make_slice(g, seed=7, i0=1e5)]
