@@ -711,6 +711,7 @@ class Cnn:
         with torch.cuda.device(device):
             _check(load().dect_cnn_create(device, max_pixels, C.byref(h)), "dect_cnn_create")
         self._h = h
+        self.max_pixels = int(max_pixels)
         self.num_params = int(load().dect_cnn_num_params())
 
     def close(self):

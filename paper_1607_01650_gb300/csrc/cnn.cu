@@ -1031,12 +1031,15 @@ __global__ void __launch_bounds__(256) k_sum_cols(const float *part, int nblk, i
 // ---------------------------------------------------------------------------
 // Elementwise pieces
 // ---------------------------------------------------------------------------
+// network input: channel 0 = x / s, channels 1 .. 31 zero (the first layer's
+// padded input); grid-stride, as its grid is capped (grid_for)
 __global__ void k_in_prep(const float *x, int P, float inv_s, bf16 *xin)
 {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= (int64_t)P * 32) return;
-    const int p = (int)(i / 32), c = (int)(i % 32);
-    xin[i] = __float2bfloat16(c == 0 ? x[p] * inv_s : 0.f);
+    const int64_t n = (int64_t)P * 32;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int p = (int)(i / 32), c = (int)(i % 32);
+        xin[i] = __float2bfloat16(c == 0 ? x[p] * inv_s : 0.f);
+    }
 }
 
 // dst (H/2 x W/2) = 2x2 average of src (H x W), C channels

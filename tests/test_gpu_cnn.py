@@ -52,6 +52,27 @@ def test_forward_matches_oracle(net, B, H, W):
         assert np.linalg.norm(res_gpu - res_ref) <= 3e-2 * np.linalg.norm(res_ref)
 
 
+def test_forward_matches_oracle_beyond_one_grid_pass():
+    """B H W above the elementwise kernels' capped grid (152 x 16 blocks of
+    256 threads cover 19456 pixels of 32 input channels): every pixel of the
+    second image lies beyond one pass of the grid."""
+    B, H, W = 2, 128, 96
+    rng = np.random.default_rng(5)
+    p = _params(9)
+    x = (0.02 * rng.random((B, H, W))).astype(np.float32)
+    big = dect.Cnn(max_pixels=B * H * W)
+    big.set_params(p.astype(np.float32))
+    out = big.forward(torch.tensor(x, device="cuda"), S).cpu().numpy()
+    big.close()
+    for b in range(B):
+        ref = oracle.cnn_forward(p.astype(np.float32).astype(np.float64), x[b].astype(np.float64), S)
+        res_gpu, res_ref = out[b] - x[b], ref - x[b]
+        assert np.linalg.norm(res_gpu - res_ref) <= 3e-2 * np.linalg.norm(res_ref), b
+        # the last rows as well (a stale input there would leave the norm test
+        # to the first rows)
+        assert np.linalg.norm(res_gpu[-16:] - res_ref[-16:]) <= 3e-2 * np.linalg.norm(res_ref[-16:]), b
+
+
 def test_gradient_matches_oracle(net):
     rng = np.random.default_rng(3)
     p = _params(11).astype(np.float32)

@@ -90,3 +90,30 @@ def test_warm_start_is_faster_at_paper_size():
     assert all(r.converged for r in rc + rw)
     assert np.mean([r.iters for r in rw]) + k0 < np.mean([r.iters for r in rc])
     assert warm_ms < cold_ms, (warm_ms, cold_ms)
+
+
+def test_tiled_application_equals_whole_image():
+    """The network applied tile by tile (crops with a 32-pixel halo, batched
+    by shape within the workspace) gives the whole image's output, pixel for
+    pixel, also where tiles meet and at the image border, and with tiles that
+    do not divide the image."""
+    rng = np.random.default_rng(4)
+    p = synth.cnn_init(2)
+    p[-33:] = rng.standard_normal(33) * 0.3
+    o = 0
+    for cin, cout in synth.CNN_LAYERS:
+        o += cout * cin * 9
+        p[o:o + cout] = 0.05 * rng.standard_normal(cout)
+        o += cout
+    B, H, W = 2, 384, 320
+    net = dect.Cnn(max_pixels=B * H * W)
+    net.set_params(p.astype(np.float32))
+    g = synth.tiny_geometry(n=64)
+    u = synth.rasterize(synth.random_ellipse_phantom(g, seed=5, axis_range=(6.0, 20.0)), 64, 1.0, supersample=2)
+    img = np.kron(u[0] + 2.0 * u[1], np.ones((6, 5)))[:H, :W]
+    x = torch.tensor(np.stack([0.02 * img, 0.015 * img[::-1]]).astype(np.float32) +
+                     1e-3 * rng.standard_normal((B, H, W)).astype(np.float32), device="cuda")
+    whole = net.forward(x, ws.SCALE)
+    for tile in (128, 96):
+        tiled = ws.apply_tiled(net, x, ws.SCALE, tile=tile, halo=32)
+        assert torch.equal(tiled, whole), tile
