@@ -471,6 +471,17 @@ def run_learned(args, rank, world, local):
         res["warm" if warm else "cold"] = {"slices_per_s": len(held) * S * args.steps / (ms / 1e3),
                                             "mean_iterations": float(np.mean(iters)),
                                             "mean_objective": float(np.mean(objs))}
+    # the same slices warm-started for the cold run's mean iteration count
+    # (20 plain + the rest after the network, no stop rule): the objective at
+    # an equal budget, beside the speed-up to the stop rule
+    budget = int(round(res["cold"]["mean_iterations"]))
+    pb = dataclasses.replace(stop, max_iter=budget - 20, rel_obj_tol=0.0)
+    objs = []
+    for m in held:
+        _, reps, _ = ws.warm_started_adm(net, plan, m, pb)
+        objs += [r.objective for r in reps]
+    res["warm_at_cold_budget"] = {"adm_iterations": budget, "mean_objective": float(np.mean(objs)),
+                                  "objective_over_cold": float(np.mean(objs)) / res["cold"]["mean_objective"]}
     line = {"metric": "DECT slices/s to 1e-4 rel. objective at 512^2/60 views, CNN warm start (2 energies + PLS)",
             "value": res["warm"]["slices_per_s"], "unit": UNIT, "n_gpus": 1, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * len(held) * S / res["warm"]["slices_per_s"],
@@ -481,7 +492,7 @@ def run_learned(args, rank, world, local):
                        "epochs": args.epochs, "final_train_mse": losses[-1], "first_epoch_mse": losses[0],
                        "epoch_mse": [float("%.5g" % v) for v in losses], "conv_path": args.conv_path,
                        "pairs_seconds": round(t_pairs, 2), "train_seconds": round(t_train, 2),
-                       "cold": res["cold"], "warm": res["warm"],
+                       "cold": res["cold"], "warm": res["warm"], "warm_at_cold_budget": res["warm_at_cold_budget"],
                        "speedup_vs_cold": res["warm"]["slices_per_s"] / res["cold"]["slices_per_s"],
                        "objective_warm_over_cold": res["warm"]["mean_objective"] / res["cold"]["mean_objective"],
                        "note": "both runs stop at the 1e-4 relative-objective rule; the stop points differ, "
